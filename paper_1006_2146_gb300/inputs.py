@@ -1,0 +1,235 @@
+"""Seeded synthetic inputs (initial states) shared by the tests, the bench and the smoke run.
+
+This module holds no arithmetic of the ADER-WENO method itself: it only
+builds zone-averaged conserved states (numpy, FP64) of analytic or seeded
+fields on a periodic unit cube, with the shapes of the paper's workloads.
+
+Layout: U has shape (5, n, n, n) = (rho, rho vx, rho vy, rho vz, eps) with the
+grid axes ordered (z, y, x); Bface has shape (3, n, n, n), Bface[d][..., i_d]
+the face average of B_d on face i_d - 1/2 (x = i * dx for face i).
+Units are Gaussian (B^2 / 8 pi in the energy), as in the paper's Eq. 3.
+"""
+import numpy as np
+
+FOUR_PI = 4.0 * np.pi
+
+
+def _gauss(npts):
+    x, w = np.polynomial.legendre.leggauss(npts)
+    return 0.5 * x, 0.5 * w          # nodes/weights on [-1/2, 1/2]
+
+
+def grid_shape(n):
+    """(nz, ny, nx) from an int n (cube) or a tuple (nz, ny, nx)."""
+    return (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
+
+
+def _centres(shape):
+    nz, ny, nx = shape
+    return ((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx)
+
+
+def cell_average(fn, n, npts=4):
+    """Average of fn(x, y, z) over every zone of the periodic unit cube (tensor Gauss-Legendre)."""
+    shape = grid_shape(n)
+    xg, wg = _gauss(npts)
+    cz, cy, cx = _centres(shape)
+    out = 0.0
+    for a, wa in zip(xg, wg):
+        for b, wb in zip(xg, wg):
+            for e, we in zip(xg, wg):
+                z = (cz + e / shape[0])[:, None, None]
+                y = (cy + b / shape[1])[None, :, None]
+                x = (cx + a / shape[2])[None, None, :]
+                out = out + wa * wb * we * fn(x, y, z)
+    return np.broadcast_to(out, shape).astype(np.float64).copy()
+
+
+def subsample_average(fn, n, sub=8):
+    """Average of a discontinuous fn by sub^3 mid-point samples per zone."""
+    shape = grid_shape(n)
+    s = (np.arange(sub) + 0.5) / sub - 0.5
+    cz, cy, cx = _centres(shape)
+    out = np.zeros(shape)
+    for a in s:
+        for b in s:
+            for e in s:
+                z = (cz + e / shape[0])[:, None, None]
+                y = (cy + b / shape[1])[None, :, None]
+                x = (cx + a / shape[2])[None, None, :]
+                out += fn(x, y, z)
+    return out / sub ** 3
+
+
+def _cons(rho, v, P, gamma, B=None):
+    ke = 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+    me = 0.0 if B is None else (B[0] ** 2 + B[1] ** 2 + B[2] ** 2) / (2.0 * FOUR_PI)
+    return np.stack([rho, rho * v[0], rho * v[1], rho * v[2], P / (gamma - 1.0) + ke + me])
+
+
+def density_wave(n, t=0.0, amp=0.2, vel=(1.0, 1.0, 1.0), P=1.0, gamma=1.4, npts=4):
+    """rho = 1 + amp sin(2 pi (x + y + z - (vx + vy + vz) t)), uniform v and P (exact translation)."""
+    s = vel[0] + vel[1] + vel[2]
+    rho = cell_average(lambda x, y, z: 1.0 + amp * np.sin(2 * np.pi * (x + y + z - s * t)), n, npts)
+    one = np.ones_like(rho)
+    return _cons(rho, [vel[0] * one, vel[1] * one, vel[2] * one], P * one, gamma)
+
+
+def sod_planar(n, gamma=1.4, normal=(1, 1, 0), left=(1.0, 1.0), right=(0.125, 0.1), sub=8):
+    """Planar Sod tube: (rho, P) = left where frac(n.x) < 1/2, else right; at rest.
+
+    The integer normal keeps the problem periodic on the unit cube.
+    """
+    def ind(x, y, z):
+        s = normal[0] * x + normal[1] * y + normal[2] * z
+        return ((s - np.floor(s)) < 0.5).astype(np.float64)
+    f = subsample_average(ind, n, sub)
+    rho = right[0] + (left[0] - right[0]) * f
+    P = right[1] + (left[1] - right[1]) * f
+    z = np.zeros_like(rho)
+    return _cons(rho, [z, z, z], P, gamma)
+
+
+def blast(n, gamma=1.4, p_in=1000.0, p_out=0.1, radius=0.1, center=(0.5, 0.5, 0.5), sub=4):
+    """Hydrodynamic blast (Sec. VIII.3): rho = 1 at rest, P = p_in for r < radius else p_out."""
+    def ind(x, y, z):
+        r2 = (x - center[0]) ** 2 + (y - center[1]) ** 2 + (z - center[2]) ** 2
+        return (r2 < radius * radius).astype(np.float64)
+    f = subsample_average(ind, n, sub)
+    P = p_out + (p_in - p_out) * f
+    rho = np.ones_like(P)
+    z = np.zeros_like(P)
+    return _cons(rho, [z, z, z], P, gamma)
+
+
+def random_smooth(n, seed, amp=0.1, kmax=None, gamma=1.4, P0=1.0):
+    """Seeded Gaussian random fields for rho and v (|k|^-2 spectrum, |k| <= kmax), P = P0."""
+    rng = np.random.default_rng(seed)
+    shape = grid_shape(n)
+    kmax = kmax or max(1, min(shape) // 4)
+    kz, ky, kx = np.meshgrid(*(np.fft.fftfreq(m) * m for m in shape), indexing="ij")
+    kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    filt = np.where((kk > 0) & (kk <= kmax), 1.0 / np.maximum(kk, 1.0), 0.0)
+
+    def field():
+        ph = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+        f = np.real(np.fft.ifftn(np.fft.fftn(ph.real) * filt))
+        return f / (np.abs(f).max() + 1e-300)
+    rho = 1.0 + amp * field()
+    v = [amp * field() for _ in range(3)]
+    P = P0 * np.ones_like(rho)
+    return _cons(rho, v, P, gamma)
+
+
+# ----------------------------------------------------------------------------- MHD
+def _edge_line_average(A, n, npts, d):
+    """Average of the component A_d along every edge parallel to direction d.
+
+    Edge (i, j, k) of direction d starts at the grid node x = (i, j, k)/n and
+    spans one zone along d.  Returns an (n, n, n) array indexed [k, j, i].
+    """
+    xg, wg = _gauss(npts)
+    idx = np.arange(n) / n
+    out = 0.0
+    for s, w in zip(xg, wg):
+        pos = [idx, idx, idx]
+        pos = [p.copy() for p in pos]
+        pos[d] = idx + (s + 0.5) / n
+        z = pos[2][:, None, None]
+        y = pos[1][None, :, None]
+        x = pos[0][None, None, :]
+        out = out + w * A(x, y, z)
+    return np.broadcast_to(out, (n, n, n)).astype(np.float64).copy()
+
+
+def face_field_from_potential(Acomp, n, npts=6):
+    """Face-averaged B = curl A by Stokes' theorem over each face (divergence-free to round-off).
+
+    Acomp = (Ax, Ay, Az) callables of (x, y, z).  Bface[d][k, j, i] is the
+    average normal field on the face of direction d through the grid node (i, j, k).
+    """
+    h = 1.0 / n
+    Ae = [_edge_line_average(Acomp[d], n, npts, d) for d in range(3)]   # line averages
+    sh = lambda a, d: np.roll(a, -1, axis=2 - d)
+    # Bx on x-face: (1/h^2) * circulation = (1/h)[(Az(j+1) - Az(j)) - (Ay(k+1) - Ay(k))]
+    Bx = ((sh(Ae[2], 1) - Ae[2]) - (sh(Ae[1], 2) - Ae[1])) / h
+    By = ((sh(Ae[0], 2) - Ae[0]) - (sh(Ae[2], 0) - Ae[2])) / h
+    Bz = ((sh(Ae[1], 0) - Ae[1]) - (sh(Ae[0], 1) - Ae[0])) / h
+    return np.stack([Bx, By, Bz])
+
+
+def alfven_wave(n, t=0.0, B0=1.0, amp=0.1, rho0=1.0, P0=1.0, gamma=5.0 / 3.0, npts=4):
+    """Circularly polarised Alfven wave along (1,1,1) (exact nonlinear solution, Gaussian units).
+
+    Wave vector 2 pi (1,1,1) (wavelength 1/sqrt(3), periodic on the unit
+    cube); B = B0 n + amp B0 (cos phi e1 + sin phi e2), v = -(B - B0 n)/sqrt(4 pi rho0),
+    phase phi = k . x - |k| V_A t with V_A = B0 / sqrt(4 pi rho0).
+    Returns (U, Bface); Bface comes from a vector potential.
+    """
+    nvec = np.array([1.0, 1.0, 1.0]) / np.sqrt(3.0)
+    e1 = np.array([1.0, -1.0, 0.0]) / np.sqrt(2.0)
+    e2 = np.cross(nvec, e1)
+    kmag = 2 * np.pi * np.sqrt(3.0)
+    VA = B0 / np.sqrt(FOUR_PI * rho0)
+
+    def phase(x, y, z):
+        return 2 * np.pi * (x + y + z) - kmag * VA * t
+
+    def Bvec(x, y, z, c):
+        ph = phase(x, y, z)
+        return B0 * nvec[c] + amp * B0 * (np.cos(ph) * e1[c] + np.sin(ph) * e2[c])
+
+    # vector potential: uniform part B0 n = curl(A0) with A0 = (B0/2) n x r, plus
+    # the wave part: curl of (amp B0/k)(cos phi e1 + sin phi e2) equals amp B0 (cos e1 + sin e2)
+    # because n x e1 = e2 and n x e2 = -e1 (k = |k| n).
+    def Acomp(c):
+        def A(x, y, z):
+            r = [x, y, z]
+            nxr = [nvec[1] * r[2] - nvec[2] * r[1], nvec[2] * r[0] - nvec[0] * r[2], nvec[0] * r[1] - nvec[1] * r[0]]
+            ph = phase(x, y, z)
+            wave = (amp * B0 / kmag) * (np.cos(ph) * e1[c] + np.sin(ph) * e2[c])
+            return 0.5 * B0 * nxr[c] + wave
+        return A
+    Bface = face_field_from_potential([Acomp(0), Acomp(1), Acomp(2)], n, npts=6)
+    # the uniform part's potential is not periodic; its face averages are exact
+    # (linear A), so replace them by the exact uniform values to restore periodicity
+    Bface = _periodic_fix(Bface, n, [B0 * nvec[c] for c in range(3)],
+                          [lambda x, y, z, c=c: (amp * B0 / kmag) * (np.cos(phase(x, y, z)) * e1[c] + np.sin(phase(x, y, z)) * e2[c]) for c in range(3)])
+    rho = rho0 * np.ones((n, n, n))
+    vz = [cell_average(lambda x, y, z, c=c: -(Bvec(x, y, z, c) - B0 * nvec[c]) / np.sqrt(FOUR_PI * rho0), n, npts)
+          for c in range(3)]
+    # energy: cell average of P/(g-1) + rho v^2/2 + B^2/8pi (|v|, |B| constant for this wave)
+    v2 = (amp * B0) ** 2 / (FOUR_PI * rho0)
+    B2 = B0 ** 2 * (1.0 + amp ** 2)
+    eps = (P0 / (gamma - 1.0) + 0.5 * rho0 * v2 + B2 / (2.0 * FOUR_PI)) * np.ones((n, n, n))
+    U = np.stack([rho, rho0 * vz[0], rho0 * vz[1], rho0 * vz[2], eps])
+    return U, Bface
+
+
+def _periodic_fix(Bface, n, uniform, wave_A):
+    """Face field = uniform part + curl of the (periodic) wave potential."""
+    Bw = face_field_from_potential(wave_A, n, npts=6)
+    return np.stack([Bw[c] + uniform[c] for c in range(3)])
+
+
+def orszag_tang(n, gamma=5.0 / 3.0, rho0=25.0 / (36.0 * np.pi), P0=5.0 / (12.0 * np.pi), B0=None):
+    """Orszag-Tang-type vortex extruded in z (standard 2-D fields; Gaussian units).
+
+    v = (-sin 2 pi y, sin 2 pi x, 0), B = B0 (-sin 2 pi y, sin 4 pi x, 0) from
+    A_z = B0 (cos 4 pi x / (4 pi) + cos 2 pi y / (2 pi)), B0 = sqrt(4 pi) / sqrt(4 pi) ... chosen
+    as 1/sqrt(4 pi) * sqrt(4 pi) = 1 in Heaviside units, i.e. sqrt(4 pi) * (1/sqrt(4 pi)) here.
+    """
+    if B0 is None:
+        B0 = 1.0          # equals the Heaviside-unit amplitude 1/sqrt(4 pi) times sqrt(4 pi)
+    Az = lambda x, y, z: B0 * (np.cos(4 * np.pi * x) / (4 * np.pi) + np.cos(2 * np.pi * y) / (2 * np.pi)) + 0 * z
+    zero = lambda x, y, z: 0.0 * (x + y + z)
+    Bface = face_field_from_potential([zero, zero, Az], n, npts=6)
+    rho = rho0 * np.ones((n, n, n))
+    vx = cell_average(lambda x, y, z: -np.sin(2 * np.pi * y) + 0 * x * z, n)
+    vy = cell_average(lambda x, y, z: np.sin(2 * np.pi * x) + 0 * y * z, n)
+    Bx2 = cell_average(lambda x, y, z: (B0 * np.sin(2 * np.pi * y)) ** 2 + 0 * x * z, n)
+    By2 = cell_average(lambda x, y, z: (B0 * np.sin(4 * np.pi * x)) ** 2 + 0 * y * z, n)
+    v2 = cell_average(lambda x, y, z: np.sin(2 * np.pi * y) ** 2 + np.sin(2 * np.pi * x) ** 2 + 0 * z, n)
+    eps = P0 / (gamma - 1.0) + 0.5 * rho0 * v2 + (Bx2 + By2) / (2.0 * FOUR_PI)
+    U = np.stack([rho, rho0 * vx, rho0 * vy, np.zeros_like(rho), eps])
+    return U, Bface
