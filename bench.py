@@ -1,0 +1,333 @@
+"""Throughput of the GB300 ADER-WENO step: 3-D zone-updates/s.
+
+Workload (default): 3-D Euler, gamma = 1.4, 256^3 periodic unit cube, planar
+Sod tube along (1,1,0) (rho 1/0.125, P 1/0.1), third-order nodal ADER-WENO,
+HLL flux, CFL 0.4, FP64 -- the 256^3 member of the smooth-advection +
+Sod-tube configuration family.  One step = the whole hot path: the CFL dt
+reduction (ader_max_dt) then one ADER step with that dt kept on the device
+(ader_step_devdt).  The state (671 MB) exceeds L2 (129 MB), so no flush is
+needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent problem of the same size (weak
+scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D zone-updates/s (ADER-WENO step incl. CFL dt reduction)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--order", type=int, default=3)
+    p.add_argument("--form", default="nodal", choices=["modal", "nodal"])
+    p.add_argument("--solver", default="hll", choices=["hll", "linearized"])
+    p.add_argument("--fp32", action="store_true")
+    p.add_argument("--no-variants", action="store_true", help="skip the per-variant table")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- peaks
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+def alu_peak_tflops(fp32, sm_mhz):
+    """ALU peak from unit counts and clock: 152 SMs; FP64 2 DFMA/clk/SM (the 1.25 TFLOP/s nominal rate
+    at 2070 MHz), FP32 128 FFMA/clk/SM; 2 FLOP per FMA."""
+    per_clk = 128 * 2 if fp32 else 2 * 2
+    return 152 * per_clk * sm_mhz * 1e6 / 1e12
+
+
+def flops_per_zone(order, form, solver, fp32):
+    """Exact FLOPs per zone of each kernel (op-counting instantiation of the kernels' per-zone code)."""
+    path = os.path.join(ROOT, "paper_1006_2146_gb300", "flops.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        f = json.load(fh)["order%d" % order]
+    return {"weno_reconstruction": f["weno_reconstruction"],
+            "predictor_faces": f["predictor_faces_" + form],
+            "riemann_update": f["riemann_update_" + solver]}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_config(ader, torch, n, order, form, solver, fp32, steps, warmup, stream, profile=False, state=None):
+    """Times `steps` steps of max_dt + step_devdt; returns (seconds, profile dict, solver, device state)."""
+    from paper_1006_2146_gb300 import inputs
+    s = ader.Solver((n, n, n), order=order, form=form, solver=solver, fp32=fp32)
+    if state is None:
+        state = torch.from_numpy(inputs.sod_planar(n, sub=2)).to("cuda")
+    d = state.clone()
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            s.max_dt(d, 0.4, dt, stream)
+            s.step_devdt(d, dt, stream)
+    torch.cuda.synchronize()
+    if profile:
+        ader.ader_profile(s.h, True)
+        ader.ader_profile_reset(s.h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            s.max_dt(d, 0.4, dt, stream)
+            s.step_devdt(d, dt, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    prof = ader.ader_profile_read(s.h) if profile else None
+    status = s.status(stream)
+    launches = ader.ader_launches_per_step(s.h) + 1
+    if status != 0:
+        raise RuntimeError("device status %d after the timed steps: %s" % (status, ader.ader_last_error(s.h)))
+    return e0.elapsed_time(e1) / 1e3, prof, s, d, launches
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    import paper_1006_2146_gb300 as ader
+    from paper_1006_2146_gb300 import inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ader.load()
+    n = args.n
+    zones = n ** 3
+    stream = torch.cuda.Stream()
+    U0 = torch.from_numpy(inputs.sod_planar(n, sub=2)).to("cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # headline: timed region bracketed by barrier + synchronize
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    t0 = time.perf_counter()
+    secs, prof, s, d, launches = run_config(ader, torch, n, args.order, args.form, args.solver, args.fp32,
+                                            args.steps, args.warmup, stream, profile=True, state=U0)
+    barrier()
+    wall = time.perf_counter() - t0
+    ck = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([secs], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        secs = float(tt.item())
+    value = zones * args.steps * world / secs
+
+    # dominant kernel roofline (ALU-bound: FLOPs per zone x zones / mean launch time)
+    fpz = flops_per_zone(args.order, args.form, args.solver, args.fp32)
+    kname, (kl, kms) = max(((k, v) for k, v in prof.items()), key=lambda kv: kv[1][1])
+    k_avg = kms / kl / 1e3
+    achieved = fpz[kname] * zones / k_avg / 1e12 if kname in fpz else None
+    sm_mhz = ck.get("sm_mhz") or 2070.0
+    peak = alu_peak_tflops(args.fp32, 2070.0)
+    total_ms = sum(v[1] for v in prof.values())
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_basis": "derived: 152 SM x %s at 2070 MHz max clock" % ("128 FFMA/clk" if args.fp32 else "2 DFMA/clk (1.25 TFLOP/s nominal FP64)"),
+                "flops_per_zone": fpz.get(kname), "mean_launch_ms": k_avg * 1e3,
+                "kernel_share": {k: round(v[1] / total_ms, 4) for k, v in prof.items()},
+                "hbm": {"algorithmic_bytes_per_zone_update": 80,
+                        "achieved_gbs": 80.0 * zones * args.steps / secs / 1e9,
+                        "peak_gbs": peaks().get("hbm_gbs"), "frac": 80.0 * zones * args.steps / secs / 1e9 / peaks().get("hbm_gbs", 6658.3)}}
+    s.close()
+    del d
+
+    # end-to-end through host memory: ader_step_host (H2D state, max_dt, step, D2H state) per step
+    host = torch.from_numpy(inputs.sod_planar(n, sub=2)).pin_memory().numpy()
+    se = ader.Solver((n, n, n), order=args.order, form=args.form, solver=args.solver, fp32=args.fp32)
+    for _ in range(2):
+        ader.ader_step_host(se.h, host, None, 0.4)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ader.ader_step_host(se.h, host, None, 0.4)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    se.close()
+    e2e = {"value": zones * args.steps * world / e2e_s, "unit": "zone-updates/s",
+           "h2d_bytes_per_step": 5 * 8 * zones, "d2h_bytes_per_step": 5 * 8 * zones + 8}
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        vs = []
+        for order in (2, 3, 4):
+            vs.append(("fp64_modal_hll_o%d" % order, order, "modal", "hll", False))
+            vs.append(("fp32_modal_hll_o%d" % order, order, "modal", "hll", True))
+        vs += [("fp64_nodal_linearized_o3", 3, "nodal", "linearized", False),
+               ("fp32_nodal_hll_o3", 3, "nodal", "hll", True)]
+        for name, order, form, solver, fp32 in vs:
+            vsecs, vprof, vs_, _, _ = run_config(ader, torch, n, order, form, solver, fp32, 3, 1, stream,
+                                                 profile=True, state=U0)
+            vs_.close()
+            variants[name] = {"zone_updates_per_s": zones * 3 / vsecs, "ms_per_step": vsecs / 3 * 1e3,
+                              "kernel_ms": {k: round(v[1] / v[0], 3) for k, v in vprof.items()}}
+        # SSP-RK of the same order and solver on the same GPU (Eq. 19), per step
+        srk = ader.Solver((n, n, n), order=3, form="nodal", solver="hll")
+        drk = U0.clone()
+        dtv = 1e-4
+        with torch.cuda.stream(stream):
+            srk.rk_step(drk, dtv, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                srk.rk_step(drk, dtv, stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        rks = e0.elapsed_time(e1) / 1e3
+        variants["fp64_ssprk3_hll_o3"] = {"zone_updates_per_s": zones * 3 / rks, "ms_per_step": rks / 3 * 1e3}
+        srk.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, budget_s=15.0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.fp32 else "f64",
+                "data": "synthetic (seeded analytic Sod tube; no dataset)",
+                "config": {"workload": "3D Euler Sod tube along (1,1,0), %d^3 periodic, order %d %s %s, CFL 0.4"
+                                       % (n, args.order, args.form, args.solver.upper()),
+                           "grid": n, "order": args.order, "form": args.form, "solver": args.solver,
+                           "precision": "fp32 bulk + fp64 update" if args.fp32 else "fp64",
+                           "l2": "state 671 MB > L2 129 MB (no flush needed)",
+                           "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
+                "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps,
+                "launches_per_step": launches, "clocks": ck, "wall_s_timed": wall, "variants": variants}
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle timings
+def cpu_baseline(args, budget_s=15.0):
+    """The FP64 oracle (numpy, as it stands) on a bounded sample of the same workload."""
+    import numpy as np
+
+    from oracle import scheme
+    from paper_1006_2146_gb300 import inputs
+    m = 32
+    U = inputs.sod_planar(m, sub=2)
+    dx = (1.0 / m,) * 3
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s or steps == 0:
+        dt = scheme.max_dt(U, dx, 0.4)
+        U = scheme.ader_step(U, dx, dt, args.order, args.form, args.solver)
+        steps += 1
+    el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+    return {"value": m ** 3 * steps / el, "unit": "zone-updates/s", "cores": threads, "kind": "oracle",
+            "sample": "%d steps of the same scheme on a %d^3 Sod tube (numpy FP64 oracle, %.1f s)" % (steps, m, el)}
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cpu = cpu_baseline(args, budget_s=max(5.0, 2.0 * args.steps))
+    line = {"metric": METRIC, "value": cpu["value"], "unit": "zone-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "3D Euler Sod tube along (1,1,0), order %d %s %s (bounded 32^3 sample)"
+                                   % (args.order, args.form, args.solver.upper())},
+            "cpu_baseline": cpu,
+            "e2e": {"value": cpu["value"], "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        reference_arm(a)
+    else:
+        gpu_arm(a)

@@ -1,0 +1,129 @@
+/*
+ * ader.h -- C ABI of the GB300 (sm_103a) one-step ADER-WENO update on 3-D periodic meshes.
+ *
+ * The operation is the time step of Balsara, Meyer, Dumbser, Du & Xu,
+ * "Efficient implementation of ADER schemes for Euler and MHD flows on
+ * structured meshes" (arXiv:1006.2146):
+ *   reconstruction (Sec. II.1), ADER-CG space-time predictor (Sec. II.2;
+ *   modal Sec. IV, nodal Apps. A-C), space-time averaged fluxes at faces with
+ *   the eigen-structure frozen at the face barycentre (Sec. II.3, Sec. V,
+ *   App. D), and the single conservative update of Eq. 6.  The SSP-RK step
+ *   of Eqs. 18-20 is provided for comparison on the same GPU.
+ *
+ * Conventions common to every entry point
+ *   - Every array argument is a DEVICE pointer owned by the caller unless the
+ *     name ends in _host.  The library owns only the scratch it allocates in
+ *     ader_create and frees in ader_destroy; no entry point except
+ *     ader_create allocates memory.
+ *   - State layout (structure of arrays, FP64, x fastest):
+ *       U[v][k][j][i], v = 0..4 = (rho, rho vx, rho vy, rho vz, eps),
+ *       element (v, k, j, i) at U[((v*nz + k)*ny + j)*nx + i].
+ *     eps is the total energy rho v^2/2 + P/(gamma-1) (+ B^2/8pi for MHD,
+ *     Gaussian units, Eq. 3).
+ *   - Boundaries are periodic in all three directions.  nx, ny, nz >= 1.
+ *   - Work is enqueued asynchronously on the given CUDA stream (NULL = the
+ *     legacy default stream); the call returns before the GPU finishes.
+ *   - Return value: ADER_OK (0) or a negative ADER_ERR_* code.  The text of
+ *     the last error of a context is returned by ader_last_error().  Errors
+ *     detected on the device (a non-physical state: rho <= 0 or P <= 0, a
+ *     non-finite value) set a device flag that ader_sync_status() reads.
+ */
+#ifndef ADER_GB300_H
+#define ADER_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int nx, ny, nz;          /* zones per direction */
+    double dx, dy, dz;       /* zone sizes */
+} ader_grid;
+
+/* Riemann solver at the faces (Sec. II.3, Eq. 56). */
+enum { ADER_HLL = 0, ADER_LINEARIZED = 1 };
+
+/* Option flags for ader_create. */
+enum {
+    ADER_MHD = 1u << 0,                 /* ideal MHD with face-centred B (reserved; not yet built) */
+    ADER_NODAL = 1u << 1,               /* nodal predictor (Apps. A-C); default modal (Sec. IV) */
+    ADER_FP32_BULK = 1u << 2,           /* FP32 reconstruction/predictor/fluxes, FP64 update and reductions */
+    ADER_CONVERGED_PREDICTOR = 1u << 4  /* iterate the predictor to tolerance instead of M-1 times */
+};
+
+enum {
+    ADER_OK = 0,
+    ADER_ERR_ARG = -1,          /* invalid argument (null pointer, bad size/order/flag) */
+    ADER_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+    ADER_ERR_UNPHYSICAL = -3,   /* device flag: rho <= 0 or P <= 0 met */
+    ADER_ERR_NONFINITE = -4,    /* device flag: a NaN or Inf met */
+    ADER_ERR_NOT_CONVERGED = -5 /* device flag: converged predictor hit its iteration cap */
+};
+
+typedef struct ader_ctx ader_ctx;
+
+/* Create a context for one grid.
+ *   order  : 2, 3 or 4 (spatial and temporal order; L_S = 4/10/20 spatial
+ *            modes, L = 5/15/35 space-time modes, Eqs. 10-16)
+ *   gamma  : ratio of specific heats (> 1)
+ *   solver : ADER_HLL or ADER_LINEARIZED
+ *   flags  : bitwise OR of ADER_NODAL, ADER_FP32_BULK, ADER_CONVERGED_PREDICTOR
+ * Allocates the device scratch for one step of this grid on the current
+ * device.  *out receives the context; on failure *out is NULL. */
+int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigned flags, ader_ctx** out);
+
+/* One ADER-WENO step of size dt (host value), in place on U (Eq. 6).
+ * Bface must be NULL (Euler). */
+int ader_step(ader_ctx* ctx, double* U, double* Bface, double dt, void* stream);
+
+/* Same as ader_step with dt read on the device from dt_dev (one double), so
+ * that a max_dt + step sequence needs no host round trip (graph capturable). */
+int ader_step_devdt(ader_ctx* ctx, double* U, double* Bface, const double* dt_dev, void* stream);
+
+/* CFL time step (reading of the paper's CFL rule, Secs. II.d and VI):
+ *   dt = cfl / max over zones of sum_d (|v_d| + c_d) / dx_d,
+ * c_d the sound speed.  Written to dt_dev (one double, device).  Reduction
+ * in FP64 with warp shuffles. */
+int ader_max_dt(ader_ctx* ctx, const double* U, const double* Bface, double cfl, double* dt_dev, void* stream);
+
+/* One SSP-RK step of the context's order (Eq. 18 for order 2, Eq. 19 for
+ * order 3, Eq. 20 for order 4) with the same reconstruction and Riemann
+ * solver and the App. D facial quadrature with every time mode zero. */
+int ader_rk_step(ader_ctx* ctx, double* U, double* Bface, double dt, void* stream);
+
+/* End-to-end step through host memory: copies U_host to the device, runs
+ * ader_max_dt (cfl) then ader_step, copies U back and returns the dt used in
+ * *dt_used_host.  Synchronous.  U_host should be pinned for full speed. */
+int ader_step_host(ader_ctx* ctx, double* U_host, double* Bface_host, double cfl, double* dt_used_host);
+
+/* Totals of the five conserved variables (FP64 reduction), written to
+ * totals_dev[0..4] (device). */
+int ader_diagnostics(ader_ctx* ctx, const double* U, const double* Bface, double* totals_dev, void* stream);
+
+/* Synchronise the stream and turn the device error flag into a return code
+ * (ADER_OK, ADER_ERR_UNPHYSICAL, ADER_ERR_NONFINITE, ADER_ERR_NOT_CONVERGED);
+ * clears the flag. */
+int ader_sync_status(ader_ctx* ctx, void* stream);
+
+/* Number of kernel launches the last ader_step / ader_rk_step enqueued. */
+int ader_launches_per_step(const ader_ctx* ctx);
+
+/* Per-kernel timing (tracing).  While enabled, every kernel the context
+ * enqueues is bracketed by CUDA events on its stream.  ader_profile_read
+ * synchronises the events, writes for up to `cap` kernel names their launch
+ * count and summed device time (ms) and returns the number of names (or a
+ * negative code); names are static strings owned by the library.  enable = 0
+ * stops recording; ader_profile_reset clears the totals. */
+int ader_profile(ader_ctx* ctx, int enable);
+int ader_profile_reset(ader_ctx* ctx);
+int ader_profile_read(ader_ctx* ctx, const char** names, int* launches, double* ms, int cap);
+
+const char* ader_last_error(const ader_ctx* ctx);
+void ader_destroy(ader_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADER_GB300_H */

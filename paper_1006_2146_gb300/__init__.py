@@ -1,0 +1,50 @@
+"""GB300-native (sm_103a) one-step ADER-WENO update on 3-D periodic meshes.
+
+The operation is the time step of Balsara, Meyer, Dumbser, Du & Xu,
+"Efficient implementation of ADER schemes for Euler and MHD flows on
+structured meshes" (arXiv:1006.2146).  The compute runs in the CUDA library
+built from csrc/ (C ABI: include/ader.h); this package is its ctypes binding
+plus the seeded input generators (``inputs``).
+"""
+from . import inputs  # noqa: F401
+from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_FP32_BULK, ADER_HLL, ADER_LINEARIZED, ADER_MHD, ADER_NODAL,  # noqa: F401
+                   AderError, ader_create, ader_destroy, ader_diagnostics, ader_last_error, ader_launches_per_step,
+                   ader_max_dt, ader_profile, ader_profile_read, ader_profile_reset, ader_rk_step, ader_step, ader_step_devdt, ader_step_host, ader_sync_status, load)
+
+
+class Solver:
+    """One ADER context on the current CUDA device (owns the library scratch)."""
+
+    def __init__(self, shape, order=3, form="modal", solver="hll", gamma=1.4, fp32=False, lengths=(1.0, 1.0, 1.0)):
+        nz, ny, nx = shape
+        self.shape = tuple(shape)
+        self.dx = (lengths[0] / nx, lengths[1] / ny, lengths[2] / nz)
+        flags = (ADER_NODAL if form == "nodal" else 0) | (ADER_FP32_BULK if fp32 else 0)
+        sol = ADER_HLL if solver == "hll" else ADER_LINEARIZED
+        self.h = ader_create(nx, ny, nz, self.dx[0], self.dx[1], self.dx[2], order, gamma, sol, flags)
+
+    def step(self, U, dt, stream=None):
+        ader_step(self.h, U, None, dt, stream)
+
+    def step_devdt(self, U, dt_dev, stream=None):
+        ader_step_devdt(self.h, U, None, dt_dev, stream)
+
+    def max_dt(self, U, cfl, dt_dev, stream=None):
+        ader_max_dt(self.h, U, None, cfl, dt_dev, stream)
+
+    def rk_step(self, U, dt, stream=None):
+        ader_rk_step(self.h, U, None, dt, stream)
+
+    def status(self, stream=None):
+        return ader_sync_status(self.h, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ader_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,169 @@
+"""ctypes binding of libader_gb300.so (include/ader.h): argument marshalling only.
+
+The functions keep the C names.  Device arrays are passed as torch CUDA
+tensors (float64, contiguous, the layout of ader.h); streams as
+torch.cuda.Stream or None (the current stream).  Every numerical step runs in
+the library's CUDA kernels; there is no fallback: a missing library raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libader_gb300.so")
+
+ADER_HLL, ADER_LINEARIZED = 0, 1
+ADER_MHD, ADER_NODAL, ADER_FP32_BULK, ADER_CONVERGED_PREDICTOR = 1, 2, 4, 16
+ADER_OK, ADER_ERR_ARG, ADER_ERR_CUDA, ADER_ERR_UNPHYSICAL, ADER_ERR_NONFINITE, ADER_ERR_NOT_CONVERGED = 0, -1, -2, -3, -4, -5
+
+EXPORTS = ("ader_create", "ader_step", "ader_step_devdt", "ader_max_dt", "ader_rk_step", "ader_step_host",
+           "ader_diagnostics", "ader_sync_status", "ader_launches_per_step", "ader_profile", "ader_profile_reset",
+           "ader_profile_read", "ader_last_error", "ader_destroy")
+
+
+class AderError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("ADER error %d: %s" % (code, msg))
+        self.code = code
+
+
+class ader_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+_LIB = None
+
+
+def load(path=None):
+    """Load the shared library (build it first with paper_1006_2146_gb300.build.build())."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError("libader_gb300.so not found at %s: run __graft_entry__.build() (nvcc, sm_103a)" % p)
+    lib = ctypes.CDLL(p)
+    vp, dbl, i32, u32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_uint
+    lib.ader_create.argtypes = [ctypes.POINTER(ader_grid), i32, dbl, i32, u32, ctypes.POINTER(vp)]
+    lib.ader_step.argtypes = [vp, vp, vp, dbl, vp]
+    lib.ader_step_devdt.argtypes = [vp, vp, vp, vp, vp]
+    lib.ader_max_dt.argtypes = [vp, vp, vp, dbl, vp, vp]
+    lib.ader_rk_step.argtypes = [vp, vp, vp, dbl, vp]
+    lib.ader_step_host.argtypes = [vp, vp, vp, dbl, ctypes.POINTER(dbl)]
+    lib.ader_diagnostics.argtypes = [vp, vp, vp, vp, vp]
+    lib.ader_sync_status.argtypes = [vp, vp]
+    lib.ader_launches_per_step.argtypes = [vp]
+    lib.ader_profile.argtypes = [vp, i32]
+    lib.ader_profile_reset.argtypes = [vp]
+    lib.ader_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32),
+                                      ctypes.POINTER(dbl), i32]
+    lib.ader_last_error.argtypes = [vp]
+    lib.ader_last_error.restype = ctypes.c_char_p
+    lib.ader_destroy.argtypes = [vp]
+    lib.ader_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("ader_destroy", "ader_last_error"):
+            getattr(lib, name).restype = i32
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    if hasattr(t, "ctypes"):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(int(t))
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+def _check(h, rc):
+    if rc != ADER_OK:
+        msg = load().ader_last_error(h).decode() if h else "invalid argument"
+        raise AderError(rc, msg)
+    return rc
+
+
+def ader_create(nx, ny, nz, dx, dy, dz, order=3, gamma=1.4, solver=ADER_HLL, flags=0):
+    g = ader_grid(nx, ny, nz, dx, dy, dz)
+    h = ctypes.c_void_p()
+    rc = load().ader_create(ctypes.byref(g), order, gamma, solver, flags, ctypes.byref(h))
+    if rc != ADER_OK:
+        raise AderError(rc, "ader_create failed (arguments or device memory)")
+    return h
+
+
+def ader_step(h, U, Bface, dt, stream=None):
+    return _check(h, load().ader_step(h, _ptr(U), _ptr(Bface), float(dt), _stream(stream)))
+
+
+def ader_step_devdt(h, U, Bface, dt_dev, stream=None):
+    return _check(h, load().ader_step_devdt(h, _ptr(U), _ptr(Bface), _ptr(dt_dev), _stream(stream)))
+
+
+def ader_max_dt(h, U, Bface, cfl, dt_dev, stream=None):
+    return _check(h, load().ader_max_dt(h, _ptr(U), _ptr(Bface), float(cfl), _ptr(dt_dev), _stream(stream)))
+
+
+def ader_rk_step(h, U, Bface, dt, stream=None):
+    return _check(h, load().ader_rk_step(h, _ptr(U), _ptr(Bface), float(dt), _stream(stream)))
+
+
+def ader_step_host(h, U_host, Bface_host, cfl):
+    """Host-memory step (copies inside); returns the dt used."""
+    dt = ctypes.c_double(0.0)
+    _check(h, load().ader_step_host(h, _ptr(U_host), _ptr(Bface_host), float(cfl), ctypes.byref(dt)))
+    return dt.value
+
+
+def ader_diagnostics(h, U, Bface, totals_dev, stream=None):
+    return _check(h, load().ader_diagnostics(h, _ptr(U), _ptr(Bface), _ptr(totals_dev), _stream(stream)))
+
+
+def ader_sync_status(h, stream=None):
+    """Returns the status code (does not raise on device flags)."""
+    return load().ader_sync_status(h, _stream(stream))
+
+
+def ader_launches_per_step(h):
+    return load().ader_launches_per_step(h)
+
+
+def ader_profile(h, enable=True):
+    return _check(h, load().ader_profile(h, 1 if enable else 0))
+
+
+def ader_profile_reset(h):
+    return _check(h, load().ader_profile_reset(h))
+
+
+def ader_profile_read(h):
+    """{kernel name: (launches, total device ms)} of the traced launches so far."""
+    cap = 32
+    names = (ctypes.c_char_p * cap)()
+    counts = (ctypes.c_int * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = load().ader_profile_read(h, names, counts, ms, cap)
+    if n < 0:
+        _check(h, n)
+    return {names[k].decode(): (counts[k], ms[k]) for k in range(min(n, cap))}
+
+
+def ader_last_error(h):
+    return load().ader_last_error(h).decode()
+
+
+def ader_destroy(h):
+    if h:
+        load().ader_destroy(h)

@@ -1,0 +1,389 @@
+// C ABI of the library (include/ader.h): context, scratch ownership, step
+// sequencing and error reporting.  Every numerical step runs in the kernels
+// of recon.cu, step_o*.cu and reduce.cu.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ader.h"
+#include "kernels.cuh"
+
+using namespace ader;
+
+struct ader_ctx {
+    ader_grid g;
+    Grid grid;
+    int order, solver;
+    unsigned flags;
+    double gamma;
+    bool fp32;
+    size_t rsize;                 // bytes per bulk scalar (4 or 8)
+    void* S1 = nullptr;
+    void* S2 = nullptr;
+    void* S3 = nullptr;
+    unsigned* flag = nullptr;                 // device error flag
+    unsigned long long* dtscr = nullptr;      // max_dt scratch (2 words)
+    double* partial = nullptr;                // totals partials
+    int tot_blocks = 0;
+    double* dt_dev = nullptr;                 // device dt of the host-memory path
+    double* Ustage = nullptr;                 // device state of the host-memory path
+    double* rk[7] = {};                       // SSP-RK stage states and operators
+    int launches = 0;
+    std::string err;
+    // tracing: pending event pairs per kernel name, folded into totals on read
+    bool profiling = false;
+    struct Pending { const char* name; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> spare;
+    std::vector<const char*> tnames;
+    std::vector<int> tcount;
+    std::vector<double> tms;
+};
+
+// Brackets one kernel launch with events when tracing is on.
+struct Trace {
+    ader_ctx* c;
+    const char* name;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    static cudaEvent_t take(ader_ctx* c) {
+        if (!c->spare.empty()) {
+            cudaEvent_t e = c->spare.back();
+            c->spare.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    Trace(ader_ctx* c_, const char* n, cudaStream_t s) : c(c_), name(n), st(s) {
+        if (c && c->profiling) {
+            a = take(c);
+            b = take(c);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~Trace() {
+        if (a) {
+            cudaEventRecord(b, st);
+            c->pending.push_back({name, a, b});
+        }
+    }
+};
+
+static int fail(ader_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+static int cuda_check(ader_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return ADER_OK;
+    return fail(c, ADER_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, int n_iter) {
+    StepArgs a;
+    a.grid = c->grid;
+    a.order = c->order;
+    a.form = (c->flags & ADER_NODAL) ? FORM_NODAL : FORM_MODAL;
+    a.solver = c->solver;
+    a.fp32 = c->fp32 ? 1 : 0;
+    a.n_iter = n_iter;
+    a.gamma = c->gamma;
+    a.dx[0] = c->g.dx;
+    a.dx[1] = c->g.dy;
+    a.dx[2] = c->g.dz;
+    a.dt = dt;
+    a.dt_dev = dt_dev;
+    a.S1 = c->S1;
+    a.S2 = c->S2;
+    a.S3 = c->S3;
+    a.flag = c->flag;
+    return a;
+}
+
+template <class R>
+static int enqueue_faces(ader_ctx* c, const StepArgs& a, const double* U, cudaStream_t st) {
+    int n;
+    {
+        Trace t(c, "weno_reconstruction", st);
+        n = launch_recon<R>(a, U, st);
+    }
+    Trace t(c, "predictor_faces", st);
+    switch (a.order) {
+        case 2: n += launch_predict_faces_order<2, R>(a, U, st); break;
+        case 3: n += launch_predict_faces_order<3, R>(a, U, st); break;
+        default: n += launch_predict_faces_order<4, R>(a, U, st); break;
+    }
+    return n;
+}
+
+// out = base + c * L(U) after computing the face data of U
+static int enqueue_operator(ader_ctx* c, const StepArgs& a, const double* U, double* out, const double* base,
+                            double coef, bool use_dt_dev, cudaStream_t st) {
+    int n = c->fp32 ? enqueue_faces<float>(c, a, U, st) : enqueue_faces<double>(c, a, U, st);
+    Trace t(c, "riemann_update", st);
+    n += c->fp32 ? launch_flux_update<float>(a, out, base, coef, use_dt_dev, st)
+                 : launch_flux_update<double>(a, out, base, coef, use_dt_dev, st);
+    return n;
+}
+
+extern "C" {
+
+int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigned flags, ader_ctx** out) {
+    if (!out) return ADER_ERR_ARG;
+    *out = nullptr;
+    if (!g || g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0))
+        return ADER_ERR_ARG;
+    if (order < 2 || order > 4 || !(gamma > 1.0) || (solver != ADER_HLL && solver != ADER_LINEARIZED))
+        return ADER_ERR_ARG;
+    const unsigned known = ADER_NODAL | ADER_FP32_BULK;
+    if (flags & ~known) return ADER_ERR_ARG;        // MHD and converged predictor are not built yet
+    ader_ctx* c = new ader_ctx();
+    c->g = *g;
+    c->grid.nx = g->nx;
+    c->grid.ny = g->ny;
+    c->grid.nz = g->nz;
+    c->grid.n = (long long)g->nx * g->ny * g->nz;
+    c->order = order;
+    c->solver = solver;
+    c->flags = flags;
+    c->gamma = gamma;
+    c->fp32 = (flags & ADER_FP32_BULK) != 0;
+    c->rsize = c->fp32 ? 4 : 8;
+    const size_t N = (size_t)c->grid.n;
+    int rc = ADER_OK;
+    auto alloc = [&](void** p, size_t bytes, const char* what) {
+        if (rc != ADER_OK || bytes == 0) return;
+        rc = cuda_check(c, cudaMalloc(p, bytes), what);
+    };
+    alloc(&c->S1, N * s1_per_zone(order) * c->rsize, "cudaMalloc S1");
+    alloc(&c->S2, N * (s2_per_zone(order) ? s2_per_zone(order) : 1) * c->rsize, "cudaMalloc S2");
+    alloc(&c->S3, N * s3_per_zone() * c->rsize, "cudaMalloc S3");
+    alloc((void**)&c->flag, sizeof(unsigned), "cudaMalloc flag");
+    alloc((void**)&c->dtscr, 2 * sizeof(unsigned long long), "cudaMalloc dt scratch");
+    c->tot_blocks = 1024;
+    alloc((void**)&c->partial, c->tot_blocks * 5 * sizeof(double), "cudaMalloc partials");
+    alloc((void**)&c->dt_dev, sizeof(double), "cudaMalloc dt");
+    alloc((void**)&c->Ustage, N * 5 * sizeof(double), "cudaMalloc host-path state");
+    for (int s = 0; s < 7; ++s) alloc((void**)&c->rk[s], N * 5 * sizeof(double), "cudaMalloc RK stage");
+    if (rc == ADER_OK) rc = cuda_check(c, cudaMemset(c->flag, 0, sizeof(unsigned)), "cudaMemset flag");
+    if (rc == ADER_OK) rc = cuda_check(c, cudaMemset(c->dtscr, 0, 2 * sizeof(unsigned long long)), "cudaMemset");
+    if (rc != ADER_OK) {
+        ader_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return ADER_OK;
+}
+
+void ader_destroy(ader_ctx* c) {
+    if (!c) return;
+    for (auto& p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->spare) cudaEventDestroy(e);
+    void* ptrs[] = {c->S1, c->S2, c->S3, c->flag, c->dtscr, c->partial, c->dt_dev, c->Ustage,
+                    c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6]};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+const char* ader_last_error(const ader_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int ader_launches_per_step(const ader_ctx* c) { return c ? c->launches : 0; }
+
+int ader_profile(ader_ctx* c, int enable) {
+    if (!c) return ADER_ERR_ARG;
+    c->profiling = enable != 0;
+    return ADER_OK;
+}
+
+int ader_profile_reset(ader_ctx* c) {
+    if (!c) return ADER_ERR_ARG;
+    for (auto& p : c->pending) {
+        c->spare.push_back(p.a);
+        c->spare.push_back(p.b);
+    }
+    c->pending.clear();
+    c->tnames.clear();
+    c->tcount.clear();
+    c->tms.clear();
+    return ADER_OK;
+}
+
+int ader_profile_read(ader_ctx* c, const char** names, int* launches, double* ms, int cap) {
+    if (!c) return ADER_ERR_ARG;
+    for (auto& p : c->pending) {
+        cudaError_t e = cudaEventSynchronize(p.b);
+        if (e != cudaSuccess) return cuda_check(c, e, "cudaEventSynchronize");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, p.a, p.b);
+        size_t k = 0;
+        while (k < c->tnames.size() && strcmp(c->tnames[k], p.name) != 0) ++k;
+        if (k == c->tnames.size()) {
+            c->tnames.push_back(p.name);
+            c->tcount.push_back(0);
+            c->tms.push_back(0.0);
+        }
+        c->tcount[k] += 1;
+        c->tms[k] += t;
+        c->spare.push_back(p.a);
+        c->spare.push_back(p.b);
+    }
+    c->pending.clear();
+    const int n = (int)c->tnames.size();
+    for (int k = 0; k < n && k < cap; ++k) {
+        if (names) names[k] = c->tnames[k];
+        if (launches) launches[k] = c->tcount[k];
+        if (ms) ms[k] = c->tms[k];
+    }
+    return n;
+}
+
+static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const double* dt_dev, void* stream) {
+    if (!c) return ADER_ERR_ARG;
+    if (!U) return fail(c, ADER_ERR_ARG, "U is null");
+    if (Bface) return fail(c, ADER_ERR_ARG, "Bface must be null: MHD is not built in this library version");
+    if (!dt_dev && !(dt > 0.0)) return fail(c, ADER_ERR_ARG, "dt must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    const StepArgs a = make_args(c, dt, dt_dev, c->order - 1);
+    c->launches = enqueue_operator(c, a, U, U, U, dt_dev ? 1.0 : dt, dt_dev != nullptr, st);
+    return cuda_check(c, cudaGetLastError(), "ader_step launch");
+}
+
+int ader_step(ader_ctx* c, double* U, double* Bface, double dt, void* stream) {
+    return step_common(c, U, Bface, dt, nullptr, stream);
+}
+
+int ader_step_devdt(ader_ctx* c, double* U, double* Bface, const double* dt_dev, void* stream) {
+    if (c && !dt_dev) return fail(c, ADER_ERR_ARG, "dt_dev is null");
+    return step_common(c, U, Bface, 0.0, dt_dev, stream);
+}
+
+int ader_max_dt(ader_ctx* c, const double* U, const double* Bface, double cfl, double* dt_dev, void* stream) {
+    if (!c) return ADER_ERR_ARG;
+    if (!U || !dt_dev) return fail(c, ADER_ERR_ARG, "null pointer");
+    if (Bface) return fail(c, ADER_ERR_ARG, "Bface must be null: MHD is not built in this library version");
+    if (!(cfl > 0.0)) return fail(c, ADER_ERR_ARG, "cfl must be positive");
+    const double dx[3] = {c->g.dx, c->g.dy, c->g.dz};
+    Trace t(c, "max_dt", (cudaStream_t)stream);
+    launch_max_dt(c->grid, U, c->gamma, dx, cfl, dt_dev, c->dtscr, c->flag, (cudaStream_t)stream);
+    return cuda_check(c, cudaGetLastError(), "ader_max_dt launch");
+}
+
+int ader_diagnostics(ader_ctx* c, const double* U, const double* Bface, double* totals_dev, void* stream) {
+    if (!c) return ADER_ERR_ARG;
+    if (!U || !totals_dev) return fail(c, ADER_ERR_ARG, "null pointer");
+    if (Bface) return fail(c, ADER_ERR_ARG, "Bface must be null: MHD is not built in this library version");
+    launch_totals(c->grid, U, totals_dev, c->partial, c->tot_blocks, (cudaStream_t)stream);
+    return cuda_check(c, cudaGetLastError(), "ader_diagnostics launch");
+}
+
+// SSP-RK stage tables of Eqs. 18-20: U(s) = sum_j A[s][j] U(j) + dt sum_j B[s][j] L(U(j))
+static const double RK2A[2][2] = {{1.0, 0.0}, {0.5, 0.5}};
+static const double RK2B[2][2] = {{1.0, 0.0}, {0.0, 0.5}};
+static const double RK3A[3][3] = {{1.0, 0, 0}, {0.75, 0.25, 0}, {1.0 / 3.0, 0.0, 2.0 / 3.0}};
+static const double RK3B[3][3] = {{1.0, 0, 0}, {0.0, 0.25, 0}, {0.0, 0.0, 2.0 / 3.0}};
+static const double RK4A[5][5] = {{1.0, 0, 0, 0, 0},
+                                  {0.44437049406734, 0.55562950593266, 0, 0, 0},
+                                  {0.62010185138540, 0.0, 0.37989814861460, 0, 0},
+                                  {0.17807995410773, 0.0, 0.0, 0.82192004589227, 0},
+                                  {0.00683325884039, 0.0, 0.51723167208978, 0.12759831133288, 0.34833675773694}};
+static const double RK4B[5][5] = {{0.39175222700392, 0, 0, 0, 0},
+                                  {0.0, 0.36841059262959, 0, 0, 0},
+                                  {0.0, 0.0, 0.25189177424738, 0, 0},
+                                  {0.0, 0.0, 0.0, 0.54497475021237, 0},
+                                  {0.0, 0.0, 0.0, 0.08460416338212, 0.22600748319395}};
+
+int ader_rk_step(ader_ctx* c, double* U, double* Bface, double dt, void* stream) {
+    if (!c) return ADER_ERR_ARG;
+    if (!U) return fail(c, ADER_ERR_ARG, "U is null");
+    if (Bface) return fail(c, ADER_ERR_ARG, "Bface must be null: MHD is not built in this library version");
+    if (!(dt > 0.0)) return fail(c, ADER_ERR_ARG, "dt must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ns = c->order == 2 ? 2 : (c->order == 3 ? 3 : 5);
+    const double* A = c->order == 2 ? &RK2A[0][0] : (c->order == 3 ? &RK3A[0][0] : &RK4A[0][0]);
+    const double* B = c->order == 2 ? &RK2B[0][0] : (c->order == 3 ? &RK3B[0][0] : &RK4B[0][0]);
+    const StepArgs a = make_args(c, dt, nullptr, 0);
+    const long long cnt = c->grid.n * 5;
+    // states[0] = U^n (copied), states[s] = U(s); ops[s] = L(U(s)) (stored only where reused)
+    double* states[5] = {c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4]};
+    double* ops[2] = {c->rk[5], c->rk[6]};
+    int n = 0;
+    cudaError_t e = cudaMemcpyAsync(states[0], U, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaMemcpyAsync");
+    for (int s = 0; s < ns; ++s) {
+        const double* rowA = A + s * ns;
+        const double* rowB = B + s * ns;
+        // state part of the stage
+        const double* X[6];
+        double w[6];
+        int m = 0;
+        for (int j = 0; j <= s; ++j)
+            if (rowA[j] != 0.0) {
+                X[m] = states[j];
+                w[m++] = rowA[j];
+            }
+        // operator terms other than L(U(s)) come from stored operators (only SSP(5,4)'s last stage)
+        if (ns == 5 && s == 4) {
+            X[m] = ops[0];          // L(U(3)) stored at stage 3
+            w[m++] = rowB[3] * dt;
+        }
+        double* dst = (s == ns - 1) ? U : states[s + 1];
+        {
+            Trace t(c, "rk_combine", st);
+            n += launch_lincomb(dst, m, X, w, cnt, st);
+        }
+        if (ns == 5 && s == 3) {
+            // keep L(U(3)) for the final stage: ops[0] = L(U(3)); then dst += B[3][3] dt L(U(3))
+            n += enqueue_operator(c, a, states[3], ops[0], nullptr, 1.0, false, st);
+            const double* Y[2] = {dst, ops[0]};
+            const double wy[2] = {1.0, rowB[3] * dt};
+            Trace t(c, "rk_combine", st);
+            n += launch_lincomb(dst, 2, Y, wy, cnt, st);
+        } else {
+            n += enqueue_operator(c, a, states[s], dst, dst, rowB[s] * dt, false, st);
+        }
+    }
+    c->launches = n + 1;
+    return cuda_check(c, cudaGetLastError(), "ader_rk_step launch");
+}
+
+int ader_sync_status(ader_ctx* c, void* stream) {
+    if (!c) return ADER_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    int rc = cuda_check(c, cudaMemcpyAsync(&h, c->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "flag read");
+    if (rc == ADER_OK) rc = cuda_check(c, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (rc != ADER_OK) return rc;
+    if (h) {
+        cudaMemsetAsync(c->flag, 0, sizeof(unsigned), st);
+        cudaStreamSynchronize(st);
+    }
+    if (h & FLAG_NONFINITE) return fail(c, ADER_ERR_NONFINITE, "non-finite value in the updated state");
+    if (h & FLAG_UNPHYSICAL) return fail(c, ADER_ERR_UNPHYSICAL, "rho <= 0 or P <= 0 in a zone");
+    if (h & FLAG_NOT_CONVERGED) return fail(c, ADER_ERR_NOT_CONVERGED, "predictor iteration cap reached");
+    return ADER_OK;
+}
+
+int ader_step_host(ader_ctx* c, double* U_host, double* Bface_host, double cfl, double* dt_used_host) {
+    if (!c) return ADER_ERR_ARG;
+    if (!U_host) return fail(c, ADER_ERR_ARG, "U_host is null");
+    if (Bface_host) return fail(c, ADER_ERR_ARG, "Bface must be null: MHD is not built in this library version");
+    const size_t bytes = (size_t)c->grid.n * 5 * sizeof(double);
+    cudaStream_t st = 0;
+    int rc = cuda_check(c, cudaMemcpyAsync(c->Ustage, U_host, bytes, cudaMemcpyHostToDevice, st), "H2D");
+    if (rc == ADER_OK) rc = ader_max_dt(c, c->Ustage, nullptr, cfl, c->dt_dev, st);
+    if (rc == ADER_OK) rc = ader_step_devdt(c, c->Ustage, nullptr, c->dt_dev, st);
+    if (rc == ADER_OK) rc = cuda_check(c, cudaMemcpyAsync(U_host, c->Ustage, bytes, cudaMemcpyDeviceToHost, st), "D2H");
+    if (rc == ADER_OK && dt_used_host)
+        rc = cuda_check(c, cudaMemcpyAsync(dt_used_host, c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, st), "D2H dt");
+    if (rc == ADER_OK) rc = cuda_check(c, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return rc;
+}
+
+}  // extern "C"

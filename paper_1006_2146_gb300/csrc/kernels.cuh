@@ -1,0 +1,48 @@
+// Launch interface shared by the kernel translation units and the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ader {
+
+enum { FORM_MODAL = 0, FORM_NODAL = 1 };
+enum { SOLVER_HLL = 0, SOLVER_LINEARIZED = 1 };
+
+// Everything a step's kernels need, passed by value.
+struct StepArgs {
+    Grid grid;
+    int order;          // 2, 3, 4
+    int form;           // FORM_MODAL / FORM_NODAL
+    int solver;         // SOLVER_HLL / SOLVER_LINEARIZED
+    int fp32;           // 1: FP32 bulk arithmetic
+    int n_iter;         // predictor iterations (order - 1 by default; 0 = spatial only, used by SSP-RK)
+    double gamma;
+    double dx[3];
+    double dt;          // used when dt_dev is null
+    const double* dt_dev;
+    void* S1;           // 1-D WENO moments          (R)
+    void* S2;           // cross moments             (R)
+    void* S3;           // face-side data             (R)
+    unsigned* flag;     // device error flag
+};
+
+// Number of R values per zone in each scratch array.
+inline int s1_per_zone(int order) { return 5 * 3 * (order - 1); }
+inline int s2_per_zone(int order) { return order == 2 ? 0 : (order == 3 ? 15 : 50); }
+inline int s3_per_zone() { return 6 * 3 * 5; }
+
+template <class R> int launch_recon(const StepArgs& a, const double* U, cudaStream_t st);
+template <int ORDER, class R> int launch_predict_faces_order(const StepArgs& a, const double* U, cudaStream_t st);
+// out = base + c * L(U) with L = -sum_d (F(i+1/2) - F(i-1/2)) / dx_d from the face data in S3;
+// c = c_host, multiplied by *a.dt_dev when use_dt_dev; base may equal out (in place) or be null (out = c L).
+template <class R> int launch_flux_update(const StepArgs& a, double* out, const double* base, double c_host,
+                                          bool use_dt_dev, cudaStream_t st);
+// out = sum_i c[i] X[i], i < n (n <= 6)
+int launch_lincomb(double* out, int n, const double* const* X, const double* c, long long count, cudaStream_t st);
+
+int launch_max_dt(const Grid& g, const double* U, double gamma, const double dx[3], double cfl, double* dt_dev,
+                  unsigned long long* scratch, unsigned* flag, cudaStream_t st);
+int launch_totals(const Grid& g, const double* U, double* totals_dev, double* partial, int nblocks, cudaStream_t st);
+
+}  // namespace ader

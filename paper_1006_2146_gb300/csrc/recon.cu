@@ -1,0 +1,74 @@
+// Zone-centred WENO reconstruction to Hermite modes (Sec. II.1, Eqs. 10-12).
+//
+// The paper defers the zone-centred scheme to its ref. [11]; this file
+// implements the reading stated in the library's design notes:
+//   * 1-D, per direction: order 3 (and 2) blends the 3-zone stencils
+//     {i-2..i}, {i-1..i+1}, {i..i+2} with linear weights (1, 10, 1)/12; order 4
+//     blends the 4-zone stencils {i-3..i} .. {i..i+3} with (1, 10, 10, 1)/22.
+//     Each candidate is the polynomial a + b P1 + c P2 (+ d P3) whose zone
+//     averages match the stencil (cell average of P1, P2, P3 over zone k is
+//     k, k^2, k^3 + k/10).  Order 2 keeps only b.
+//   * smoothness IS = b^2 + 13 c^2 / 3 (Eq. 24 form) or
+//     (b + d/10)^2 + 13 c^2 / 3 + 781 d^2 / 20 (Eq. 29 form);
+//     weights gamma_s / (1e-12 + IS_s)^2, normalised.
+//   * cross moments: WENO slope S_e (order-3 candidate set, b kept) of a
+//     moment field in a transverse direction, symmetrised:
+//     w8 = (S_y w2 + S_x w3)/2, w9 = (S_z w3 + S_y w4)/2, w10 = (S_z w2 + S_x w4)/2,
+//     w14 = S_y w5, w15 = S_z w5, w16 = S_x w6, w17 = S_z w6, w18 = S_x w7,
+//     w19 = S_y w7, w20 = (S_z w8 + S_x w9 + S_y w10)/3.
+//
+// Scratch layouts (N = nx*ny*nz zones, NV = 5 variables):
+//   S1[((r*3 + d)*NV + v)*N + zone]  1-D moment r (0: P1, 1: P2, 2: P3) along d
+//   S2[(c*NV + v)*N + zone]          cross moment c: w8 w9 w10 w14 w15 w16 w17 w18 w19 w20
+#include "common.cuh"
+#include "kernels.cuh"
+#include "weno.cuh"
+
+namespace ader {
+
+// ---------------------------------------------------------------- kernels (one thread per zone)
+template <int ORDER, class R>
+__global__ void __launch_bounds__(128) k_weno1d(Grid g, const double* __restrict__ U, R* __restrict__ S1) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < g.n) zone_weno1d<ORDER>(g, U, S1, z);
+}
+
+template <int ORDER, class R>
+__global__ void __launch_bounds__(128) k_cross1(Grid g, const R* __restrict__ S1, R* __restrict__ S2) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < g.n) zone_cross1<ORDER>(g, S1, S2, z);
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) k_cross2(Grid g, R* __restrict__ S2) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < g.n) zone_cross2(g, S2, z);
+}
+
+template <class R>
+int launch_recon(const StepArgs& a, const double* U, cudaStream_t st) {
+    const int T = 128;
+    const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
+    R* S1 = (R*)a.S1;
+    R* S2 = (R*)a.S2;
+    int n = 0;
+    switch (a.order) {
+        case 2: k_weno1d<2, R><<<blocks, T, 0, st>>>(a.grid, U, S1); n = 1; break;
+        case 3:
+            k_weno1d<3, R><<<blocks, T, 0, st>>>(a.grid, U, S1);
+            k_cross1<3, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
+            n = 2;
+            break;
+        default:
+            k_weno1d<4, R><<<blocks, T, 0, st>>>(a.grid, U, S1);
+            k_cross1<4, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
+            k_cross2<R><<<blocks, T, 0, st>>>(a.grid, S2);
+            n = 3;
+    }
+    return n;
+}
+
+template int launch_recon<double>(const StepArgs&, const double*, cudaStream_t);
+template int launch_recon<float>(const StepArgs&, const double*, cudaStream_t);
+
+}  // namespace ader

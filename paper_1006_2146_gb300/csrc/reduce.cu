@@ -1,0 +1,146 @@
+// FP64 reductions: the CFL time step (warp shuffles, one launch with a
+// last-block finish) and the conservation totals (deterministic two passes);
+// plus the flux-update launcher and the state linear combination of SSP-RK.
+#include "kernels.cuh"
+#include "step_kernels.cuh"
+
+namespace ader {
+
+// dt = cfl / max over zones of sum_d (|v_d| + a) / dx_d (reading of the CFL rule).
+// scratch[0]: running maximum as the bit pattern of a non-negative double
+// (ordered like an unsigned integer); scratch[1]: blocks finished.  The last
+// block to finish writes dt and resets both words for the next call.
+__global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict__ U, double gamma, double idx,
+                                                double idy, double idz, double cfl, double* dt_out,
+                                                unsigned long long* scratch, unsigned* flag) {
+    double s = 0.0;
+    bool bad = false;
+    const long long N = g.n;
+    for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < N; z += (long long)gridDim.x * blockDim.x) {
+        const double rho = U[z], mx = U[N + z], my = U[2 * N + z], mz = U[3 * N + z], E = U[4 * N + z];
+        const double ir = 1.0 / rho;
+        const double vx = mx * ir, vy = my * ir, vz = mz * ir;
+        const double p = (gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy + mz * vz));
+        if (!(rho > 0.0) || !(p > 0.0)) {
+            bad = true;
+            continue;
+        }
+        const double a = sqrt(gamma * p * ir);
+        const double v = (fabs(vx) + a) * idx + (fabs(vy) + a) * idy + (fabs(vz) + a) * idz;
+        s = fmax(s, v);
+    }
+    if (bad) raise_flag(flag, FLAG_UNPHYSICAL);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    __shared__ double warp_max[8];
+    __shared__ bool last;
+    if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, warp_max[w]);
+        atomicMax(&scratch[0], (unsigned long long)__double_as_longlong(b));
+        __threadfence();
+        const unsigned long long done = atomicAdd(&scratch[1], 1ull);
+        last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const double mx = __longlong_as_double((long long)atomicAdd(&scratch[0], 0ull));
+        *dt_out = mx > 0.0 ? cfl / mx : 0.0;
+        scratch[0] = 0ull;
+        scratch[1] = 0ull;
+    }
+}
+
+int launch_max_dt(const Grid& g, const double* U, double gamma, const double dx[3], double cfl, double* dt_dev,
+                  unsigned long long* scratch, unsigned* flag, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = (g.n + 255) / 256;
+    const long long cap = (long long)sms * 8;
+    const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+    k_max_dt<<<blocks, 256, 0, st>>>(g, U, gamma, 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2], cfl, dt_dev, scratch, flag);
+    return 1;
+}
+
+// ---------------------------------------------------------------- totals
+__global__ void __launch_bounds__(256) k_totals_partial(Grid g, const double* __restrict__ U, double* partial) {
+    double s[5] = {0, 0, 0, 0, 0};
+    const long long N = g.n;
+    for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < N; z += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s[v] += U[v * N + z];
+    __shared__ double sh[5][256];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sh[v][threadIdx.x] = s[v];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sh[v][threadIdx.x] += sh[v][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) partial[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_totals_final(const double* partial, int nblocks, double* out) {
+    if (threadIdx.x < 5) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partial[b * 5 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+int launch_totals(const Grid& g, const double* U, double* totals_dev, double* partial, int nblocks, cudaStream_t st) {
+    k_totals_partial<<<nblocks, 256, 0, st>>>(g, U, partial);
+    k_totals_final<<<1, 32, 0, st>>>(partial, nblocks, totals_dev);
+    return 2;
+}
+
+// ---------------------------------------------------------------- SSP-RK combination
+struct Comb {
+    const double* X[6];
+    double c[6];
+    int n;
+};
+
+__global__ void __launch_bounds__(256) k_lincomb(double* out, Comb cb, long long count) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < cb.n; ++t) s += cb.c[t] * cb.X[t][i];
+        out[i] = s;
+    }
+}
+
+int launch_lincomb(double* out, int n, const double* const* X, const double* c, long long count, cudaStream_t st) {
+    Comb cb;
+    cb.n = n;
+    for (int t = 0; t < n; ++t) {
+        cb.X[t] = X[t];
+        cb.c[t] = c[t];
+    }
+    const long long blocks = (count + 255) / 256;
+    k_lincomb<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(out, cb, count);
+    return 1;
+}
+
+// ---------------------------------------------------------------- flux + update
+template <class R>
+int launch_flux_update(const StepArgs& a, double* out, const double* base, double c_host, bool use_dt_dev,
+                       cudaStream_t st) {
+    const int T = 128;
+    const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
+    if (a.solver == SOLVER_HLL)
+        k_flux_update<SOLVER_HLL, R><<<blocks, T, 0, st>>>(a, out, base, c_host, use_dt_dev ? 1 : 0);
+    else
+        k_flux_update<SOLVER_LINEARIZED, R><<<blocks, T, 0, st>>>(a, out, base, c_host, use_dt_dev ? 1 : 0);
+    return 1;
+}
+
+template int launch_flux_update<double>(const StepArgs&, double*, const double*, double, bool, cudaStream_t);
+template int launch_flux_update<float>(const StepArgs&, double*, const double*, double, bool, cudaStream_t);
+
+}  // namespace ader

@@ -1,0 +1,22 @@
+// Order-3 instantiation of the predictor + face kernel (see step_kernels.cuh).
+#include "step_kernels.cuh"
+#include "zone_o3.cuh"
+
+namespace ader {
+
+template <> struct ZoneOps<3> {
+    template <class R> static ADER_DEV void predict_modal(Vec<5, R>* m, R gm1, R cx, R cy, R cz, int n) {
+        o3::predict_modal(m, gm1, cx, cy, cz, n);
+    }
+    template <class R> static ADER_DEV void predict_nodal(Vec<5, R>* m, R gm1, R cx, R cy, R cz, int n) {
+        o3::predict_nodal(m, gm1, cx, cy, cz, n);
+    }
+    template <int D, class R> static ADER_DEV void face(const Vec<5, R>* p, R gm1, Vec<5, R>& ub, Vec<5, R>& avg, Vec<5, R>& Fa) {
+        o3::face<D>(p, gm1, ub, avg, Fa);
+    }
+};
+
+template int launch_predict_faces_order<3, double>(const StepArgs&, const double*, cudaStream_t);
+template int launch_predict_faces_order<3, float>(const StepArgs&, const double*, cudaStream_t);
+
+}  // namespace ader

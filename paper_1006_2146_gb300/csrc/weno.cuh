@@ -1,0 +1,166 @@
+// WENO building blocks of the zone-centred reconstruction (see recon.cu for the reading).
+#pragma once
+#include "common.cuh"
+
+namespace ader {
+
+constexpr double WENO_EPS = 1.0e-12;
+
+template <class R>
+ADER_DEV R wsq(R is) {
+    const R t = R(WENO_EPS) + is;
+    return t * t;
+}
+
+// order-3 1-D WENO on the five values a[-2..2] (a[2] = centre); returns b, c
+template <class R>
+ADER_DEV void weno3(const R* a, R& b, R& c) {
+    const R um2 = a[0], um1 = a[1], u0 = a[2], up1 = a[3], up2 = a[4];
+    const R bL = R(0.5) * (um2 - R(4) * um1 + R(3) * u0), cL = R(0.5) * (um2 - R(2) * um1 + u0);
+    const R bC = R(0.5) * (up1 - um1), cC = R(0.5) * (up1 - R(2) * u0 + um1);
+    const R bR = R(0.5) * (R(-3) * u0 + R(4) * up1 - up2), cR = R(0.5) * (u0 - R(2) * up1 + up2);
+    const R k13 = R(13.0 / 3.0);
+    const R aL = R(1.0 / 12.0) / wsq(bL * bL + k13 * cL * cL);
+    const R aC = R(10.0 / 12.0) / wsq(bC * bC + k13 * cC * cC);
+    const R aR = R(1.0 / 12.0) / wsq(bR * bR + k13 * cR * cR);
+    const R inv = rcp(aL + aC + aR);
+    b = (aL * bL + aC * bC + aR * bR) * inv;
+    c = (aL * cL + aC * cC + aR * cR) * inv;
+}
+
+// order-4 1-D WENO on the seven values a[-3..3] (a[3] = centre); returns b, c, d
+template <class R>
+ADER_DEV void weno4(const R* a, R& b, R& c, R& d) {
+    const R um3 = a[0], um2 = a[1], um1 = a[2], u0 = a[3], up1 = a[4], up2 = a[5], up3 = a[6];
+    R cb[4], cc[4], cd[4];
+    // stencil {i-3..i}
+    cb[0] = (R(109) * u0 - R(177) * um1 + R(87) * um2 - R(19) * um3) * R(1.0 / 60.0);
+    cc[0] = (R(2) * u0 - R(5) * um1 + R(4) * um2 - um3) * R(0.5);
+    cd[0] = (u0 - R(3) * um1 + R(3) * um2 - um3) * R(1.0 / 6.0);
+    // stencil {i-2..i+1}
+    cb[1] = (R(33) * u0 - R(63) * um1 + R(11) * um2 + R(19) * up1) * R(1.0 / 60.0);
+    cc[1] = (um1 + up1 - R(2) * u0) * R(0.5);
+    cd[1] = (R(3) * um1 - R(3) * u0 - um2 + up1) * R(1.0 / 6.0);
+    // stencil {i-1..i+2}
+    cb[2] = (R(63) * up1 - R(33) * u0 - R(19) * um1 - R(11) * up2) * R(1.0 / 60.0);
+    cc[2] = (um1 + up1 - R(2) * u0) * R(0.5);
+    cd[2] = (R(3) * u0 - um1 - R(3) * up1 + up2) * R(1.0 / 6.0);
+    // stencil {i..i+3}
+    cb[3] = (R(177) * up1 - R(109) * u0 - R(87) * up2 + R(19) * up3) * R(1.0 / 60.0);
+    cc[3] = (R(2) * u0 - R(5) * up1 + R(4) * up2 - up3) * R(0.5);
+    cd[3] = (R(3) * up1 - u0 - R(3) * up2 + up3) * R(1.0 / 6.0);
+    const R g[4] = {R(1.0 / 22.0), R(10.0 / 22.0), R(10.0 / 22.0), R(1.0 / 22.0)};
+    R al[4], s = R(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const R t = cb[q] + R(0.1) * cd[q];
+        const R is = t * t + R(13.0 / 3.0) * cc[q] * cc[q] + R(781.0 / 20.0) * cd[q] * cd[q];
+        al[q] = g[q] / wsq(is);
+        s += al[q];
+    }
+    const R inv = rcp(s);
+    b = (al[0] * cb[0] + al[1] * cb[1] + al[2] * cb[2] + al[3] * cb[3]) * inv;
+    c = (al[0] * cc[0] + al[1] * cc[1] + al[2] * cc[2] + al[3] * cc[3]) * inv;
+    d = (al[0] * cd[0] + al[1] * cd[1] + al[2] * cd[2] + al[3] * cd[3]) * inv;
+}
+
+template <class R>
+ADER_DEV R slope(const R* a) {
+    R b, c;
+    weno3(a, b, c);
+    return b;
+}
+
+
+ADER_DEV void zone_ijk(const Grid& g, long long z, int& i, int& j, int& k) {
+    i = (int)(z % g.nx);
+    long long t = z / g.nx;
+    j = (int)(t % g.ny);
+    k = (int)(t / g.ny);
+}
+
+// slope along direction d of the field F at zone (i, j, k)
+template <class R>
+ADER_DEV R slope_of(const Grid& g, const R* __restrict__ F, int i, int j, int k, int d) {
+    R a[5];
+#pragma unroll
+    for (int o = -2; o <= 2; ++o) a[o + 2] = F[nbr(g, i, j, k, d == 0 ? o : 0, d == 1 ? o : 0, d == 2 ? o : 0)];
+    return slope(a);
+}
+
+
+// ---------------------------------------------------------------- per-zone bodies of the kernels
+// 1-D moments of every variable of zone z (S1 layout in recon.cu)
+template <int ORDER, class R>
+ADER_DEV void zone_weno1d(const Grid& g, const double* __restrict__ U, R* __restrict__ S1, long long z) {
+    int i, j, k;
+    zone_ijk(g, z, i, j, k);
+    constexpr int RAD = ORDER == 4 ? 3 : 2;
+    constexpr int NV = 5;
+    for (int v = 0; v < NV; ++v) {
+        const double* Uv = U + (long long)v * g.n;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            R a[2 * RAD + 1];
+#pragma unroll
+            for (int o = -RAD; o <= RAD; ++o)
+                a[o + RAD] = R(Uv[nbr(g, i, j, k, d == 0 ? o : 0, d == 1 ? o : 0, d == 2 ? o : 0)]);
+            if (ORDER == 4) {
+                R b, c, e;
+                weno4(a, b, c, e);
+                S1[((0 * 3 + d) * NV + v) * g.n + z] = b;
+                S1[((1 * 3 + d) * NV + v) * g.n + z] = c;
+                S1[((2 * 3 + d) * NV + v) * g.n + z] = e;
+            } else {
+                R b, c;
+                weno3(a, b, c);
+                S1[((0 * 3 + d) * NV + v) * g.n + z] = b;
+                if (ORDER == 3) S1[((1 * 3 + d) * NV + v) * g.n + z] = c;
+            }
+        }
+    }
+}
+
+// first-level cross moments w8 w9 w10 (w14..w19 at order 4) of zone z
+template <int ORDER, class R>
+ADER_DEV void zone_cross1(const Grid& g, const R* __restrict__ S1, R* __restrict__ S2, long long z) {
+    int i, j, k;
+    zone_ijk(g, z, i, j, k);
+    constexpr int NV = 5;
+    for (int v = 0; v < NV; ++v) {
+        const R* w2 = S1 + ((0 * 3 + 0) * NV + v) * g.n;
+        const R* w3 = S1 + ((0 * 3 + 1) * NV + v) * g.n;
+        const R* w4 = S1 + ((0 * 3 + 2) * NV + v) * g.n;
+        S2[(0 * NV + v) * g.n + z] = R(0.5) * (slope_of(g, w2, i, j, k, 1) + slope_of(g, w3, i, j, k, 0));
+        S2[(1 * NV + v) * g.n + z] = R(0.5) * (slope_of(g, w3, i, j, k, 2) + slope_of(g, w4, i, j, k, 1));
+        S2[(2 * NV + v) * g.n + z] = R(0.5) * (slope_of(g, w2, i, j, k, 2) + slope_of(g, w4, i, j, k, 0));
+        if (ORDER == 4) {
+            const R* w5 = S1 + ((1 * 3 + 0) * NV + v) * g.n;
+            const R* w6 = S1 + ((1 * 3 + 1) * NV + v) * g.n;
+            const R* w7 = S1 + ((1 * 3 + 2) * NV + v) * g.n;
+            S2[(3 * NV + v) * g.n + z] = slope_of(g, w5, i, j, k, 1);   // w14
+            S2[(4 * NV + v) * g.n + z] = slope_of(g, w5, i, j, k, 2);   // w15
+            S2[(5 * NV + v) * g.n + z] = slope_of(g, w6, i, j, k, 0);   // w16
+            S2[(6 * NV + v) * g.n + z] = slope_of(g, w6, i, j, k, 2);   // w17
+            S2[(7 * NV + v) * g.n + z] = slope_of(g, w7, i, j, k, 0);   // w18
+            S2[(8 * NV + v) * g.n + z] = slope_of(g, w7, i, j, k, 1);   // w19
+        }
+    }
+}
+
+// w20 of zone z from the first-level cross moments of its neighbours
+template <class R>
+ADER_DEV void zone_cross2(const Grid& g, R* __restrict__ S2, long long z) {
+    int i, j, k;
+    zone_ijk(g, z, i, j, k);
+    constexpr int NV = 5;
+    for (int v = 0; v < NV; ++v) {
+        const R* w8 = S2 + (0 * NV + v) * g.n;
+        const R* w9 = S2 + (1 * NV + v) * g.n;
+        const R* w10 = S2 + (2 * NV + v) * g.n;
+        S2[(9 * NV + v) * g.n + z] = (slope_of(g, w8, i, j, k, 2) + slope_of(g, w9, i, j, k, 0) +
+                                      slope_of(g, w10, i, j, k, 1)) * R(1.0 / 3.0);
+    }
+}
+
+}  // namespace ader
