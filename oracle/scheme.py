@@ -69,10 +69,12 @@ def ader_step(U, dx, dt, order, form="nodal", solver="hll", gamma=1.4, Bface=Non
 
 
 def max_dt(U, dx, cfl, gamma=1.4, Bface=None):
-    """dt = cfl / max over zones of sum_d (|v_d| + c_d)/dx_d (reading of the CFL rule, Secs. II.d, VI)."""
+    """dt = cfl / max over zones of sum_d (|v_d| + c_d)/dx_d (reading of the CFL rule, Secs. II.d, VI).
+
+    For MHD c_d is the fast speed of the zone state whose field is the mean of
+    the two face values (Sec. III, opening).
+    """
     if Bface is not None:
-        Uz, _ = zone_state(U, Bface, 2)
-        Uz = Uz[:, ...]
         zb = [weno.face_b_moments(Bface[d], d, 2)[0] for d in range(3)]
         Uz = np.concatenate([U, np.stack(zb)], axis=0)
     else:
@@ -84,8 +86,60 @@ def max_dt(U, dx, cfl, gamma=1.4, Bface=None):
 
 
 # ----------------------------------------------------------------------------- constrained transport
+def edge_fluxes(edge_data, Uz, order, gamma, solver):
+    """Numerical flux of each face evaluated with the face's edge averages (Sec. II.3, Eq. 57).
+
+    The frozen wave speeds (or eigen-structure) are the face's own (barycentre
+    states, Eq. 54); the averaged states and fluxes are the edge averages of
+    Eq. 57 and of the facial flux polynomial (Eqs. D.5, D.10, D.15).  Returns
+    Fe[d][(e, se)]: flux of the face i+1/2 of direction d at its edge on side se
+    of direction e, stored at the face's lower zone.
+    """
+    solve = riemann.SOLVERS[solver]
+    Fe = []
+    for d in range(3):
+        up, um = edge_data[d]
+        ubR = weno.shift(um[0], d, 1)
+        zR = weno.shift(Uz, d, 1)
+        out = {}
+        for key, (uL, FL) in up[3].items():
+            uR, FR = um[3][key]
+            out[key] = solve(d, gamma, up[0], ubR, uL, weno.shift(uR, d, 1), FL, weno.shift(FR, d, 1), Uz, zR)
+        Fe.append(out)
+    return Fe
+
+
+def edge_emfs(Fe):
+    """Edge-averaged electric fields as the mean of the four adjacent faces' edge fluxes (Sec. II.3, Eq. 7).
+
+    Ez on the z-edge (i+1/2, j+1/2), Ey on the y-edge (i+1/2, k+1/2) and Ex on the
+    x-edge (j+1/2, k+1/2), each stored at zone (k, j, i).  Eq. 7 identifies
+    Ez = -F7 = G6, Ey = F8 = -H6, Ex = -G8 = H7 (0-based components 6, 7, 5 ...).
+    """
+    sh = weno.shift
+    Ez = 0.25 * (-Fe[0][1, +1][6] - sh(Fe[0][1, -1][6], 1, 1) + Fe[1][0, +1][5] + sh(Fe[1][0, -1][5], 0, 1))
+    Ey = 0.25 * (Fe[0][2, +1][7] + sh(Fe[0][2, -1][7], 2, 1) - Fe[2][0, +1][5] - sh(Fe[2][0, -1][5], 0, 1))
+    Ex = 0.25 * (-Fe[1][2, +1][7] - sh(Fe[1][2, -1][7], 2, 1) + Fe[2][1, +1][6] + sh(Fe[2][1, -1][6], 1, 1))
+    return Ex, Ey, Ez
+
+
 def ct_update(Bface, F, edge_data, Uz, order, gamma, solver, dt, dx):
-    raise NotImplementedError("MHD constrained transport")
+    """Face-averaged B at t^{n+1} by the discrete Stokes theorem of Eq. 8."""
+    Ex, Ey, Ez = edge_emfs(edge_fluxes(edge_data, Uz, order, gamma, solver))
+    sh = weno.shift
+    # Bface[d][..., i_d] is the face i_d - 1/2: its edges are stored one zone lower along d
+    Ez_x, Ey_x = sh(Ez, 0, -1), sh(Ey, 0, -1)
+    Ex_y, Ez_y = sh(Ex, 1, -1), sh(Ez, 1, -1)
+    Ey_z, Ex_z = sh(Ey, 2, -1), sh(Ex, 2, -1)
+    Bx = Bface[0] - dt * ((Ez_x - sh(Ez_x, 1, -1)) / dx[1] - (Ey_x - sh(Ey_x, 2, -1)) / dx[2])
+    By = Bface[1] - dt * ((Ex_y - sh(Ex_y, 2, -1)) / dx[2] - (Ez_y - sh(Ez_y, 0, -1)) / dx[0])
+    Bz = Bface[2] - dt * ((Ey_z - sh(Ey_z, 0, -1)) / dx[0] - (Ex_z - sh(Ex_z, 1, -1)) / dx[1])
+    return np.stack([Bx, By, Bz])
+
+
+def div_b(Bface, dx):
+    """Discrete divergence of the face field in every zone (what Eq. 8 preserves)."""
+    return sum((weno.shift(Bface[d], d, 1) - Bface[d]) / dx[d] for d in range(3))
 
 
 # ----------------------------------------------------------------------------- SSP-RK, Sec. II.d

@@ -179,22 +179,13 @@ def alfven_wave(n, t=0.0, B0=1.0, amp=0.1, rho0=1.0, P0=1.0, gamma=5.0 / 3.0, np
         ph = phase(x, y, z)
         return B0 * nvec[c] + amp * B0 * (np.cos(ph) * e1[c] + np.sin(ph) * e2[c])
 
-    # vector potential: uniform part B0 n = curl(A0) with A0 = (B0/2) n x r, plus
-    # the wave part: curl of (amp B0/k)(cos phi e1 + sin phi e2) equals amp B0 (cos e1 + sin e2)
-    # because n x e1 = e2 and n x e2 = -e1 (k = |k| n).
-    def Acomp(c):
-        def A(x, y, z):
-            r = [x, y, z]
-            nxr = [nvec[1] * r[2] - nvec[2] * r[1], nvec[2] * r[0] - nvec[0] * r[2], nvec[0] * r[1] - nvec[1] * r[0]]
-            ph = phase(x, y, z)
-            wave = (amp * B0 / kmag) * (np.cos(ph) * e1[c] + np.sin(ph) * e2[c])
-            return 0.5 * B0 * nxr[c] + wave
-        return A
-    Bface = face_field_from_potential([Acomp(0), Acomp(1), Acomp(2)], n, npts=6)
-    # the uniform part's potential is not periodic; its face averages are exact
-    # (linear A), so replace them by the exact uniform values to restore periodicity
-    Bface = _periodic_fix(Bface, n, [B0 * nvec[c] for c in range(3)],
-                          [lambda x, y, z, c=c: (amp * B0 / kmag) * (np.cos(phase(x, y, z)) * e1[c] + np.sin(phase(x, y, z)) * e2[c]) for c in range(3)])
+    # The wave part of B is curl(A_w) with A_w = -(amp B0 / |k|)(cos phi e1 + sin phi e2): since
+    # curl A_w = |k| n x dA_w/dphi and n x e1 = e2, n x e2 = -e1, this is amp B0 (cos phi e1 + sin phi e2).
+    # A_w is periodic; the uniform part B0 n is added to the face averages exactly.
+    wave_A = [lambda x, y, z, c=c: -(amp * B0 / kmag) * (np.cos(phase(x, y, z)) * e1[c] + np.sin(phase(x, y, z)) * e2[c])
+              for c in range(3)]
+    Bw = face_field_from_potential(wave_A, n, npts=6)
+    Bface = np.stack([Bw[c] + B0 * nvec[c] for c in range(3)])
     rho = rho0 * np.ones((n, n, n))
     vz = [cell_average(lambda x, y, z, c=c: -(Bvec(x, y, z, c) - B0 * nvec[c]) / np.sqrt(FOUR_PI * rho0), n, npts)
           for c in range(3)]
@@ -206,18 +197,12 @@ def alfven_wave(n, t=0.0, B0=1.0, amp=0.1, rho0=1.0, P0=1.0, gamma=5.0 / 3.0, np
     return U, Bface
 
 
-def _periodic_fix(Bface, n, uniform, wave_A):
-    """Face field = uniform part + curl of the (periodic) wave potential."""
-    Bw = face_field_from_potential(wave_A, n, npts=6)
-    return np.stack([Bw[c] + uniform[c] for c in range(3)])
-
-
 def orszag_tang(n, gamma=5.0 / 3.0, rho0=25.0 / (36.0 * np.pi), P0=5.0 / (12.0 * np.pi), B0=None):
-    """Orszag-Tang-type vortex extruded in z (standard 2-D fields; Gaussian units).
+    """Orszag-Tang-type vortex, uniform in z (the standard 2-D fields; Gaussian units).
 
-    v = (-sin 2 pi y, sin 2 pi x, 0), B = B0 (-sin 2 pi y, sin 4 pi x, 0) from
-    A_z = B0 (cos 4 pi x / (4 pi) + cos 2 pi y / (2 pi)), B0 = sqrt(4 pi) / sqrt(4 pi) ... chosen
-    as 1/sqrt(4 pi) * sqrt(4 pi) = 1 in Heaviside units, i.e. sqrt(4 pi) * (1/sqrt(4 pi)) here.
+    v = (-sin 2 pi y, sin 2 pi x, 0) and B = B0 (-sin 2 pi y, sin 4 pi x, 0) = curl(A_z z) with
+    A_z = B0 (cos 4 pi x / (4 pi) + cos 2 pi y / (2 pi)); B0 = 1 here is the usual Heaviside
+    amplitude 1/sqrt(4 pi) converted to Gaussian units.  rho and P are uniform.
     """
     if B0 is None:
         B0 = 1.0          # equals the Heaviside-unit amplitude 1/sqrt(4 pi) times sqrt(4 pi)
