@@ -47,7 +47,7 @@ enum { ADER_HLL = 0, ADER_LINEARIZED = 1 };
 
 /* Option flags for ader_create. */
 enum {
-    ADER_MHD = 1u << 0,                 /* ideal MHD with face-centred B (reserved; not yet built) */
+    ADER_MHD = 1u << 0,                 /* ideal MHD with face-centred B and constrained transport (HLL only) */
     ADER_NODAL = 1u << 1,               /* nodal predictor (Apps. A-C); default modal (Sec. IV) */
     ADER_FP32_BULK = 1u << 2,           /* FP32 reconstruction/predictor/fluxes, FP64 update and reductions */
     ADER_CONVERGED_PREDICTOR = 1u << 4  /* iterate the predictor to tolerance instead of M-1 times */
@@ -75,7 +75,12 @@ typedef struct ader_ctx ader_ctx;
 int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigned flags, ader_ctx** out);
 
 /* One ADER-WENO step of size dt (host value), in place on U (Eq. 6).
- * Bface must be NULL (Euler). */
+ * Euler: Bface must be NULL.  MHD (ADER_MHD): Bface[d][k][j][i] (3 x nz x ny x nx,
+ * FP64) is the face-averaged normal field B_d on the face i_d - 1/2 of zone
+ * (i, j, k) along d; the zone field is rebuilt from it every step (Sec. III,
+ * face-B WENO) and it is advanced in place by constrained transport with
+ * edge-averaged electric fields (Eqs. 7-8), which keeps its discrete
+ * divergence unchanged to round-off.  U's energy includes B^2/8pi. */
 int ader_step(ader_ctx* ctx, double* U, double* Bface, double dt, void* stream);
 
 /* Same as ader_step with dt read on the device from dt_dev (one double), so
@@ -84,18 +89,21 @@ int ader_step_devdt(ader_ctx* ctx, double* U, double* Bface, const double* dt_de
 
 /* CFL time step (reading of the paper's CFL rule, Secs. II.d and VI):
  *   dt = cfl / max over zones of sum_d (|v_d| + c_d) / dx_d,
- * c_d the sound speed.  Written to dt_dev (one double, device).  Reduction
+ * c_d the sound speed (MHD: the fast speed with the zone field taken as the
+ * mean of its two face values; Bface as for ader_step).  Written to dt_dev (one double, device).  Reduction
  * in FP64 with warp shuffles. */
 int ader_max_dt(ader_ctx* ctx, const double* U, const double* Bface, double cfl, double* dt_dev, void* stream);
 
 /* One SSP-RK step of the context's order (Eq. 18 for order 2, Eq. 19 for
  * order 3, Eq. 20 for order 4) with the same reconstruction and Riemann
- * solver and the App. D facial quadrature with every time mode zero. */
+ * solver and the App. D facial quadrature with every time mode zero.
+ * Euler contexts only. */
 int ader_rk_step(ader_ctx* ctx, double* U, double* Bface, double dt, void* stream);
 
 /* End-to-end step through host memory: copies U_host to the device, runs
  * ader_max_dt (cfl) then ader_step, copies U back and returns the dt used in
- * *dt_used_host.  Synchronous.  U_host should be pinned for full speed. */
+ * *dt_used_host.  Synchronous.  U_host should be pinned for full speed.
+ * Euler contexts only. */
 int ader_step_host(ader_ctx* ctx, double* U_host, double* Bface_host, double cfl, double* dt_used_host);
 
 /* Totals of the five conserved variables (FP64 reduction), written to

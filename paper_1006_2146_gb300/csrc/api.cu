@@ -22,6 +22,9 @@ struct ader_ctx {
     void* S1 = nullptr;
     void* S2 = nullptr;
     void* S3 = nullptr;
+    void* ZB = nullptr;                       // MHD: zone field from the face-B WENO
+    void* E = nullptr;                        // MHD: edge EMFs
+    bool mhd = false;
     unsigned* flag = nullptr;                 // device error flag
     unsigned long long* dtscr = nullptr;      // max_dt scratch (2 words)
     double* partial = nullptr;                // totals partials
@@ -100,6 +103,10 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.S2 = c->S2;
     a.S3 = c->S3;
     a.flag = c->flag;
+    a.mhd = c->mhd ? 1 : 0;
+    a.Bface = nullptr;
+    a.ZB = c->ZB;
+    a.E = c->E;
     return a;
 }
 
@@ -111,10 +118,18 @@ static int enqueue_faces(ader_ctx* c, const StepArgs& a, const double* U, cudaSt
         n = launch_recon<R>(a, U, st);
     }
     Trace t(c, "predictor_faces", st);
-    switch (a.order) {
-        case 2: n += launch_predict_faces_order<2, R>(a, U, st); break;
-        case 3: n += launch_predict_faces_order<3, R>(a, U, st); break;
-        default: n += launch_predict_faces_order<4, R>(a, U, st); break;
+    if (a.mhd) {
+        switch (a.order) {
+            case 2: n += launch_predict_faces_nv<2, 8, R>(a, U, st); break;
+            case 3: n += launch_predict_faces_nv<3, 8, R>(a, U, st); break;
+            default: n += launch_predict_faces_nv<4, 8, R>(a, U, st); break;
+        }
+    } else {
+        switch (a.order) {
+            case 2: n += launch_predict_faces_nv<2, 5, R>(a, U, st); break;
+            case 3: n += launch_predict_faces_nv<3, 5, R>(a, U, st); break;
+            default: n += launch_predict_faces_nv<4, 5, R>(a, U, st); break;
+        }
     }
     return n;
 }
@@ -138,8 +153,9 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
         return ADER_ERR_ARG;
     if (order < 2 || order > 4 || !(gamma > 1.0) || (solver != ADER_HLL && solver != ADER_LINEARIZED))
         return ADER_ERR_ARG;
-    const unsigned known = ADER_NODAL | ADER_FP32_BULK;
-    if (flags & ~known) return ADER_ERR_ARG;        // MHD and converged predictor are not built yet
+    const unsigned known = ADER_MHD | ADER_NODAL | ADER_FP32_BULK;
+    if (flags & ~known) return ADER_ERR_ARG;        // the converged predictor is not built
+    if ((flags & ADER_MHD) && solver != ADER_HLL) return ADER_ERR_ARG;   // MHD: HLL only
     ader_ctx* c = new ader_ctx();
     c->g = *g;
     c->grid.nx = g->nx;
@@ -152,15 +168,21 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
     c->gamma = gamma;
     c->fp32 = (flags & ADER_FP32_BULK) != 0;
     c->rsize = c->fp32 ? 4 : 8;
+    c->mhd = (flags & ADER_MHD) != 0;
+    const int mh = c->mhd ? 1 : 0;
     const size_t N = (size_t)c->grid.n;
     int rc = ADER_OK;
     auto alloc = [&](void** p, size_t bytes, const char* what) {
         if (rc != ADER_OK || bytes == 0) return;
         rc = cuda_check(c, cudaMalloc(p, bytes), what);
     };
-    alloc(&c->S1, N * s1_per_zone(order) * c->rsize, "cudaMalloc S1");
-    alloc(&c->S2, N * (s2_per_zone(order) ? s2_per_zone(order) : 1) * c->rsize, "cudaMalloc S2");
-    alloc(&c->S3, N * s3_per_zone() * c->rsize, "cudaMalloc S3");
+    alloc(&c->S1, N * s1_per_zone(order, mh) * c->rsize, "cudaMalloc S1");
+    alloc(&c->S2, N * (s2_per_zone(order, mh) ? s2_per_zone(order, mh) : 1) * c->rsize, "cudaMalloc S2");
+    alloc(&c->S3, N * s3_per_zone(mh) * c->rsize, "cudaMalloc S3");
+    if (c->mhd) {
+        alloc(&c->ZB, N * 3 * c->rsize, "cudaMalloc zone B");
+        alloc(&c->E, N * 3 * c->rsize, "cudaMalloc EMF");
+    }
     alloc((void**)&c->flag, sizeof(unsigned), "cudaMalloc flag");
     alloc((void**)&c->dtscr, 2 * sizeof(unsigned long long), "cudaMalloc dt scratch");
     c->tot_blocks = 1024;
@@ -185,7 +207,7 @@ void ader_destroy(ader_ctx* c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->spare) cudaEventDestroy(e);
-    void* ptrs[] = {c->S1, c->S2, c->S3, c->flag, c->dtscr, c->partial, c->dt_dev, c->Ustage,
+    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->flag, c->dtscr, c->partial, c->dt_dev, c->Ustage,
                     c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -244,14 +266,27 @@ int ader_profile_read(ader_ctx* c, const char** names, int* launches, double* ms
     return n;
 }
 
+static int check_bface(ader_ctx* c, const double* Bface) {
+    if (c->mhd && !Bface) return fail(c, ADER_ERR_ARG, "MHD context: Bface is required");
+    if (!c->mhd && Bface) return fail(c, ADER_ERR_ARG, "Euler context: Bface must be null");
+    return ADER_OK;
+}
+
 static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const double* dt_dev, void* stream) {
     if (!c) return ADER_ERR_ARG;
     if (!U) return fail(c, ADER_ERR_ARG, "U is null");
-    if (Bface) return fail(c, ADER_ERR_ARG, "Bface must be null: MHD is not built in this library version");
+    if (int rc = check_bface(c, Bface)) return rc;
     if (!dt_dev && !(dt > 0.0)) return fail(c, ADER_ERR_ARG, "dt must be positive");
     cudaStream_t st = (cudaStream_t)stream;
-    const StepArgs a = make_args(c, dt, dt_dev, c->order - 1);
-    c->launches = enqueue_operator(c, a, U, U, U, dt_dev ? 1.0 : dt, dt_dev != nullptr, st);
+    StepArgs a = make_args(c, dt, dt_dev, c->order - 1);
+    a.Bface = Bface;
+    const double coef = dt_dev ? 1.0 : dt;
+    c->launches = enqueue_operator(c, a, U, U, U, coef, dt_dev != nullptr, st);
+    if (c->mhd) {
+        Trace t(c, "emf_ct", st);
+        c->launches += c->fp32 ? launch_emf_ct<float>(a, Bface, coef, dt_dev != nullptr, st)
+                               : launch_emf_ct<double>(a, Bface, coef, dt_dev != nullptr, st);
+    }
     return cuda_check(c, cudaGetLastError(), "ader_step launch");
 }
 
@@ -267,18 +302,18 @@ int ader_step_devdt(ader_ctx* c, double* U, double* Bface, const double* dt_dev,
 int ader_max_dt(ader_ctx* c, const double* U, const double* Bface, double cfl, double* dt_dev, void* stream) {
     if (!c) return ADER_ERR_ARG;
     if (!U || !dt_dev) return fail(c, ADER_ERR_ARG, "null pointer");
-    if (Bface) return fail(c, ADER_ERR_ARG, "Bface must be null: MHD is not built in this library version");
+    if (int rc = check_bface(c, Bface)) return rc;
     if (!(cfl > 0.0)) return fail(c, ADER_ERR_ARG, "cfl must be positive");
     const double dx[3] = {c->g.dx, c->g.dy, c->g.dz};
     Trace t(c, "max_dt", (cudaStream_t)stream);
-    launch_max_dt(c->grid, U, c->gamma, dx, cfl, dt_dev, c->dtscr, c->flag, (cudaStream_t)stream);
+    launch_max_dt(c->grid, U, Bface, c->gamma, dx, cfl, dt_dev, c->dtscr, c->flag, (cudaStream_t)stream);
     return cuda_check(c, cudaGetLastError(), "ader_max_dt launch");
 }
 
 int ader_diagnostics(ader_ctx* c, const double* U, const double* Bface, double* totals_dev, void* stream) {
     if (!c) return ADER_ERR_ARG;
     if (!U || !totals_dev) return fail(c, ADER_ERR_ARG, "null pointer");
-    if (Bface) return fail(c, ADER_ERR_ARG, "Bface must be null: MHD is not built in this library version");
+    if (int rc = check_bface(c, Bface)) return rc;
     launch_totals(c->grid, U, totals_dev, c->partial, c->tot_blocks, (cudaStream_t)stream);
     return cuda_check(c, cudaGetLastError(), "ader_diagnostics launch");
 }
@@ -302,7 +337,7 @@ static const double RK4B[5][5] = {{0.39175222700392, 0, 0, 0, 0},
 int ader_rk_step(ader_ctx* c, double* U, double* Bface, double dt, void* stream) {
     if (!c) return ADER_ERR_ARG;
     if (!U) return fail(c, ADER_ERR_ARG, "U is null");
-    if (Bface) return fail(c, ADER_ERR_ARG, "Bface must be null: MHD is not built in this library version");
+    if (Bface || c->mhd) return fail(c, ADER_ERR_ARG, "ader_rk_step is built for Euler contexts only");
     if (!(dt > 0.0)) return fail(c, ADER_ERR_ARG, "dt must be positive");
     cudaStream_t st = (cudaStream_t)stream;
     const int ns = c->order == 2 ? 2 : (c->order == 3 ? 3 : 5);
@@ -373,7 +408,7 @@ int ader_sync_status(ader_ctx* c, void* stream) {
 int ader_step_host(ader_ctx* c, double* U_host, double* Bface_host, double cfl, double* dt_used_host) {
     if (!c) return ADER_ERR_ARG;
     if (!U_host) return fail(c, ADER_ERR_ARG, "U_host is null");
-    if (Bface_host) return fail(c, ADER_ERR_ARG, "Bface must be null: MHD is not built in this library version");
+    if (Bface_host || c->mhd) return fail(c, ADER_ERR_ARG, "ader_step_host is built for Euler contexts only");
     const size_t bytes = (size_t)c->grid.n * 5 * sizeof(double);
     cudaStream_t st = 0;
     int rc = cuda_check(c, cudaMemcpyAsync(c->Ustage, U_host, bytes, cudaMemcpyHostToDevice, st), "H2D");

@@ -76,40 +76,85 @@ ADER_DEV Vec<NV, R> scale(R s, const Vec<NV, R>& a) {
 
 template <class R> ADER_DEV R rcp(R x) { return R(1) / x; }
 
-// ------------------------------------------------------------------ Euler physics, Eq. 3
-template <class R>
+// ------------------------------------------------------------------ physics, Eq. 3 (Gaussian units)
+// NV = 5: Euler (rho, rho v, eps).  NV = 8: ideal MHD (rho, rho v, eps, B) with
+// eps = rho v^2/2 + P/(gamma-1) + B^2/(8 pi).
+constexpr double INV_FOUR_PI = 0.079577471545947667884;   // 1 / (4 pi)
+
+template <int NV, class R>
 struct Prim {
-    R irho, vx, vy, vz, p;
+    R irho, vx, vy, vz, p;        // p: gas pressure
+    R ptot, vB;                    // MHD: P + B^2/8pi and v.B (unused for Euler)
 };
 
-template <class R>
-ADER_DEV Prim<R> primitives(const Vec<5, R>& u, R gm1) {
-    Prim<R> q;
+template <int NV, class R>
+ADER_DEV Prim<NV, R> primitives(const Vec<NV, R>& u, R gm1) {
+    Prim<NV, R> q;
     q.irho = rcp(u[0]);
     q.vx = u[1] * q.irho;
     q.vy = u[2] * q.irho;
     q.vz = u[3] * q.irho;
-    q.p = gm1 * (u[4] - R(0.5) * (u[1] * q.vx + u[2] * q.vy + u[3] * q.vz));
+    const R ke = R(0.5) * (u[1] * q.vx + u[2] * q.vy + u[3] * q.vz);
+    if constexpr (NV == 8) {
+        const R pm = R(0.5 * INV_FOUR_PI) * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
+        q.p = gm1 * (u[4] - ke - pm);
+        q.ptot = q.p + pm;
+        q.vB = q.vx * u[5] + q.vy * u[6] + q.vz * u[7];
+    } else {
+        q.p = gm1 * (u[4] - ke);
+        q.ptot = q.p;
+        q.vB = R(0);
+    }
     return q;
 }
 
-// physical flux in direction D (0: F, 1: G, 2: H)
-template <int D, class R>
-ADER_DEV Vec<5, R> flux_from(const Vec<5, R>& u, const Prim<R>& q) {
+// physical flux in direction D (0: F, 1: G, 2: H) of Eq. 3
+template <int D, int NV, class R>
+ADER_DEV Vec<NV, R> flux_from(const Vec<NV, R>& u, const Prim<NV, R>& q) {
     const R vn = D == 0 ? q.vx : (D == 1 ? q.vy : q.vz);
-    Vec<5, R> f;
+    Vec<NV, R> f;
     f[0] = u[1 + D];
-    f[1] = u[1] * vn;
-    f[2] = u[2] * vn;
-    f[3] = u[3] * vn;
-    f[1 + D] += q.p;
-    f[4] = (u[4] + q.p) * vn;
+    if constexpr (NV == 8) {
+        const R bn = R(INV_FOUR_PI) * u[5 + D];
+        f[1] = u[1] * vn - bn * u[5];
+        f[2] = u[2] * vn - bn * u[6];
+        f[3] = u[3] * vn - bn * u[7];
+        f[1 + D] += q.ptot;
+        f[4] = (u[4] + q.ptot) * vn - bn * q.vB;
+        const R Bn = u[5 + D];
+        f[5] = vn * u[5] - q.vx * Bn;
+        f[6] = vn * u[6] - q.vy * Bn;
+        f[7] = vn * u[7] - q.vz * Bn;
+        f[5 + D] = R(0);
+    } else {
+        f[1] = u[1] * vn;
+        f[2] = u[2] * vn;
+        f[3] = u[3] * vn;
+        f[1 + D] += q.p;
+        f[4] = (u[4] + q.p) * vn;
+    }
     return f;
 }
 
-template <int D, class R>
-ADER_DEV Vec<5, R> flux(const Vec<5, R>& u, R gm1) {
+template <int D, int NV, class R>
+ADER_DEV Vec<NV, R> flux(const Vec<NV, R>& u, R gm1) {
     return flux_from<D>(u, primitives(u, gm1));
+}
+
+// fast magnetosonic speed in direction D (the sound speed for Euler)
+template <int D, int NV, class R>
+ADER_DEV R fast_speed(const Vec<NV, R>& u, const Prim<NV, R>& q, R gamma) {
+    const R a2 = gamma * q.p * q.irho;
+    if constexpr (NV == 8) {
+        const R f = R(INV_FOUR_PI) * q.irho;
+        const R b2 = f * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]);
+        const R bn2 = f * u[5 + D] * u[5 + D];
+        const R s = a2 + b2;
+        const R disc = sqrt(fmax(s * s - R(4) * a2 * bn2, R(0)));
+        return sqrt(R(0.5) * (s + disc));
+    } else {
+        return sqrt(a2);
+    }
 }
 
 // ------------------------------------------------------------------ indexing

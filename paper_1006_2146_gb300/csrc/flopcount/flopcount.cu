@@ -37,9 +37,7 @@ inline Cnt fmax(Cnt a, Cnt b) { ++g_cmp; return Cnt(std::fmax(a.v, b.v)); }
 inline Cnt fabs(Cnt a) { ++g_cmp; return Cnt(std::fabs(a.v)); }
 
 #include "../weno.cuh"
-#include "../step_o2.cu"
-#include "../step_o3.cu"
-#include "../step_o4.cu"
+#include "../step_inst.cuh"
 
 using namespace ader;
 
@@ -76,25 +74,25 @@ int main() {
         a.flag = &flag;
         reset();
         for (long long z = 0; z < N; ++z) {
-            if (order == 2) zone_weno1d<2, Cnt>(g, U.data(), S1.data(), z);
-            if (order == 3) zone_weno1d<3, Cnt>(g, U.data(), S1.data(), z);
-            if (order == 4) zone_weno1d<4, Cnt>(g, U.data(), S1.data(), z);
+            if (order == 2) zone_weno1d<2, 5, Cnt>(g, U.data(), nullptr, S1.data(), z);
+            if (order == 3) zone_weno1d<3, 5, Cnt>(g, U.data(), nullptr, S1.data(), z);
+            if (order == 4) zone_weno1d<4, 5, Cnt>(g, U.data(), nullptr, S1.data(), z);
         }
         if (order >= 3)
             for (long long z = 0; z < N; ++z) {
-                if (order == 3) zone_cross1<3, Cnt>(g, S1.data(), S2.data(), z);
-                else zone_cross1<4, Cnt>(g, S1.data(), S2.data(), z);
+                if (order == 3) zone_cross1<3, 5, Cnt>(g, S1.data(), S2.data(), z);
+                else zone_cross1<4, 5, Cnt>(g, S1.data(), S2.data(), z);
             }
         if (order == 4)
-            for (long long z = 0; z < N; ++z) zone_cross2<Cnt>(g, S2.data(), z);
+            for (long long z = 0; z < N; ++z) zone_cross2<5, Cnt>(g, S2.data(), z);
         const double recon = (double)flops() / N;
         std::printf("  \"order%d\": {\"weno_reconstruction\": %.1f", order, recon);
         for (int form = 0; form < 2; ++form) {
             reset();
             for (long long z = 0; z < N; ++z) {
-                if (order == 2) form ? zone_predict_faces<2, 1, Cnt>(a, U.data(), z) : zone_predict_faces<2, 0, Cnt>(a, U.data(), z);
-                if (order == 3) form ? zone_predict_faces<3, 1, Cnt>(a, U.data(), z) : zone_predict_faces<3, 0, Cnt>(a, U.data(), z);
-                if (order == 4) form ? zone_predict_faces<4, 1, Cnt>(a, U.data(), z) : zone_predict_faces<4, 0, Cnt>(a, U.data(), z);
+                if (order == 2) form ? zone_predict_faces<2, 1, 5, Cnt>(a, U.data(), z) : zone_predict_faces<2, 0, 5, Cnt>(a, U.data(), z);
+                if (order == 3) form ? zone_predict_faces<3, 1, 5, Cnt>(a, U.data(), z) : zone_predict_faces<3, 0, 5, Cnt>(a, U.data(), z);
+                if (order == 4) form ? zone_predict_faces<4, 1, 5, Cnt>(a, U.data(), z) : zone_predict_faces<4, 0, 5, Cnt>(a, U.data(), z);
             }
             std::printf(", \"predictor_faces_%s\": %.1f", form ? "nodal" : "modal", (double)flops() / N);
         }
@@ -102,17 +100,17 @@ int main() {
         a.n_iter = 0;
         reset();
         for (long long z = 0; z < N; ++z) {
-            if (order == 2) zone_predict_faces<2, 0, Cnt>(a, U.data(), z);
-            if (order == 3) zone_predict_faces<3, 0, Cnt>(a, U.data(), z);
-            if (order == 4) zone_predict_faces<4, 0, Cnt>(a, U.data(), z);
+            if (order == 2) zone_predict_faces<2, 0, 5, Cnt>(a, U.data(), z);
+            if (order == 3) zone_predict_faces<3, 0, 5, Cnt>(a, U.data(), z);
+            if (order == 4) zone_predict_faces<4, 0, 5, Cnt>(a, U.data(), z);
         }
         std::printf(", \"faces_spatial_only\": %.1f", (double)flops() / N);
         std::vector<double> out(5 * N);
         for (int sol = 0; sol < 2; ++sol) {
             reset();
             for (long long z = 0; z < N; ++z) {
-                if (sol == 0) zone_flux_update<0, Cnt>(a, out.data(), U.data(), 0.01, 0, z);
-                else zone_flux_update<1, Cnt>(a, out.data(), U.data(), 0.01, 0, z);
+                if (sol == 0) zone_flux_update<0, 5, Cnt>(a, out.data(), U.data(), 0.01, 0, z);
+                else zone_flux_update<1, 5, Cnt>(a, out.data(), U.data(), 0.01, 0, z);
             }
             // FP64 accumulation: per direction and variable one subtract, one multiply, one subtract; then base + c*acc
             const double acc = 3 * 5 * 3 + 5 * 2;

@@ -134,24 +134,24 @@ def emit():
         "namespace o4 {",
         "",
         "// qt[k-21] = u[base(k)] + tau = 0 flux terms; f, g, h indexed by node 1..20",
-        "template <class R>",
-        "ADER_DEV void nodal_o4_qterms(const Vec<5, R>* u, const Vec<5, R>* f, const Vec<5, R>* g,",
-        "                              const Vec<5, R>* h, Vec<5, R>* qt) {",
+        "template <int NV, class R>",
+        "ADER_DEV void nodal_o4_qterms(const Vec<NV, R>* u, const Vec<NV, R>* f, const Vec<NV, R>* g,",
+        "                              const Vec<NV, R>* h, Vec<NV, R>* qt) {",
     ]
     for k in range(21, 36):
         t = _terms(C, k, 1, 20, None, 0)
         lines.append("    qt[%d] = u[%d]%s;" % (k - 21, base_node(k), "".join("\n        + " + s for s in t)))
     lines += ["}", "",
               "// e[k-21] = value at node k before the first iteration (no time evolution)",
-              "template <class R>",
-              "ADER_DEV void nodal_o4_initial(const Vec<5, R>* u, Vec<5, R>* e) {"]
+              "template <int NV, class R>",
+              "ADER_DEV void nodal_o4_initial(const Vec<NV, R>* u, Vec<NV, R>* e) {"]
     for k in range(21, 36):
         lines.append("    e[%d] = u[%d];" % (k - 21, base_node(k)))
     lines += ["}", "",
               "// one Picard step: e[k-21] = qt[k-21] + tau > 0 flux terms; f, g, h indexed by node - 21",
-              "template <class R>",
-              "ADER_DEV void nodal_o4_update(const Vec<5, R>* qt, const Vec<5, R>* f, const Vec<5, R>* g,",
-              "                              const Vec<5, R>* h, Vec<5, R>* e) {"]
+              "template <int NV, class R>",
+              "ADER_DEV void nodal_o4_update(const Vec<NV, R>* qt, const Vec<NV, R>* f, const Vec<NV, R>* g,",
+              "                              const Vec<NV, R>* h, Vec<NV, R>* e) {"]
     for k in range(21, 36):
         t = _terms(C, k, 21, 35, None, 21)
         assert all("[14]" not in s for s in t), "node 35 flux must not enter the update"

@@ -25,15 +25,22 @@ struct StepArgs {
     void* S2;           // cross moments             (R)
     void* S3;           // face-side data             (R)
     unsigned* flag;     // device error flag
+    int mhd;            // 1: ideal MHD (8 variables, face-centred B)
+    const double* Bface; // MHD: face field B_d on faces i_d - 1/2 (3 x N), read
+    void* ZB;           // MHD: zone-averaged B from the face-B WENO (3 x N, R)
+    void* E;            // MHD: edge EMFs Ex, Ey, Ez (3 x N, R)
 };
 
 // Number of R values per zone in each scratch array.
-inline int s1_per_zone(int order) { return 5 * 3 * (order - 1); }
-inline int s2_per_zone(int order) { return order == 2 ? 0 : (order == 3 ? 15 : 50); }
-inline int s3_per_zone() { return 6 * 3 * 5; }
+inline int nvar(int mhd) { return mhd ? 8 : 5; }
+inline int s1_per_zone(int order, int mhd) { return nvar(mhd) * 3 * (order - 1); }
+inline int s2_per_zone(int order, int mhd) { return order == 2 ? 0 : nvar(mhd) * (order == 3 ? 3 : 10); }
+// face-side values per side: u_b, <u>, <F> (NV each) and, for MHD, 4 edges x (<u_c>, <F_c>)
+ADER_DEV constexpr int side_values(int nv) { return 3 * nv + (nv == 8 ? 8 : 0); }
+inline int s3_per_zone(int mhd) { return 6 * side_values(nvar(mhd)); }
 
 template <class R> int launch_recon(const StepArgs& a, const double* U, cudaStream_t st);
-template <int ORDER, class R> int launch_predict_faces_order(const StepArgs& a, const double* U, cudaStream_t st);
+template <int ORDER, int NV, class R> int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st);
 // out = base + c * L(U) with L = -sum_d (F(i+1/2) - F(i-1/2)) / dx_d from the face data in S3;
 // c = c_host, multiplied by *a.dt_dev when use_dt_dev; base may equal out (in place) or be null (out = c L).
 template <class R> int launch_flux_update(const StepArgs& a, double* out, const double* base, double c_host,
@@ -41,8 +48,10 @@ template <class R> int launch_flux_update(const StepArgs& a, double* out, const 
 // out = sum_i c[i] X[i], i < n (n <= 6)
 int launch_lincomb(double* out, int n, const double* const* X, const double* c, long long count, cudaStream_t st);
 
-int launch_max_dt(const Grid& g, const double* U, double gamma, const double dx[3], double cfl, double* dt_dev,
-                  unsigned long long* scratch, unsigned* flag, cudaStream_t st);
+int launch_max_dt(const Grid& g, const double* U, const double* Bf, double gamma, const double dx[3], double cfl,
+                  double* dt_dev, unsigned long long* scratch, unsigned* flag, cudaStream_t st);
+// MHD: edge EMFs from the face data in S3, then Eq. 8 on Bf (in place) with step c_host (x *dt_dev)
+template <class R> int launch_emf_ct(const StepArgs& a, double* Bf, double c_host, bool use_dt_dev, cudaStream_t st);
 int launch_totals(const Grid& g, const double* U, double* totals_dev, double* partial, int nblocks, cudaStream_t st);
 
 }  // namespace ader

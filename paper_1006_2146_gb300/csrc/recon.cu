@@ -28,44 +28,66 @@ namespace ader {
 
 // ---------------------------------------------------------------- kernels (one thread per zone)
 template <int ORDER, class R>
-__global__ void __launch_bounds__(128) k_weno1d(Grid g, const double* __restrict__ U, R* __restrict__ S1) {
+__global__ void __launch_bounds__(128) k_face_b(Grid g, const double* __restrict__ Bf, R* __restrict__ ZB,
+                                                R* __restrict__ S1) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (z < g.n) zone_weno1d<ORDER>(g, U, S1, z);
+    if (z < g.n) zone_face_b<ORDER, R>(g, Bf, ZB, S1, z);
 }
 
-template <int ORDER, class R>
+template <int ORDER, int NV, class R>
+__global__ void __launch_bounds__(128) k_weno1d(Grid g, const double* __restrict__ U, const R* __restrict__ ZB,
+                                                R* __restrict__ S1) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < g.n) zone_weno1d<ORDER, NV>(g, U, ZB, S1, z);
+}
+
+template <int ORDER, int NV, class R>
 __global__ void __launch_bounds__(128) k_cross1(Grid g, const R* __restrict__ S1, R* __restrict__ S2) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (z < g.n) zone_cross1<ORDER>(g, S1, S2, z);
+    if (z < g.n) zone_cross1<ORDER, NV>(g, S1, S2, z);
 }
 
-template <class R>
+template <int NV, class R>
 __global__ void __launch_bounds__(128) k_cross2(Grid g, R* __restrict__ S2) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (z < g.n) zone_cross2(g, S2, z);
+    if (z < g.n) zone_cross2<NV>(g, S2, z);
 }
 
-template <class R>
-int launch_recon(const StepArgs& a, const double* U, cudaStream_t st) {
+template <int NV, class R>
+static int launch_recon_nv(const StepArgs& a, const double* U, cudaStream_t st) {
     const int T = 128;
     const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
     R* S1 = (R*)a.S1;
     R* S2 = (R*)a.S2;
+    R* ZB = (R*)a.ZB;
     int n = 0;
+    if (NV == 8) {
+        switch (a.order) {
+            case 2: k_face_b<2, R><<<blocks, T, 0, st>>>(a.grid, a.Bface, ZB, S1); break;
+            case 3: k_face_b<3, R><<<blocks, T, 0, st>>>(a.grid, a.Bface, ZB, S1); break;
+            default: k_face_b<4, R><<<blocks, T, 0, st>>>(a.grid, a.Bface, ZB, S1); break;
+        }
+        n = 1;
+    }
     switch (a.order) {
-        case 2: k_weno1d<2, R><<<blocks, T, 0, st>>>(a.grid, U, S1); n = 1; break;
+        case 2: k_weno1d<2, NV, R><<<blocks, T, 0, st>>>(a.grid, U, ZB, S1); n += 1; break;
         case 3:
-            k_weno1d<3, R><<<blocks, T, 0, st>>>(a.grid, U, S1);
-            k_cross1<3, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
-            n = 2;
+            k_weno1d<3, NV, R><<<blocks, T, 0, st>>>(a.grid, U, ZB, S1);
+            k_cross1<3, NV, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
+            n += 2;
             break;
         default:
-            k_weno1d<4, R><<<blocks, T, 0, st>>>(a.grid, U, S1);
-            k_cross1<4, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
-            k_cross2<R><<<blocks, T, 0, st>>>(a.grid, S2);
-            n = 3;
+            k_weno1d<4, NV, R><<<blocks, T, 0, st>>>(a.grid, U, ZB, S1);
+            k_cross1<4, NV, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
+            k_cross2<NV, R><<<blocks, T, 0, st>>>(a.grid, S2);
+            n += 3;
     }
     return n;
+}
+
+template <class R>
+int launch_recon(const StepArgs& a, const double* U, cudaStream_t st) {
+    return a.mhd ? launch_recon_nv<8, R>(a, U, st) : launch_recon_nv<5, R>(a, U, st);
 }
 
 template int launch_recon<double>(const StepArgs&, const double*, cudaStream_t);

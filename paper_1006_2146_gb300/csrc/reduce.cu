@@ -10,9 +10,11 @@ namespace ader {
 // scratch[0]: running maximum as the bit pattern of a non-negative double
 // (ordered like an unsigned integer); scratch[1]: blocks finished.  The last
 // block to finish writes dt and resets both words for the next call.
-__global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict__ U, double gamma, double idx,
-                                                double idy, double idz, double cfl, double* dt_out,
-                                                unsigned long long* scratch, unsigned* flag) {
+// For MHD (Bf non-null) c_d is the fast speed of the zone state whose field is the mean of the
+// two face values (Sec. III, opening).
+__global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict__ U, const double* __restrict__ Bf,
+                                                double gamma, double idx, double idy, double idz, double cfl,
+                                                double* dt_out, unsigned long long* scratch, unsigned* flag) {
     double s = 0.0;
     bool bad = false;
     const long long N = g.n;
@@ -20,13 +22,32 @@ __global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict
         const double rho = U[z], mx = U[N + z], my = U[2 * N + z], mz = U[3 * N + z], E = U[4 * N + z];
         const double ir = 1.0 / rho;
         const double vx = mx * ir, vy = my * ir, vz = mz * ir;
-        const double p = (gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy + mz * vz));
-        if (!(rho > 0.0) || !(p > 0.0)) {
-            bad = true;
-            continue;
+        double v;
+        if (Bf) {
+            const int i = (int)(z % g.nx);
+            const long long t = z / g.nx;
+            const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+            Vec<8, double> u;
+            u[0] = rho; u[1] = mx; u[2] = my; u[3] = mz; u[4] = E;
+            u[5] = 0.5 * (Bf[z] + Bf[nbr(g, i, j, k, 1, 0, 0)]);
+            u[6] = 0.5 * (Bf[N + z] + Bf[N + nbr(g, i, j, k, 0, 1, 0)]);
+            u[7] = 0.5 * (Bf[2 * N + z] + Bf[2 * N + nbr(g, i, j, k, 0, 0, 1)]);
+            const Prim<8, double> q = primitives(u, gamma - 1.0);
+            if (!(rho > 0.0) || !(q.p > 0.0)) {
+                bad = true;
+                continue;
+            }
+            v = (fabs(vx) + fast_speed<0>(u, q, gamma)) * idx + (fabs(vy) + fast_speed<1>(u, q, gamma)) * idy +
+                (fabs(vz) + fast_speed<2>(u, q, gamma)) * idz;
+        } else {
+            const double p = (gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy + mz * vz));
+            if (!(rho > 0.0) || !(p > 0.0)) {
+                bad = true;
+                continue;
+            }
+            const double a = sqrt(gamma * p * ir);
+            v = (fabs(vx) + a) * idx + (fabs(vy) + a) * idy + (fabs(vz) + a) * idz;
         }
-        const double a = sqrt(gamma * p * ir);
-        const double v = (fabs(vx) + a) * idx + (fabs(vy) + a) * idy + (fabs(vz) + a) * idz;
         s = fmax(s, v);
     }
     if (bad) raise_flag(flag, FLAG_UNPHYSICAL);
@@ -54,15 +75,15 @@ __global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict
     }
 }
 
-int launch_max_dt(const Grid& g, const double* U, double gamma, const double dx[3], double cfl, double* dt_dev,
-                  unsigned long long* scratch, unsigned* flag, cudaStream_t st) {
+int launch_max_dt(const Grid& g, const double* U, const double* Bf, double gamma, const double dx[3], double cfl,
+                  double* dt_dev, unsigned long long* scratch, unsigned* flag, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long want = (g.n + 255) / 256;
     const long long cap = (long long)sms * 8;
     const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
-    k_max_dt<<<blocks, 256, 0, st>>>(g, U, gamma, 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2], cfl, dt_dev, scratch, flag);
+    k_max_dt<<<blocks, 256, 0, st>>>(g, U, Bf, gamma, 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2], cfl, dt_dev, scratch, flag);
     return 1;
 }
 
@@ -133,14 +154,28 @@ int launch_flux_update(const StepArgs& a, double* out, const double* base, doubl
                        cudaStream_t st) {
     const int T = 128;
     const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
-    if (a.solver == SOLVER_HLL)
-        k_flux_update<SOLVER_HLL, R><<<blocks, T, 0, st>>>(a, out, base, c_host, use_dt_dev ? 1 : 0);
+    const int dd = use_dt_dev ? 1 : 0;
+    if (a.mhd)
+        k_flux_update<SOLVER_HLL, 8, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+    else if (a.solver == SOLVER_HLL)
+        k_flux_update<SOLVER_HLL, 5, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
     else
-        k_flux_update<SOLVER_LINEARIZED, R><<<blocks, T, 0, st>>>(a, out, base, c_host, use_dt_dev ? 1 : 0);
+        k_flux_update<SOLVER_LINEARIZED, 5, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
     return 1;
+}
+
+template <class R>
+int launch_emf_ct(const StepArgs& a, double* Bf, double c_host, bool use_dt_dev, cudaStream_t st) {
+    const int T = 128;
+    const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
+    k_emf<R><<<blocks, T, 0, st>>>(a);
+    k_ct<R><<<blocks, T, 0, st>>>(a, Bf, c_host, use_dt_dev ? 1 : 0);
+    return 2;
 }
 
 template int launch_flux_update<double>(const StepArgs&, double*, const double*, double, bool, cudaStream_t);
 template int launch_flux_update<float>(const StepArgs&, double*, const double*, double, bool, cudaStream_t);
+template int launch_emf_ct<double>(const StepArgs&, double*, double, bool, cudaStream_t);
+template int launch_emf_ct<float>(const StepArgs&, double*, double, bool, cudaStream_t);
 
 }  // namespace ader

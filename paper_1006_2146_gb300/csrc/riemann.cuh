@@ -16,30 +16,32 @@
 
 namespace ader {
 
-template <class R>
+template <int NV, class R>
 struct FaceSide {
-    Vec<5, R> ub, avg, F;
+    Vec<NV, R> ub, avg, F;
 };
 
-template <int D, class R>
-ADER_DEV Vec<5, R> riemann_hll(const FaceSide<R>& L, const FaceSide<R>& Rt, R gamma, R gm1) {
-    const Prim<R> pl = primitives(L.ub, gm1), pr = primitives(Rt.ub, gm1);
+// HLL with the fast speeds (sound speeds for Euler) of the barycentre states
+template <int D, int NV, class R>
+ADER_DEV Vec<NV, R> riemann_hll(const FaceSide<NV, R>& L, const FaceSide<NV, R>& Rt, R gamma, R gm1) {
+    const Prim<NV, R> pl = primitives(L.ub, gm1), pr = primitives(Rt.ub, gm1);
     const R vl = D == 0 ? pl.vx : (D == 1 ? pl.vy : pl.vz);
     const R vr = D == 0 ? pr.vx : (D == 1 ? pr.vy : pr.vz);
-    const R al = sqrt(gamma * pl.p * pl.irho), ar = sqrt(gamma * pr.p * pr.irho);
+    const R al = fast_speed<D>(L.ub, pl, gamma), ar = fast_speed<D>(Rt.ub, pr, gamma);
     const R lamL = fmin(fmin(vl - al, vr - ar), R(0));
     const R lamR = fmax(fmax(vl + al, vr + ar), R(0));
     const R inv = rcp(lamR - lamL);
     const R wl = lamR * inv, wr = -lamL * inv, wd = lamR * lamL * inv;
-    Vec<5, R> out;
+    Vec<NV, R> out;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) out[v] = wl * L.F[v] + wr * Rt.F[v] + wd * (Rt.avg[v] - L.avg[v]);
+    for (int v = 0; v < NV; ++v) out[v] = wl * L.F[v] + wr * Rt.F[v] + wd * (Rt.avg[v] - L.avg[v]);
     return out;
 }
 
+// Euler only (the MHD eigen-structure is not built)
 template <int D, class R>
-ADER_DEV Vec<5, R> riemann_linearized(const FaceSide<R>& L, const FaceSide<R>& Rt, R gamma, R gm1) {
-    const Prim<R> pl = primitives(L.ub, gm1), pr = primitives(Rt.ub, gm1);
+ADER_DEV Vec<5, R> riemann_linearized(const FaceSide<5, R>& L, const FaceSide<5, R>& Rt, R gamma, R gm1) {
+    const Prim<5, R> pl = primitives(L.ub, gm1), pr = primitives(Rt.ub, gm1);
     const R rho = R(0.5) * (L.ub[0] + Rt.ub[0]);
     const R v[3] = {R(0.5) * (pl.vx + pr.vx), R(0.5) * (pl.vy + pr.vy), R(0.5) * (pl.vz + pr.vz)};
     const R p = R(0.5) * (pl.p + pr.p);
@@ -73,10 +75,12 @@ ADER_DEV Vec<5, R> riemann_linearized(const FaceSide<R>& L, const FaceSide<R>& R
     return out;
 }
 
-template <int SOLVER, int D, class R>
-ADER_DEV Vec<5, R> riemann(const FaceSide<R>& L, const FaceSide<R>& Rt, R gamma, R gm1) {
-    if (SOLVER == 0) return riemann_hll<D>(L, Rt, gamma, gm1);
-    return riemann_linearized<D>(L, Rt, gamma, gm1);
+template <int SOLVER, int D, int NV, class R>
+ADER_DEV Vec<NV, R> riemann(const FaceSide<NV, R>& L, const FaceSide<NV, R>& Rt, R gamma, R gm1) {
+    if constexpr (SOLVER == 0 || NV != 5)
+        return riemann_hll<D>(L, Rt, gamma, gm1);
+    else
+        return riemann_linearized<D>(L, Rt, gamma, gm1);
 }
 
 }  // namespace ader

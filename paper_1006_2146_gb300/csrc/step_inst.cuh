@@ -1,0 +1,41 @@
+// Instantiates the predictor + face kernel for one (order, variable count,
+// precision); included by the small step_o*_*.cu translation units so that
+// the build compiles them in parallel.  Expects ADER_ORDER, ADER_NV, ADER_REAL.
+#include "step_kernels.cuh"
+#include "zone_o2.cuh"
+#include "zone_o3.cuh"
+#include "zone_o4.cuh"
+
+namespace ader {
+
+#define ADER_ZONEOPS(O)                                                                                              \
+    template <> struct ZoneOps<O> {                                                                                  \
+        template <int NV, class R> static ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n) { \
+            o##O::predict_modal(m, gm1, cx, cy, cz, n);                                                              \
+        }                                                                                                            \
+        template <int NV, class R> static ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n) { \
+            o##O::predict_nodal(m, gm1, cx, cy, cz, n);                                                              \
+        }                                                                                                            \
+        template <int D, int NV, class R>                                                                            \
+        static ADER_DEV void face(const Vec<NV, R>* p, R gm1, Vec<NV, R>& ub, Vec<NV, R>& avg, Vec<NV, R>& Fa) {     \
+            o##O::face<D>(p, gm1, ub, avg, Fa);                                                                       \
+        }                                                                                                            \
+        template <int D, class R>                                                                                    \
+        static ADER_DEV void face_mhd(const Vec<8, R>* p, R gm1, Vec<8, R>& ub, Vec<8, R>& avg, Vec<8, R>& Fa, R* eu, \
+                                      R* ef) {                                                                       \
+            o##O::face_mhd<D>(p, gm1, ub, avg, Fa, eu, ef);                                                           \
+        }                                                                                                            \
+    };
+
+#ifndef ADER_ZONEOPS_DEFINED
+#define ADER_ZONEOPS_DEFINED
+ADER_ZONEOPS(2)
+ADER_ZONEOPS(3)
+ADER_ZONEOPS(4)
+#endif
+
+#ifdef ADER_ORDER
+template int launch_predict_faces_nv<ADER_ORDER, ADER_NV, ADER_REAL>(const StepArgs&, const double*, cudaStream_t);
+#endif
+
+}  // namespace ader

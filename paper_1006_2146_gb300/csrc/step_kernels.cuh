@@ -1,10 +1,14 @@
-// The per-zone predictor + face kernel and the flux + update kernel of one
-// ADER step (Sec. II: reconstruction -> space-time predictor -> face fluxes ->
-// Eq. 6).  Included by the per-order translation units step_o2/3/4.cu.
+// The per-zone predictor + face kernel, the flux + update kernel and, for
+// MHD, the edge-EMF and constrained-transport kernels of one ADER step
+// (Sec. II: reconstruction -> space-time predictor -> face fluxes -> Eqs. 6, 8).
+// Instantiated per (order, variables, precision) through step_inst.cuh.
 //
-// S3 layout: S3[((side*3 + q)*5 + v)*N + zone], side = 2*D + (S < 0),
-// q = 0: barycentre state u_b (Eq. 54), 1: face average <u> (Eq. 55),
-// 2: face average of the physical flux <F> (App. D).
+// S3 layout: S3[(side*NQ + q)*N + zone], side = 2*D + (S < 0), NQ =
+// side_values(NV): q in [0, NV) barycentre state u_b (Eq. 54), [NV, 2NV) face
+// average <u> (Eq. 55), [2NV, 3NV) face average of the physical flux <F>
+// (App. D); MHD adds, for the four edges t1+, t1-, t2+, t2- of the face, the
+// edge averages <u_c> and <F_c> (Eq. 57, Eqs. D.5/D.10/D.15) of the field
+// component c = 5 + t the edge's EMF needs.
 #pragma once
 #include "common.cuh"
 #include "kernels.cuh"
@@ -15,59 +19,71 @@ namespace ader {
 
 template <int ORDER> struct ZoneOps;
 
-template <int ORDER, class R>
-ADER_DEV void load_modes(const StepArgs& a, const double* __restrict__ U, long long z, Vec<5, R>* m) {
+template <int ORDER, int NV, class R>
+ADER_DEV void load_modes(const StepArgs& a, const double* __restrict__ U, long long z, Vec<NV, R>* m) {
     const long long N = a.grid.n;
     const R* S1 = (const R*)a.S1;
     const R* S2 = (const R*)a.S2;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        m[1][v] = R(U[v * N + z]);
+    for (int v = 0; v < NV; ++v) {
+        m[1][v] = v < 5 ? R(U[v * N + z]) : ((const R*)a.ZB)[(v - 5) * N + z];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) m[2 + d][v] = S1[((0 * 3 + d) * 5 + v) * N + z];          // w2 w3 w4
+        for (int d = 0; d < 3; ++d) m[2 + d][v] = S1[((0 * 3 + d) * NV + v) * N + z];          // w2 w3 w4
         if (ORDER >= 3) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) m[5 + d][v] = S1[((1 * 3 + d) * 5 + v) * N + z];      // w5 w6 w7
+            for (int d = 0; d < 3; ++d) m[5 + d][v] = S1[((1 * 3 + d) * NV + v) * N + z];      // w5 w6 w7
 #pragma unroll
-            for (int c = 0; c < 3; ++c) m[8 + c][v] = S2[(c * 5 + v) * N + z];                 // w8 w9 w10
+            for (int c = 0; c < 3; ++c) m[8 + c][v] = S2[(c * NV + v) * N + z];                 // w8 w9 w10
         }
         if (ORDER == 4) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) m[11 + d][v] = S1[((2 * 3 + d) * 5 + v) * N + z];     // w11 w12 w13
+            for (int d = 0; d < 3; ++d) m[11 + d][v] = S1[((2 * 3 + d) * NV + v) * N + z];     // w11 w12 w13
 #pragma unroll
-            for (int c = 0; c < 7; ++c) m[14 + c][v] = S2[((3 + c) * 5 + v) * N + z];          // w14..w20
+            for (int c = 0; c < 7; ++c) m[14 + c][v] = S2[((3 + c) * NV + v) * N + z];          // w14..w20
         }
     }
 }
 
-template <int ORDER, int D, int S, class R>
-ADER_DEV void store_face(const StepArgs& a, long long z, const Vec<5, R>* m, R gm1) {
+template <int ORDER, int D, int S, int NV, class R>
+ADER_DEV void store_face(const StepArgs& a, long long z, const Vec<NV, R>* m, R gm1) {
     constexpr int L = ModeCount<ORDER>::L;
-    Vec<5, R> p[L + 1];
+    constexpr int NQ = side_values(NV);
+    Vec<NV, R> p[L + 1];
     to_face_frame<ORDER, D, S>(m, p);
-    Vec<5, R> ub, avg, Fa;
-    ZoneOps<ORDER>::template face<D>(p, gm1, ub, avg, Fa);
+    Vec<NV, R> ub, avg, Fa;
+    R eu[4], ef[4];
+    if constexpr (NV == 8)
+        ZoneOps<ORDER>::template face_mhd<D>(p, gm1, ub, avg, Fa, eu, ef);
+    else
+        ZoneOps<ORDER>::template face<D>(p, gm1, ub, avg, Fa);
     // a non-physical barycentre state is replaced by the zone average for the wave speeds
-    const Prim<R> q = primitives(ub, gm1);
+    const Prim<NV, R> q = primitives(ub, gm1);
     if (!(ub[0] > R(0)) || !(q.p > R(0))) ub = m[1];
     constexpr int side = 2 * D + (S < 0 ? 1 : 0);
     R* S3 = (R*)a.S3;
     const long long N = a.grid.n;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        S3[((side * 3 + 0) * 5 + v) * N + z] = ub[v];
-        S3[((side * 3 + 1) * 5 + v) * N + z] = avg[v];
-        S3[((side * 3 + 2) * 5 + v) * N + z] = Fa[v];
+    for (int v = 0; v < NV; ++v) {
+        S3[(side * NQ + v) * N + z] = ub[v];
+        S3[(side * NQ + NV + v) * N + z] = avg[v];
+        S3[(side * NQ + 2 * NV + v) * N + z] = Fa[v];
+    }
+    if constexpr (NV == 8) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            S3[(side * NQ + 3 * NV + 2 * e) * N + z] = eu[e];
+            S3[(side * NQ + 3 * NV + 2 * e + 1) * N + z] = ef[e];
+        }
     }
 }
 
-template <int ORDER, int FORM, class R>
+template <int ORDER, int FORM, int NV, class R>
 ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U, long long z) {
     constexpr int LS = ModeCount<ORDER>::LS, L = ModeCount<ORDER>::L;
-    Vec<5, R> m[L + 1];
+    Vec<NV, R> m[L + 1];
     load_modes<ORDER>(a, U, z, m);
 #pragma unroll
-    for (int k = LS + 1; k <= L; ++k) m[k] = vzero<5, R>();
+    for (int k = LS + 1; k <= L; ++k) m[k] = vzero<NV, R>();
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
     const R gm1 = R(a.gamma - 1.0);
     const R cx = R(dt / a.dx[0]), cy = R(dt / a.dx[1]), cz = R(dt / a.dx[2]);
@@ -85,41 +101,43 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
     store_face<ORDER, 2, -1>(a, z, m, gm1);
 }
 
-template <int ORDER, int FORM, class R>
+template <int ORDER, int FORM, int NV, class R>
 __global__ void __launch_bounds__(128) k_predict_faces(StepArgs a, const double* __restrict__ U) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (z < a.grid.n) zone_predict_faces<ORDER, FORM, R>(a, U, z);
+    if (z < a.grid.n) zone_predict_faces<ORDER, FORM, NV, R>(a, U, z);
 }
 
-template <class R>
-ADER_DEV FaceSide<R> load_side(const StepArgs& a, int side, long long z) {
+template <int NV, class R>
+ADER_DEV FaceSide<NV, R> load_side(const StepArgs& a, int side, long long z) {
+    constexpr int NQ = side_values(NV);
     const R* S3 = (const R*)a.S3;
     const long long N = a.grid.n;
-    FaceSide<R> s;
+    FaceSide<NV, R> s;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        s.ub[v] = S3[((side * 3 + 0) * 5 + v) * N + z];
-        s.avg[v] = S3[((side * 3 + 1) * 5 + v) * N + z];
-        s.F[v] = S3[((side * 3 + 2) * 5 + v) * N + z];
+    for (int v = 0; v < NV; ++v) {
+        s.ub[v] = S3[(side * NQ + v) * N + z];
+        s.avg[v] = S3[(side * NQ + NV + v) * N + z];
+        s.F[v] = S3[(side * NQ + 2 * NV + v) * N + z];
     }
     return s;
 }
 
-// F(i+1/2) - F(i-1/2) in direction D, accumulated in FP64.  The same
-// function with the same operands computes a face's flux for both of its
-// zones, so the two values are identical and Eq. 6 telescopes exactly.
-template <int SOLVER, int D, class R>
+// F(i+1/2) - F(i-1/2) in direction D, accumulated in FP64 for the five
+// conserved hydrodynamic variables.  The same function with the same operands
+// computes a face's flux for both of its zones, so the two values are
+// identical and Eq. 6 telescopes exactly.
+template <int SOLVER, int D, int NV, class R>
 ADER_DEV void flux_difference(const StepArgs& a, long long z, int i, int j, int k, R gamma, R gm1, double* acc) {
     const long long zp = nbr(a.grid, i, j, k, D == 0, D == 1, D == 2);
     const long long zm = nbr(a.grid, i, j, k, -(D == 0), -(D == 1), -(D == 2));
-    const Vec<5, R> Fp = riemann<SOLVER, D>(load_side<R>(a, 2 * D, z), load_side<R>(a, 2 * D + 1, zp), gamma, gm1);
-    const Vec<5, R> Fm = riemann<SOLVER, D>(load_side<R>(a, 2 * D, zm), load_side<R>(a, 2 * D + 1, z), gamma, gm1);
+    const Vec<NV, R> Fp = riemann<SOLVER, D>(load_side<NV, R>(a, 2 * D, z), load_side<NV, R>(a, 2 * D + 1, zp), gamma, gm1);
+    const Vec<NV, R> Fm = riemann<SOLVER, D>(load_side<NV, R>(a, 2 * D, zm), load_side<NV, R>(a, 2 * D + 1, z), gamma, gm1);
     const double inv = 1.0 / a.dx[D];
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] -= ((double)Fp[v] - (double)Fm[v]) * inv;
 }
 
-template <int SOLVER, class R>
+template <int SOLVER, int NV, class R>
 ADER_DEV void zone_flux_update(const StepArgs& a, double* out, const double* base, double c_host, int use_dt_dev,
                                long long z) {
     const int i = (int)(z % a.grid.nx);
@@ -127,9 +145,9 @@ ADER_DEV void zone_flux_update(const StepArgs& a, double* out, const double* bas
     const int j = (int)(t % a.grid.ny), k = (int)(t / a.grid.ny);
     const R gamma = R(a.gamma), gm1 = R(a.gamma - 1.0);
     double acc[5] = {0, 0, 0, 0, 0};
-    flux_difference<SOLVER, 0, R>(a, z, i, j, k, gamma, gm1, acc);
-    flux_difference<SOLVER, 1, R>(a, z, i, j, k, gamma, gm1, acc);
-    flux_difference<SOLVER, 2, R>(a, z, i, j, k, gamma, gm1, acc);
+    flux_difference<SOLVER, 0, NV, R>(a, z, i, j, k, gamma, gm1, acc);
+    flux_difference<SOLVER, 1, NV, R>(a, z, i, j, k, gamma, gm1, acc);
+    flux_difference<SOLVER, 2, NV, R>(a, z, i, j, k, gamma, gm1, acc);
     const double c = use_dt_dev ? c_host * (*a.dt_dev) : c_host;
     const long long N = a.grid.n;
     bool bad = false;
@@ -142,21 +160,108 @@ ADER_DEV void zone_flux_update(const StepArgs& a, double* out, const double* bas
     if (bad) raise_flag(a.flag, FLAG_NONFINITE);
 }
 
-template <int SOLVER, class R>
+template <int SOLVER, int NV, class R>
 __global__ void __launch_bounds__(128) k_flux_update(StepArgs a, double* out, const double* base, double c_host,
                                                      int use_dt_dev) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (z < a.grid.n) zone_flux_update<SOLVER, R>(a, out, base, c_host, use_dt_dev, z);
+    if (z < a.grid.n) zone_flux_update<SOLVER, NV, R>(a, out, base, c_host, use_dt_dev, z);
 }
 
-template <int ORDER, class R>
-int launch_predict_faces_order(const StepArgs& a, const double* U, cudaStream_t st) {
+// ------------------------------------------------------------------ MHD: edge EMFs (Sec. II.3, Eq. 7)
+// HLL flux of the face of direction D between zones zl (lower) and zr,
+// evaluated with its edge slot e (0: t1+, 1: t1-, 2: t2+, 3: t2-): the face's
+// own frozen wave speeds (from its barycentre states) applied to the edge
+// averages of its two sides.
+template <int D, class R>
+ADER_DEV R edge_hll(const StepArgs& a, long long zl, long long zr, int e, R gamma, R gm1) {
+    constexpr int NQ = side_values(8);
+    const R* S3 = (const R*)a.S3;
+    const long long N = a.grid.n;
+    const int sl = 2 * D, sr = 2 * D + 1;
+    Vec<8, R> ubl, ubr;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        ubl[v] = S3[(sl * NQ + v) * N + zl];
+        ubr[v] = S3[(sr * NQ + v) * N + zr];
+    }
+    const Prim<8, R> pl = primitives(ubl, gm1), pr = primitives(ubr, gm1);
+    const R vl = D == 0 ? pl.vx : (D == 1 ? pl.vy : pl.vz);
+    const R vr = D == 0 ? pr.vx : (D == 1 ? pr.vy : pr.vz);
+    const R cl = fast_speed<D>(ubl, pl, gamma), cr = fast_speed<D>(ubr, pr, gamma);
+    const R lamL = fmin(fmin(vl - cl, vr - cr), R(0));
+    const R lamR = fmax(fmax(vl + cl, vr + cr), R(0));
+    const R uL = S3[(sl * NQ + 24 + 2 * e) * N + zl], FL = S3[(sl * NQ + 25 + 2 * e) * N + zl];
+    const R uR = S3[(sr * NQ + 24 + 2 * e) * N + zr], FR = S3[(sr * NQ + 25 + 2 * e) * N + zr];
+    return (lamR * FL - lamL * FR + lamR * lamL * (uR - uL)) / (lamR - lamL);
+}
+
+// EMFs at the three upper edges of zone (i, j, k): Ez on (i+1/2, j+1/2),
+// Ey on (i+1/2, k+1/2), Ex on (j+1/2, k+1/2); each the mean of the four
+// adjacent faces' edge fluxes with Eq. 7's signs (Ez = -F7 = G6,
+// Ey = F8 = -H6, Ex = -G8 = H7).
+template <class R>
+ADER_DEV void zone_emf(const StepArgs& a, long long z) {
+    const Grid& g = a.grid;
+    const int i = (int)(z % g.nx);
+    const long long t = z / g.nx;
+    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+    const R gamma = R(a.gamma), gm1 = R(a.gamma - 1.0);
+    const long long zx = nbr(g, i, j, k, 1, 0, 0), zy = nbr(g, i, j, k, 0, 1, 0), zz = nbr(g, i, j, k, 0, 0, 1);
+    const long long zxy = nbr(g, i, j, k, 1, 1, 0), zxz = nbr(g, i, j, k, 1, 0, 1), zyz = nbr(g, i, j, k, 0, 1, 1);
+    // x-faces: t1 = y (slots 0, 1), t2 = z (2, 3); y-faces: t1 = x, t2 = z; z-faces: t1 = x, t2 = y
+    const R Ez = R(0.25) * (-edge_hll<0, R>(a, z, zx, 0, gamma, gm1) - edge_hll<0, R>(a, zy, zxy, 1, gamma, gm1) +
+                            edge_hll<1, R>(a, z, zy, 0, gamma, gm1) + edge_hll<1, R>(a, zx, zxy, 1, gamma, gm1));
+    const R Ey = R(0.25) * (edge_hll<0, R>(a, z, zx, 2, gamma, gm1) + edge_hll<0, R>(a, zz, zxz, 3, gamma, gm1) -
+                            edge_hll<2, R>(a, z, zz, 0, gamma, gm1) - edge_hll<2, R>(a, zx, zxz, 1, gamma, gm1));
+    const R Ex = R(0.25) * (-edge_hll<1, R>(a, z, zy, 2, gamma, gm1) - edge_hll<1, R>(a, zz, zyz, 3, gamma, gm1) +
+                            edge_hll<2, R>(a, z, zz, 2, gamma, gm1) + edge_hll<2, R>(a, zy, zyz, 3, gamma, gm1));
+    R* E = (R*)a.E;
+    E[z] = Ex;
+    E[g.n + z] = Ey;
+    E[2 * g.n + z] = Ez;
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) k_emf(StepArgs a) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < a.grid.n) zone_emf<R>(a, z);
+}
+
+// Eq. 8 on the three faces i-1/2, j-1/2, k-1/2 of zone (i, j, k): each face
+// is written by exactly one zone, so the update is in place.
+template <class R>
+ADER_DEV void zone_ct(const StepArgs& a, double* Bf, double c_host, int use_dt_dev, long long z) {
+    const Grid& g = a.grid;
+    const int i = (int)(z % g.nx);
+    const long long t = z / g.nx;
+    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+    const R* E = (const R*)a.E;
+    const long long N = g.n;
+    auto Ex = [&](int di, int dj, int dk) { return (double)E[nbr(g, i, j, k, di, dj, dk)]; };
+    auto Ey = [&](int di, int dj, int dk) { return (double)E[N + nbr(g, i, j, k, di, dj, dk)]; };
+    auto Ez = [&](int di, int dj, int dk) { return (double)E[2 * N + nbr(g, i, j, k, di, dj, dk)]; };
+    const double dt = use_dt_dev ? c_host * (*a.dt_dev) : c_host;
+    const double idx = 1.0 / a.dx[0], idy = 1.0 / a.dx[1], idz = 1.0 / a.dx[2];
+    // the edges of face i-1/2 are stored one zone lower in x (likewise for y, z)
+    Bf[z] -= dt * ((Ez(-1, 0, 0) - Ez(-1, -1, 0)) * idy - (Ey(-1, 0, 0) - Ey(-1, 0, -1)) * idz);
+    Bf[N + z] -= dt * ((Ex(0, -1, 0) - Ex(0, -1, -1)) * idz - (Ez(0, -1, 0) - Ez(-1, -1, 0)) * idx);
+    Bf[2 * N + z] -= dt * ((Ey(0, 0, -1) - Ey(-1, 0, -1)) * idx - (Ex(0, 0, -1) - Ex(0, -1, -1)) * idy);
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) k_ct(StepArgs a, double* Bf, double c_host, int use_dt_dev) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < a.grid.n) zone_ct<R>(a, Bf, c_host, use_dt_dev, z);
+}
+
+template <int ORDER, int NV, class R>
+int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st) {
     const int T = 128;
     const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
     if (a.form == FORM_MODAL)
-        k_predict_faces<ORDER, FORM_MODAL, R><<<blocks, T, 0, st>>>(a, U);
+        k_predict_faces<ORDER, FORM_MODAL, NV, R><<<blocks, T, 0, st>>>(a, U);
     else
-        k_predict_faces<ORDER, FORM_NODAL, R><<<blocks, T, 0, st>>>(a, U);
+        k_predict_faces<ORDER, FORM_NODAL, NV, R><<<blocks, T, 0, st>>>(a, U);
     return 1;
 }
 

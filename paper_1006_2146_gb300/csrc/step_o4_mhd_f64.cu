@@ -1,0 +1,5 @@
+// Order-4 MHD predictor + face kernel in F64 (see step_inst.cuh).
+#define ADER_ORDER 4
+#define ADER_NV 8
+#define ADER_REAL double
+#include "step_inst.cuh"

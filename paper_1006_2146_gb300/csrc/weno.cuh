@@ -90,21 +90,29 @@ ADER_DEV R slope_of(const Grid& g, const R* __restrict__ F, int i, int j, int k,
 
 
 // ---------------------------------------------------------------- per-zone bodies of the kernels
-// 1-D moments of every variable of zone z (S1 layout in recon.cu)
-template <int ORDER, class R>
-ADER_DEV void zone_weno1d(const Grid& g, const double* __restrict__ U, R* __restrict__ S1, long long z) {
+// 1-D moments of zone z (S1 layout in recon.cu).  Variables 0..4 are read
+// from U; for MHD (NV = 8) variable 5 + e is the zone field B_e read from ZB,
+// whose moments along e come from the face-B WENO (zone_face_b), so only the
+// two transverse directions are reconstructed here.
+template <int ORDER, int NV, class R>
+ADER_DEV void zone_weno1d(const Grid& g, const double* __restrict__ U, const R* __restrict__ ZB,
+                          R* __restrict__ S1, long long z) {
     int i, j, k;
     zone_ijk(g, z, i, j, k);
     constexpr int RAD = ORDER == 4 ? 3 : 2;
-    constexpr int NV = 5;
     for (int v = 0; v < NV; ++v) {
-        const double* Uv = U + (long long)v * g.n;
+        const double* Uv = v < 5 ? U + (long long)v * g.n : nullptr;
+        const R* Bv = v >= 5 ? ZB + (long long)(v - 5) * g.n : nullptr;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
+            if (v >= 5 && d == v - 5) continue;
             R a[2 * RAD + 1];
 #pragma unroll
             for (int o = -RAD; o <= RAD; ++o)
-                a[o + RAD] = R(Uv[nbr(g, i, j, k, d == 0 ? o : 0, d == 1 ? o : 0, d == 2 ? o : 0)]);
+            {
+                const long long zz = nbr(g, i, j, k, d == 0 ? o : 0, d == 1 ? o : 0, d == 2 ? o : 0);
+                a[o + RAD] = v < 5 ? R(Uv[zz]) : Bv[zz];
+            }
             if (ORDER == 4) {
                 R b, c, e;
                 weno4(a, b, c, e);
@@ -122,11 +130,10 @@ ADER_DEV void zone_weno1d(const Grid& g, const double* __restrict__ U, R* __rest
 }
 
 // first-level cross moments w8 w9 w10 (w14..w19 at order 4) of zone z
-template <int ORDER, class R>
+template <int ORDER, int NV, class R>
 ADER_DEV void zone_cross1(const Grid& g, const R* __restrict__ S1, R* __restrict__ S2, long long z) {
     int i, j, k;
     zone_ijk(g, z, i, j, k);
-    constexpr int NV = 5;
     for (int v = 0; v < NV; ++v) {
         const R* w2 = S1 + ((0 * 3 + 0) * NV + v) * g.n;
         const R* w3 = S1 + ((0 * 3 + 1) * NV + v) * g.n;
@@ -149,17 +156,80 @@ ADER_DEV void zone_cross1(const Grid& g, const R* __restrict__ S1, R* __restrict
 }
 
 // w20 of zone z from the first-level cross moments of its neighbours
-template <class R>
+template <int NV, class R>
 ADER_DEV void zone_cross2(const Grid& g, R* __restrict__ S2, long long z) {
     int i, j, k;
     zone_ijk(g, z, i, j, k);
-    constexpr int NV = 5;
     for (int v = 0; v < NV; ++v) {
         const R* w8 = S2 + (0 * NV + v) * g.n;
         const R* w9 = S2 + (1 * NV + v) * g.n;
         const R* w10 = S2 + (2 * NV + v) * g.n;
         S2[(9 * NV + v) * g.n + z] = (slope_of(g, w8, i, j, k, 2) + slope_of(g, w9, i, j, k, 0) +
                                       slope_of(g, w10, i, j, k, 1)) * R(1.0 / 3.0);
+    }
+}
+
+// ---------------------------------------------------------------- Sec. III: zone B from face B
+// Face-B WENO along direction e for zone z: the zone-averaged normal field b0
+// (written to ZB[e]) and its normal moments b_x, b_xx, b_xxx (written to the
+// S1 slots of variable 5 + e, direction e).  Bf[e][zone i] is B_e on face i - 1/2.
+// Order 2: mean and difference (Sec. III, opening).  Order 3: Eqs. 21-24 with
+// linear weights (1/2, 1/2).  Order 4: Eqs. 25-29 with (1/4, 1/2, 1/4).
+template <int ORDER, class R>
+ADER_DEV void zone_face_b(const Grid& g, const double* __restrict__ Bf, R* __restrict__ ZB, R* __restrict__ S1,
+                          long long z) {
+    int i, j, k;
+    zone_ijk(g, z, i, j, k);
+    constexpr int NV = 8;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const double* B = Bf + (long long)e * g.n;
+        auto at = [&](int o) { return R(B[nbr(g, i, j, k, e == 0 ? o : 0, e == 1 ? o : 0, e == 2 ? o : 0)]); };
+        const R Bm = at(0), Bp = at(1);                   // faces i - 1/2 and i + 1/2
+        R m[4];
+        if (ORDER == 2) {
+            m[0] = R(0.5) * (Bp + Bm);
+            m[1] = Bp - Bm;
+        } else if (ORDER == 3) {
+            const R Bmm = at(-1), Bpp = at(2);
+            const R s1[3] = {(R(8) * Bm - Bmm + R(5) * Bp) * R(1.0 / 12.0), Bp - Bm, (Bp + Bmm - R(2) * Bm) * R(0.5)};
+            const R s2[3] = {(R(8) * Bp - Bpp + R(5) * Bm) * R(1.0 / 12.0), Bp - Bm, (Bm + Bpp - R(2) * Bp) * R(0.5)};
+            const R k13 = R(13.0 / 3.0);
+            const R a1 = R(0.5) / wsq(s1[1] * s1[1] + k13 * s1[2] * s1[2]);
+            const R a2 = R(0.5) / wsq(s2[1] * s2[1] + k13 * s2[2] * s2[2]);
+            const R inv = rcp(a1 + a2);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) m[r] = (a1 * s1[r] + a2 * s2[r]) * inv;
+        } else {
+            const R Bmm = at(-1), Bmmm = at(-2), Bpp = at(2), Bppp = at(3);
+            const R c[3][4] = {
+                {(R(9) * Bp + R(19) * Bm - R(5) * Bmm + Bmmm) * R(1.0 / 24.0),
+                 (R(59) * Bp - R(57) * Bm - R(3) * Bmm + Bmmm) * R(1.0 / 60.0),
+                 (R(3) * Bp - R(7) * Bm + R(5) * Bmm - Bmmm) * R(0.25),
+                 (Bp - R(3) * Bm + R(3) * Bmm - Bmmm) * R(1.0 / 6.0)},                       // Eq. 26
+                {(-Bpp + R(13) * Bp + R(13) * Bm - Bmm) * R(1.0 / 24.0),
+                 (-Bpp + R(63) * Bp - R(63) * Bm + Bmm) * R(1.0 / 60.0),
+                 (Bpp - Bp - Bm + Bmm) * R(0.25),
+                 (Bpp - R(3) * Bp + R(3) * Bm - Bmm) * R(1.0 / 6.0)},                        // Eq. 27
+                {(Bppp - R(5) * Bpp + R(19) * Bp + R(9) * Bm) * R(1.0 / 24.0),
+                 (-Bppp + R(3) * Bpp + R(57) * Bp - R(59) * Bm) * R(1.0 / 60.0),
+                 (-Bppp + R(5) * Bpp - R(7) * Bp + R(3) * Bm) * R(0.25),
+                 (Bppp - R(3) * Bpp + R(3) * Bp - Bm) * R(1.0 / 6.0)}};                      // Eq. 28
+            const R gl[3] = {R(0.25), R(0.5), R(0.25)};
+            R al[3], s = R(0);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const R t = c[q][1] + R(0.1) * c[q][3];
+                al[q] = gl[q] / wsq(t * t + R(13.0 / 3.0) * c[q][2] * c[q][2] + R(781.0 / 20.0) * c[q][3] * c[q][3]);
+                s += al[q];
+            }
+            const R inv = rcp(s);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) m[r] = (al[0] * c[0][r] + al[1] * c[1][r] + al[2] * c[2][r]) * inv;
+        }
+        ZB[(long long)e * g.n + z] = m[0];
+#pragma unroll
+        for (int r = 0; r < ORDER - 1; ++r) S1[((r * 3 + e) * NV + 5 + e) * g.n + z] = m[r + 1];
     }
 }
 

@@ -7,27 +7,26 @@
 namespace ader {
 namespace o2 {
 
-template <class R> using V = Vec<5, R>;
 
 // Eqs. 31-33 and 30 (one iteration, no sources)
-template <class R>
-ADER_DEV void predict_modal(V<R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
-    const V<R> u1 = m[1] + 0.5 * m[2], u2 = m[1] - 0.5 * m[2];
-    const V<R> u3 = m[1] + 0.5 * m[3], u4 = m[1] - 0.5 * m[3];
-    const V<R> u5 = m[1] + 0.5 * m[4], u6 = m[1] - 0.5 * m[4];
-    const V<R> F2 = scale(cx, flux<0>(u1, gm1) - flux<0>(u2, gm1));
-    const V<R> G3 = scale(cy, flux<1>(u3, gm1) - flux<1>(u4, gm1));
-    const V<R> H4 = scale(cz, flux<2>(u5, gm1) - flux<2>(u6, gm1));
+template <int NV, class R>
+ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
+    const Vec<NV, R> u1 = m[1] + 0.5 * m[2], u2 = m[1] - 0.5 * m[2];
+    const Vec<NV, R> u3 = m[1] + 0.5 * m[3], u4 = m[1] - 0.5 * m[3];
+    const Vec<NV, R> u5 = m[1] + 0.5 * m[4], u6 = m[1] - 0.5 * m[4];
+    const Vec<NV, R> F2 = scale(cx, flux<0>(u1, gm1) - flux<0>(u2, gm1));
+    const Vec<NV, R> G3 = scale(cy, flux<1>(u3, gm1) - flux<1>(u4, gm1));
+    const Vec<NV, R> H4 = scale(cz, flux<2>(u5, gm1) - flux<2>(u6, gm1));
     m[5] = n_iter > 0 ? -(F2 + G3 + H4) : m[5];
 }
 
 // Eqs. A.5, A.4 (h term at node 4, the zeta node of Eq. A.1) and A.6
-template <class R>
-ADER_DEV void predict_nodal(V<R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
-    const V<R> u1 = m[1];
-    const V<R> u2 = m[1] + 0.5 * m[2], u3 = m[1] + 0.5 * m[3], u4 = m[1] + 0.5 * m[4];
-    const Prim<R> p1 = primitives(u1, gm1);
-    const V<R> u5 = u1 - 2.0 * (scale(cx, flux<0>(u2, gm1) - flux_from<0>(u1, p1)) +
+template <int NV, class R>
+ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
+    const Vec<NV, R> u1 = m[1];
+    const Vec<NV, R> u2 = m[1] + 0.5 * m[2], u3 = m[1] + 0.5 * m[3], u4 = m[1] + 0.5 * m[4];
+    const Prim<NV, R> p1 = primitives(u1, gm1);
+    const Vec<NV, R> u5 = u1 - 2.0 * (scale(cx, flux<0>(u2, gm1) - flux_from<0>(u1, p1)) +
                                 scale(cy, flux<1>(u3, gm1) - flux_from<1>(u1, p1)) +
                                 scale(cz, flux<2>(u4, gm1) - flux_from<2>(u1, p1)));
     m[5] = n_iter > 0 ? u5 - u1 : m[5];
@@ -35,13 +34,42 @@ ADER_DEV void predict_nodal(V<R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
 
 // Eqs. 58-59 and D.3-D.5: composing D.4 with D.5, <F> is the mean of the flux
 // at the four tau = 1/2 facial nodes (node 5 enters only through the time mode).
-template <int D, class R>
-ADER_DEV void face(const V<R>* p, R gm1, V<R>& ub, V<R>& avg, V<R>& Fa) {
+template <int D, int NV, class R>
+ADER_DEV void face(const Vec<NV, R>* p, R gm1, Vec<NV, R>& ub, Vec<NV, R>& avg, Vec<NV, R>& Fa) {
     ub = p[1] + 0.5 * (p[2] + p[5]);
     avg = ub;
-    const V<R> q1 = ub;
+    const Vec<NV, R> q1 = ub;
     Fa = 0.25 * (flux<D>(q1 + 0.5 * p[3], gm1) + flux<D>(q1 - 0.5 * p[3], gm1) + flux<D>(q1 + 0.5 * p[4], gm1) +
                  flux<D>(q1 - 0.5 * p[4], gm1));
+}
+
+// MHD face: also the edge averages (Eq. 60 for <u>, Eqs. D.4-D.5 for <F>) of
+// the field component each edge's EMF needs.  eu/ef slots: t1+, t1-, t2+, t2-
+// (t1 < t2 the transverse axes); component 5 + t1 on the t1 edges, 5 + t2 on
+// the t2 edges.
+template <int D, class R>
+ADER_DEV void face_mhd(const Vec<8, R>* p, R gm1, Vec<8, R>& ub, Vec<8, R>& avg, Vec<8, R>& Fa, R* eu, R* ef) {
+    constexpr int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
+    ub = p[1] + 0.5 * (p[2] + p[5]);
+    avg = ub;
+    const Vec<8, R> t[6] = {ub, ub + 0.5 * p[3], ub - 0.5 * p[3], ub + 0.5 * p[4], ub - 0.5 * p[4], ub + 0.5 * p[5]};
+    Vec<8, R> F[6];
+#pragma unroll
+    for (int n = 1; n <= 5; ++n) F[n] = flux<D>(t[n], gm1);
+    Fa = 0.25 * (F[1] + F[2] + F[3] + F[4]);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int c = 5 + (s == 0 ? T1 : T2);
+        const R m2 = F[1][c] - F[2][c], m3 = F[3][c] - F[4][c];
+        const R m4 = R(2) * F[5][c] - R(0.5) * (F[1][c] + F[2][c] + F[3][c] + F[4][c]);
+        const R af = F[5][c] - m4 + R(0.5) * m4;
+        const R half = R(0.5) * (s == 0 ? m2 : m3);
+        ef[2 * s] = af + half;
+        ef[2 * s + 1] = af - half;
+        const R hu = R(0.5) * p[s == 0 ? 3 : 4][c];
+        eu[2 * s] = ub[c] + hu;
+        eu[2 * s + 1] = ub[c] - hu;
+    }
 }
 
 }  // namespace o2

@@ -12,13 +12,12 @@
 namespace ader {
 namespace o3 {
 
-template <class R> using V = Vec<5, R>;
 
 // ------------------------------------------------------------------ modal, Sec. IV.2
-template <class R>
-ADER_DEV void predict_modal(V<R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
+template <int NV, class R>
+ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
     // Eq. 38: the thirteen tau = 0 nodes of Eq. 37
-    V<R> u[14];
+    Vec<NV, R> u[14];
     u[1] = m[1] - (m[5] + m[6] + m[7]) / 12.0;
     u[2] = u[1] + 0.5 * (m[2] + m[3]) + 0.25 * (m[5] + m[6] + m[8]);
     u[3] = u[2] - m[3] - 0.5 * m[8];
@@ -33,42 +32,42 @@ ADER_DEV void predict_modal(V<R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
     u[12] = u[11] + m[3] - m[4];
     u[13] = u[10] - m[3] - m[4];
     // fluxes at the tau = 0 nodes, built once (Sec. IV.2)
-    V<R> f[14], g[14], h[14];
+    Vec<NV, R> f[14], g[14], h[14];
 #pragma unroll
     for (int n = 1; n <= 13; ++n) {
-        const Prim<R> q = primitives(u[n], gm1);
+        const Prim<NV, R> q = primitives(u[n], gm1);
         f[n] = flux_from<0>(u[n], q);
         g[n] = flux_from<1>(u[n], q);
         h[n] = flux_from<2>(u[n], q);
     }
     // Eqs. 40-42, tau = 0 modes
-    const V<R> q1 = f[2] + f[3] + f[4] + f[5], q2 = f[6] + f[7] + f[8] + f[9], q3 = f[10] + f[11] + f[12] + f[13];
-    const V<R> F2 = scale(cx, 0.25 * (q1 - q2));
-    const V<R> F5 = scale(cx, 0.5 * (q1 + q2 - q3) - 2.0 * f[1]);
-    const V<R> F8 = scale(cx, f[2] - f[3] - f[6] + f[7]);
-    const V<R> F10 = scale(cx, f[4] - f[5] - f[8] + f[9]);
-    const V<R> q4 = g[2] + g[6] + g[10] + g[12], q5 = g[3] + g[7] + g[11] + g[13], q6 = g[4] + g[5] + g[8] + g[9];
-    const V<R> G3 = scale(cy, 0.25 * (q4 - q5));
-    const V<R> G6 = scale(cy, 0.5 * (q4 + q5 - q6) - 2.0 * g[1]);
-    const V<R> G8 = scale(cy, g[2] - g[3] - g[6] + g[7]);
-    const V<R> G9 = scale(cy, g[10] - g[11] - g[12] + g[13]);
-    const V<R> q7 = h[4] + h[8] + h[10] + h[11], q8 = h[5] + h[9] + h[12] + h[13], q9 = h[2] + h[3] + h[6] + h[7];
-    const V<R> H4 = scale(cz, 0.25 * (q7 - q8));
-    const V<R> H7 = scale(cz, 0.5 * (q7 + q8 - q9) - 2.0 * h[1]);
-    const V<R> H9 = scale(cz, h[10] - h[11] - h[12] + h[13]);
-    const V<R> H10 = scale(cz, h[4] - h[5] - h[8] + h[9]);
+    const Vec<NV, R> q1 = f[2] + f[3] + f[4] + f[5], q2 = f[6] + f[7] + f[8] + f[9], q3 = f[10] + f[11] + f[12] + f[13];
+    const Vec<NV, R> F2 = scale(cx, 0.25 * (q1 - q2));
+    const Vec<NV, R> F5 = scale(cx, 0.5 * (q1 + q2 - q3) - 2.0 * f[1]);
+    const Vec<NV, R> F8 = scale(cx, f[2] - f[3] - f[6] + f[7]);
+    const Vec<NV, R> F10 = scale(cx, f[4] - f[5] - f[8] + f[9]);
+    const Vec<NV, R> q4 = g[2] + g[6] + g[10] + g[12], q5 = g[3] + g[7] + g[11] + g[13], q6 = g[4] + g[5] + g[8] + g[9];
+    const Vec<NV, R> G3 = scale(cy, 0.25 * (q4 - q5));
+    const Vec<NV, R> G6 = scale(cy, 0.5 * (q4 + q5 - q6) - 2.0 * g[1]);
+    const Vec<NV, R> G8 = scale(cy, g[2] - g[3] - g[6] + g[7]);
+    const Vec<NV, R> G9 = scale(cy, g[10] - g[11] - g[12] + g[13]);
+    const Vec<NV, R> q7 = h[4] + h[8] + h[10] + h[11], q8 = h[5] + h[9] + h[12] + h[13], q9 = h[2] + h[3] + h[6] + h[7];
+    const Vec<NV, R> H4 = scale(cz, 0.25 * (q7 - q8));
+    const Vec<NV, R> H7 = scale(cz, 0.5 * (q7 + q8 - q9) - 2.0 * h[1]);
+    const Vec<NV, R> H9 = scale(cz, h[10] - h[11] - h[12] + h[13]);
+    const Vec<NV, R> H10 = scale(cz, h[4] - h[5] - h[8] + h[9]);
     for (int it = 0; it < n_iter; ++it) {
         // Eq. 39: the tau = 1/2 nodes (node 20 serves only source terms)
-        const V<R> u14 = 0.25 * (u[2] + u[3] + u[4] + u[5] + m[12] + m[13]) + 0.5 * m[11] - 0.125 * (m[6] + m[7]);
-        const V<R> u16 = 0.25 * (u[2] + u[6] + u[10] + u[12] + m[12] + m[14]) + 0.5 * m[11] - 0.125 * (m[5] + m[7]);
-        const V<R> u18 = 0.25 * (u[4] + u[8] + u[10] + u[11] + m[12] + m[15]) + 0.5 * m[11] - 0.125 * (m[5] + m[6]);
-        const V<R> u15 = u14 - m[2] - 0.5 * m[13];
-        const V<R> u17 = u16 - m[3] - 0.5 * m[14];
-        const V<R> u19 = u18 - m[4] - 0.5 * m[15];
+        const Vec<NV, R> u14 = 0.25 * (u[2] + u[3] + u[4] + u[5] + m[12] + m[13]) + 0.5 * m[11] - 0.125 * (m[6] + m[7]);
+        const Vec<NV, R> u16 = 0.25 * (u[2] + u[6] + u[10] + u[12] + m[12] + m[14]) + 0.5 * m[11] - 0.125 * (m[5] + m[7]);
+        const Vec<NV, R> u18 = 0.25 * (u[4] + u[8] + u[10] + u[11] + m[12] + m[15]) + 0.5 * m[11] - 0.125 * (m[5] + m[6]);
+        const Vec<NV, R> u15 = u14 - m[2] - 0.5 * m[13];
+        const Vec<NV, R> u17 = u16 - m[3] - 0.5 * m[14];
+        const Vec<NV, R> u19 = u18 - m[4] - 0.5 * m[15];
         // time modes of Eqs. 40-42
-        const V<R> F13 = 2.0 * (scale(cx, flux<0>(u14, gm1) - flux<0>(u15, gm1)) - F2);
-        const V<R> G14 = 2.0 * (scale(cy, flux<1>(u16, gm1) - flux<1>(u17, gm1)) - G3);
-        const V<R> H15 = 2.0 * (scale(cz, flux<2>(u18, gm1) - flux<2>(u19, gm1)) - H4);
+        const Vec<NV, R> F13 = 2.0 * (scale(cx, flux<0>(u14, gm1) - flux<0>(u15, gm1)) - F2);
+        const Vec<NV, R> G14 = 2.0 * (scale(cy, flux<1>(u16, gm1) - flux<1>(u17, gm1)) - G3);
+        const Vec<NV, R> H15 = 2.0 * (scale(cz, flux<2>(u18, gm1) - flux<2>(u19, gm1)) - H4);
         // Eq. 36 without sources
         m[11] = -(F2 + G3 + H4);
         m[12] = -0.5 * (F13 + G14 + H15);
@@ -79,10 +78,10 @@ ADER_DEV void predict_modal(V<R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
 }
 
 // ------------------------------------------------------------------ nodal, App. B
-template <class R>
-ADER_DEV void predict_nodal(V<R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
+template <int NV, class R>
+ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
     // Eq. B.4: the ten tau = 0 nodes of Eq. B.1
-    V<R> u[16];
+    Vec<NV, R> u[16];
     u[1] = m[1] - (m[5] + m[6] + m[7]) / 12.0;
     u[2] = u[1] + 0.5 * m[2] + 0.25 * m[5];
     u[3] = 2.0 * u[1] - u[2] + 0.5 * m[5];
@@ -94,33 +93,33 @@ ADER_DEV void predict_nodal(V<R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
     u[9] = u[2] + u[6] - u[1] + 0.25 * m[10];
     u[10] = u[2] + u[4] - u[1] + 0.25 * m[8];
     // scaled fluxes at the tau = 0 nodes the q-terms of Eq. B.2 use
-    V<R> f[11], g[11], h[11];
+    Vec<NV, R> f[11], g[11], h[11];
 #pragma unroll
     for (int n = 1; n <= 10; ++n) {
-        const Prim<R> q = primitives(u[n], gm1);
+        const Prim<NV, R> q = primitives(u[n], gm1);
         f[n] = scale(cx, flux_from<0>(u[n], q));
         g[n] = scale(cy, flux_from<1>(u[n], q));
         h[n] = scale(cz, flux_from<2>(u[n], q));
     }
     // Eq. B.2 without sources
-    const V<R> q11 = u[1] + 0.5 * (f[3] - f[1]) + 0.5 * (g[5] - g[1]) + 0.5 * (h[7] - h[1]);
-    const V<R> q12 = u[2] + (36.0 * f[1] - 24.0 * f[2] - 12.0 * f[3] - 36.0 * g[1] + 24.0 * g[2] + 24.0 * g[4] +
+    const Vec<NV, R> q11 = u[1] + 0.5 * (f[3] - f[1]) + 0.5 * (g[5] - g[1]) + 0.5 * (h[7] - h[1]);
+    const Vec<NV, R> q12 = u[2] + (36.0 * f[1] - 24.0 * f[2] - 12.0 * f[3] - 36.0 * g[1] + 24.0 * g[2] + 24.0 * g[4] +
                              12.0 * g[5] - 24.0 * g[10] - 36.0 * h[1] + 24.0 * h[2] + 24.0 * h[6] + 12.0 * h[7] -
                              24.0 * h[9]) / 24.0;
-    const V<R> q13 = u[4] + (-36.0 * f[1] + 24.0 * f[2] + 12.0 * f[3] + 24.0 * f[4] - 24.0 * f[10] + 36.0 * g[1] -
+    const Vec<NV, R> q13 = u[4] + (-36.0 * f[1] + 24.0 * f[2] + 12.0 * f[3] + 24.0 * f[4] - 24.0 * f[10] + 36.0 * g[1] -
                              24.0 * g[4] - 12.0 * g[5] - 36.0 * h[1] + 24.0 * h[4] + 24.0 * h[6] + 12.0 * h[7] -
                              24.0 * h[8]) / 24.0;
-    const V<R> q14 = u[6] + (-36.0 * f[1] + 24.0 * f[2] + 12.0 * f[3] + 24.0 * f[6] - 24.0 * f[9] - 36.0 * g[1] +
+    const Vec<NV, R> q14 = u[6] + (-36.0 * f[1] + 24.0 * f[2] + 12.0 * f[3] + 24.0 * f[6] - 24.0 * f[9] - 36.0 * g[1] +
                              24.0 * g[4] + 12.0 * g[5] + 24.0 * g[6] - 24.0 * g[8] + 36.0 * h[1] - 24.0 * h[6] -
                              12.0 * h[7]) / 24.0;
-    const V<R> q15 = u[1] + (-60.0 * f[1] + 30.0 * f[2] + 30.0 * f[3] - 60.0 * g[1] + 30.0 * g[4] + 30.0 * g[5] -
+    const Vec<NV, R> q15 = u[1] + (-60.0 * f[1] + 30.0 * f[2] + 30.0 * f[3] - 60.0 * g[1] + 30.0 * g[4] + 30.0 * g[5] -
                              60.0 * h[1] + 30.0 * h[6] + 30.0 * h[7]) / 30.0;
     // initial guess: no time evolution (node values at tau > 0 equal those at tau = 0)
-    V<R> u11 = u[1], u12 = u[2], u13 = u[4], u14 = u[6], u15 = u[1];
+    Vec<NV, R> u11 = u[1], u12 = u[2], u13 = u[4], u14 = u[6], u15 = u[1];
     for (int it = 0; it < n_iter; ++it) {
         // Eq. B.3 without sources (node 15 serves only source terms)
-        const Prim<R> p11 = primitives(u11, gm1);
-        const V<R> q1 = 0.5 * (scale(cx, flux_from<0>(u11, p11) - flux<0>(u12, gm1)) +
+        const Prim<NV, R> p11 = primitives(u11, gm1);
+        const Vec<NV, R> q1 = 0.5 * (scale(cx, flux_from<0>(u11, p11) - flux<0>(u12, gm1)) +
                                scale(cy, flux_from<1>(u11, p11) - flux<1>(u13, gm1)) +
                                scale(cz, flux_from<2>(u11, p11) - flux<2>(u14, gm1)));
         u11 = q11 + q1;
@@ -143,24 +142,78 @@ ADER_DEV void predict_nodal(V<R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
 // average of the physical normal flux: composing Eq. D.9 with D.10 gives
 // <F> = (F1 + F6 + F7 + F8 + F9 + F10) / 6 over the facial nodes of Eq. D.6
 // (the four corner nodes enter only the edge averages).
-template <int D, class R>
-ADER_DEV void face(const V<R>* p, R gm1, V<R>& ub, V<R>& avg, V<R>& Fa) {
+template <int D, int NV, class R>
+ADER_DEV void face(const Vec<NV, R>* p, R gm1, Vec<NV, R>& ub, Vec<NV, R>& avg, Vec<NV, R>& Fa) {
     ub = p[1] + 0.5 * (p[2] + p[11]) + 0.25 * (p[12] + p[13]) + (2.0 * p[5] - p[6] - p[7]) / 12.0;
     avg = ub + (p[6] + p[7] + p[12]) / 12.0;
     // Eq. D.8
-    const V<R> q1 = 0.5 * p[11] + 0.25 * (p[12] + p[13]);
-    const V<R> t1 = p[1] + 0.5 * p[2] + (2.0 * p[5] - p[6] - p[7]) / 12.0;
-    const V<R> t2 = t1 + 0.5 * (p[3] + p[4]) + 0.25 * (p[6] + p[7] + p[8] + p[9] + p[10]);
-    const V<R> t3 = t2 - p[3] - 0.5 * (p[8] + p[9]);
-    const V<R> t4 = t2 - p[4] - 0.5 * (p[9] + p[10]);
-    const V<R> t5 = t4 - p[3] - 0.5 * (p[8] - p[9]);
-    const V<R> t6 = 0.5 * (t2 + t4) + q1 + 0.25 * (p[14] - p[7]);
-    const V<R> t7 = 0.5 * (t3 + t5) + q1 - 0.25 * (p[7] + p[14]);
-    const V<R> t8 = 0.5 * (t2 + t3) + q1 + 0.25 * (p[15] - p[6]);
-    const V<R> t9 = 0.5 * (t4 + t5) + q1 - 0.25 * (p[6] + p[15]);
-    const V<R> t10 = t1 + p[11] + p[12] + 0.5 * p[13];
+    const Vec<NV, R> q1 = 0.5 * p[11] + 0.25 * (p[12] + p[13]);
+    const Vec<NV, R> t1 = p[1] + 0.5 * p[2] + (2.0 * p[5] - p[6] - p[7]) / 12.0;
+    const Vec<NV, R> t2 = t1 + 0.5 * (p[3] + p[4]) + 0.25 * (p[6] + p[7] + p[8] + p[9] + p[10]);
+    const Vec<NV, R> t3 = t2 - p[3] - 0.5 * (p[8] + p[9]);
+    const Vec<NV, R> t4 = t2 - p[4] - 0.5 * (p[9] + p[10]);
+    const Vec<NV, R> t5 = t4 - p[3] - 0.5 * (p[8] - p[9]);
+    const Vec<NV, R> t6 = 0.5 * (t2 + t4) + q1 + 0.25 * (p[14] - p[7]);
+    const Vec<NV, R> t7 = 0.5 * (t3 + t5) + q1 - 0.25 * (p[7] + p[14]);
+    const Vec<NV, R> t8 = 0.5 * (t2 + t3) + q1 + 0.25 * (p[15] - p[6]);
+    const Vec<NV, R> t9 = 0.5 * (t4 + t5) + q1 - 0.25 * (p[6] + p[15]);
+    const Vec<NV, R> t10 = t1 + p[11] + p[12] + 0.5 * p[13];
     Fa = (flux<D>(t1, gm1) + flux<D>(t6, gm1) + flux<D>(t7, gm1) + flux<D>(t8, gm1) + flux<D>(t9, gm1) +
           flux<D>(t10, gm1)) / 6.0;
+}
+
+// MHD face: all ten facial nodes of Eq. D.6; edge averages by Eq. 63 (<u>)
+// and Eqs. D.9-D.10 (<F>) for the field component of each edge's EMF
+// (slots t1+, t1-, t2+, t2-; component 5 + t1 / 5 + t2).
+template <int D, class R>
+ADER_DEV void face_mhd(const Vec<8, R>* p, R gm1, Vec<8, R>& ub, Vec<8, R>& avg, Vec<8, R>& Fa, R* eu, R* ef) {
+    constexpr int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
+    ub = p[1] + 0.5 * (p[2] + p[11]) + 0.25 * (p[12] + p[13]) + (2.0 * p[5] - p[6] - p[7]) / 12.0;
+    avg = ub + (p[6] + p[7] + p[12]) / 12.0;
+    Vec<8, R> t[11];
+    const Vec<8, R> q1 = 0.5 * p[11] + 0.25 * (p[12] + p[13]);
+    t[1] = p[1] + 0.5 * p[2] + (2.0 * p[5] - p[6] - p[7]) / 12.0;
+    t[2] = t[1] + 0.5 * (p[3] + p[4]) + 0.25 * (p[6] + p[7] + p[8] + p[9] + p[10]);
+    t[3] = t[2] - p[3] - 0.5 * (p[8] + p[9]);
+    t[4] = t[2] - p[4] - 0.5 * (p[9] + p[10]);
+    t[5] = t[4] - p[3] - 0.5 * (p[8] - p[9]);
+    t[6] = 0.5 * (t[2] + t[4]) + q1 + 0.25 * (p[14] - p[7]);
+    t[7] = 0.5 * (t[3] + t[5]) + q1 - 0.25 * (p[7] + p[14]);
+    t[8] = 0.5 * (t[2] + t[3]) + q1 + 0.25 * (p[15] - p[6]);
+    t[9] = 0.5 * (t[4] + t[5]) + q1 - 0.25 * (p[6] + p[15]);
+    t[10] = t[1] + p[11] + p[12] + 0.5 * p[13];
+    Vec<8, R> F[11];
+#pragma unroll
+    for (int n = 1; n <= 10; ++n) F[n] = flux<D>(t[n], gm1);
+    Fa = (F[1] + F[6] + F[7] + F[8] + F[9] + F[10]) / 6.0;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int c = 5 + (s == 0 ? T1 : T2);
+        auto f = [&](int n) { return F[n][c]; };
+        // Eq. D.9 (the modes the edge averages need)
+        const R q2 = R(0.5) * (f(2) + f(4) - R(4) * f(1) + f(3) + f(5));
+        const R q3 = f(6) + f(7) - f(8) - f(9);
+        const R m1 = R(2.0 / 3.0) * (f(1) + R(0.125) * (f(2) + f(3) + f(4) + f(5)));
+        const R m2 = R(0.5) * (f(2) + f(4) - f(3) - f(5));
+        const R m3 = R(0.5) * (f(2) + f(3) - f(4) - f(5));
+        const R m4 = q2 + q3, m5 = q2 - q3;
+        const R m8 = R(2) * (f(1) + f(10)) - (f(6) + f(7) + f(8) + f(9)) + q2;
+        const R m7 = f(10) - f(1) - m8;
+        const R m9 = R(2) * (f(6) - f(7) - m2);
+        const R m10 = R(2) * (f(8) - f(9) - m3);
+        // Eq. D.10
+        const R af = m1 + R(0.5) * m7 + m8 * R(1.0 / 3.0);
+        const R qs = s == 0 ? R(0.5) * m2 + R(0.25) * m9 : R(0.5) * m3 + R(0.25) * m10;
+        const R plus = af + qs + (s == 0 ? m4 : m5) * R(1.0 / 6.0);
+        ef[2 * s] = plus;
+        ef[2 * s + 1] = plus - R(2) * qs;
+        // Eq. 63
+        const R qu = s == 0 ? R(0.5) * p[3][c] + R(0.25) * (p[8][c] + p[14][c])
+                            : R(0.5) * p[4][c] + R(0.25) * (p[10][c] + p[15][c]);
+        const R up = avg[c] + (s == 0 ? p[6][c] : p[7][c]) * R(1.0 / 6.0) + qu;
+        eu[2 * s] = up;
+        eu[2 * s + 1] = up - R(2) * qu;
+    }
 }
 
 }  // namespace o3

@@ -83,7 +83,12 @@ def sod_planar(n, gamma=1.4, normal=(1, 1, 0), left=(1.0, 1.0), right=(0.125, 0.
     def ind(x, y, z):
         s = normal[0] * x + normal[1] * y + normal[2] * z
         return ((s - np.floor(s)) < 0.5).astype(np.float64)
-    f = subsample_average(ind, n, sub)
+    shape = grid_shape(n)
+    if normal[2] == 0:
+        # uniform in z: average over one z-layer and repeat it
+        f = np.broadcast_to(subsample_average(ind, (1,) + shape[1:], sub), shape).copy()
+    else:
+        f = subsample_average(ind, shape, sub)
     rho = right[0] + (left[0] - right[0]) * f
     P = right[1] + (left[1] - right[1]) * f
     z = np.zeros_like(rho)

@@ -210,7 +210,7 @@ def test_full_size_sampled_parity(ader, fp32):
     depends on zones at most 4 away)."""
     import torch
     n = 256
-    U = inputs.sod_planar(n, sub=2)
+    U = inputs.sod_planar(n)
     s = ader.Solver((n, n, n), order=3, form="nodal", solver="hll", fp32=fp32)
     d = to_dev(U)
     dt = torch.zeros(1, dtype=torch.float64, device="cuda")
