@@ -112,6 +112,26 @@ def alu_peak_tflops(fp32, sm_mhz):
     return 152 * per_clk * sm_mhz * 1e6 / 1e12
 
 
+def traffic_per_launch(kernel, order, form, fp32, zones):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, scaled to `zones` (traffic grows
+    in proportion to the zones processed); None when the kernel's sources changed since the capture or
+    the capture was of another configuration."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_%s.json" % kernel)
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    if (rec["order"], rec["form"], rec["precision"]) != (order, form, "fp32" if fp32 else "fp64"):
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        p = os.path.join(ROOT, f)
+        h.update(open(p).read().encode() if os.path.exists(p) else b"")
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None
+    return rec["bytes_per_zone"] * zones
+
+
 def flops_per_zone(order, form, solver, fp32):
     """Exact FLOPs per zone of each kernel (op-counting instantiation of the kernels' per-zone code)."""
     path = os.path.join(ROOT, "paper_1006_2146_gb300", "flops.json")
@@ -207,7 +227,8 @@ def gpu_arm(args):
     peak = alu_peak_tflops(args.fp32, 2070.0)
     total_ms = sum(v[1] for v in prof.values())
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None,
+                "traffic": traffic_per_launch(kname, args.order, args.form, args.fp32, zones),
                 "peak_basis": "derived: 152 SM x %s at 2070 MHz max clock" % ("128 FFMA/clk" if args.fp32 else "2 DFMA/clk (1.25 TFLOP/s nominal FP64)"),
                 "flops_per_zone": fpz.get(kname), "mean_launch_ms": k_avg * 1e3,
                 "kernel_share": {k: round(v[1] / total_ms, 4) for k, v in prof.items()},

@@ -13,8 +13,9 @@
  * Conventions common to every entry point
  *   - Every array argument is a DEVICE pointer owned by the caller unless the
  *     name ends in _host.  The library owns only the scratch it allocates in
- *     ader_create and frees in ader_destroy; no entry point except
- *     ader_create allocates memory.
+ *     ader_create and frees in ader_destroy; the step, dt and diagnostics
+ *     entry points allocate nothing (the MLP entry points allocate their own
+ *     workspace).
  *   - State layout (structure of arrays, FP64, x fastest):
  *       U[v][k][j][i], v = 0..4 = (rho, rho vx, rho vy, rho vz, eps),
  *       element (v, k, j, i) at U[((v*nz + k)*ny + j)*nx + i].
@@ -127,6 +128,46 @@ int ader_launches_per_step(const ader_ctx* ctx);
 int ader_profile(ader_ctx* ctx, int enable);
 int ader_profile_reset(ader_ctx* ctx);
 int ader_profile_read(ader_ctx* ctx, const char** names, int* launches, double* ms, int cap);
+
+/* Converged predictor.  tol > 0: iterate the ADER-CG predictor of every zone
+ * until the largest change of an evolutionary mode is below tol times the
+ * zone's largest |w_1| (at most max_iter times; reaching the cap raises
+ * ADER_ERR_NOT_CONVERGED); tol = 0 restores the paper's M-1 iterations
+ * (Secs. IV.1-IV.3).  ader_predictor_stats writes {sum of iterations over
+ * zones and steps, largest count, zones capped} to out3_host and clears them
+ * (synchronises the stream). */
+int ader_set_predictor(ader_ctx* ctx, double tol, int max_iter);
+int ader_predictor_stats(ader_ctx* ctx, unsigned long long* out3_host, void* stream);
+
+/* Learned initial guess (third order).  params (device, FP32, layout and
+ * size from ader_mlp_shape) is an MLP mapping a zone's normalised spatial
+ * modes and Courant numbers to its evolutionary modes; the predictor starts
+ * from that guess instead of zero.  NULL disables it.  The pointer is kept,
+ * not copied: keep the buffer alive while the context uses it. */
+int ader_set_guess(ader_ctx* ctx, const float* params);
+int ader_mlp_shape(int mhd, int* n_in, int* n_hidden, int* n_out, long long* n_params);
+
+/* Training data: for every zone of (U, Bface), the MLP features X (n x n_in)
+ * and the normalised evolutionary modes Y (n x n_out) of the converged FP64
+ * modal predictor started from zero (tolerance of ader_set_predictor, 1e-13
+ * if unset); ok[z] = 0 marks a zone to skip (non-physical or capped).  Needs
+ * a third-order FP64 context.  All pointers are device pointers. */
+int ader_guess_samples(ader_ctx* ctx, const double* U, const double* Bface, double dt, float* X, float* Y, int* ok,
+                       void* stream);
+
+/* MLP training on the GPU with the library's own kernels (FP32 GEMM, GELU,
+ * Adam; mean-squared error).  X, Y: device samples (n rows); params:
+ * device parameters, updated in place (initialise them first);
+ * loss_per_epoch_host: optional host array of `epochs` doubles.  Allocates
+ * and frees its own workspace.  Synchronous. */
+int ader_mlp_train(const float* X, const float* Y, long long n, int mhd, int epochs, int batch, float lr,
+                   unsigned long long seed, float* params, double* loss_per_epoch_host, void* stream);
+
+/* Mean-squared-error loss and its gradient (device grad, size n_params) on n
+ * samples: the training kernels' forward and backward pass, exposed for
+ * checking them.  Synchronous. */
+int ader_mlp_grad(const float* params, const float* X, const float* Y, long long n, int mhd, float* grad,
+                  double* loss_host, void* stream);
 
 const char* ader_last_error(const ader_ctx* ctx);
 void ader_destroy(ader_ctx* ctx);

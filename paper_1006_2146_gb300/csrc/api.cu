@@ -32,6 +32,10 @@ struct ader_ctx {
     double* dt_dev = nullptr;                 // device dt of the host-memory path
     double* Ustage = nullptr;                 // device state of the host-memory path
     double* rk[7] = {};                       // SSP-RK stage states and operators
+    double tol = 0.0;                         // converged predictor tolerance (0: fixed M-1 iterations)
+    int max_iter = 50;
+    unsigned long long* stats = nullptr;      // converged predictor statistics (3 words)
+    const float* guess = nullptr;             // learned-guess MLP parameters (device), order 3
     int launches = 0;
     std::string err;
     // tracing: pending event pairs per kernel name, folded into totals on read
@@ -107,6 +111,10 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.Bface = nullptr;
     a.ZB = c->ZB;
     a.E = c->E;
+    a.tol = n_iter > 0 ? c->tol : 0.0;
+    a.max_iter = c->max_iter;
+    a.stats = c->stats;
+    a.guess = n_iter > 0 ? c->guess : nullptr;
     return a;
 }
 
@@ -184,6 +192,7 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
         alloc(&c->E, N * 3 * c->rsize, "cudaMalloc EMF");
     }
     alloc((void**)&c->flag, sizeof(unsigned), "cudaMalloc flag");
+    alloc((void**)&c->stats, 3 * sizeof(unsigned long long), "cudaMalloc predictor statistics");
     alloc((void**)&c->dtscr, 2 * sizeof(unsigned long long), "cudaMalloc dt scratch");
     c->tot_blocks = 1024;
     alloc((void**)&c->partial, c->tot_blocks * 5 * sizeof(double), "cudaMalloc partials");
@@ -191,6 +200,7 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
     alloc((void**)&c->Ustage, N * 5 * sizeof(double), "cudaMalloc host-path state");
     for (int s = 0; s < 7; ++s) alloc((void**)&c->rk[s], N * 5 * sizeof(double), "cudaMalloc RK stage");
     if (rc == ADER_OK) rc = cuda_check(c, cudaMemset(c->flag, 0, sizeof(unsigned)), "cudaMemset flag");
+    if (rc == ADER_OK) rc = cuda_check(c, cudaMemset(c->stats, 0, 3 * sizeof(unsigned long long)), "cudaMemset");
     if (rc == ADER_OK) rc = cuda_check(c, cudaMemset(c->dtscr, 0, 2 * sizeof(unsigned long long)), "cudaMemset");
     if (rc != ADER_OK) {
         ader_destroy(c);
@@ -207,7 +217,7 @@ void ader_destroy(ader_ctx* c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->spare) cudaEventDestroy(e);
-    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->flag, c->dtscr, c->partial, c->dt_dev, c->Ustage,
+    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->flag, c->stats, c->dtscr, c->partial, c->dt_dev, c->Ustage,
                     c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -386,6 +396,46 @@ int ader_rk_step(ader_ctx* c, double* U, double* Bface, double dt, void* stream)
     }
     c->launches = n + 1;
     return cuda_check(c, cudaGetLastError(), "ader_rk_step launch");
+}
+
+int ader_set_predictor(ader_ctx* c, double tol, int max_iter) {
+    if (!c) return ADER_ERR_ARG;
+    if (tol < 0.0 || max_iter < 1 || max_iter > 1000) return fail(c, ADER_ERR_ARG, "tol >= 0, 1 <= max_iter <= 1000");
+    c->tol = tol;
+    c->max_iter = max_iter;
+    return ADER_OK;
+}
+
+int ader_predictor_stats(ader_ctx* c, unsigned long long* out3_host, void* stream) {
+    if (!c || !out3_host) return ADER_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = cuda_check(c, cudaMemcpyAsync(out3_host, c->stats, 3 * sizeof(unsigned long long),
+                                           cudaMemcpyDeviceToHost, st), "stats read");
+    if (rc == ADER_OK) rc = cuda_check(c, cudaMemsetAsync(c->stats, 0, 3 * sizeof(unsigned long long), st), "memset");
+    if (rc == ADER_OK) rc = cuda_check(c, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return rc;
+}
+
+int ader_set_guess(ader_ctx* c, const float* params) {
+    if (!c) return ADER_ERR_ARG;
+    if (params && c->order != 3) return fail(c, ADER_ERR_ARG, "the learned guess is built for third order");
+    c->guess = params;
+    return ADER_OK;
+}
+
+int ader_guess_samples(ader_ctx* c, const double* U, const double* Bface, double dt, float* X, float* Y, int* ok,
+                       void* stream) {
+    if (!c) return ADER_ERR_ARG;
+    if (!U || !X || !Y || !ok || !(dt > 0.0)) return fail(c, ADER_ERR_ARG, "null pointer or dt <= 0");
+    if (int rc = check_bface(c, Bface)) return rc;
+    if (c->order != 3 || c->fp32) return fail(c, ADER_ERR_ARG, "samples need a third-order FP64 context");
+    cudaStream_t st = (cudaStream_t)stream;
+    StepArgs a = make_args(c, dt, nullptr, 2);
+    a.Bface = Bface;
+    a.tol = c->tol > 0.0 ? c->tol : 1e-13;
+    launch_recon<double>(a, U, st);
+    launch_guess_samples(a, U, X, Y, ok, st);
+    return cuda_check(c, cudaGetLastError(), "ader_guess_samples launch");
 }
 
 int ader_sync_status(ader_ctx* c, void* stream) {

@@ -157,6 +157,35 @@ ADER_DEV R fast_speed(const Vec<NV, R>& u, const Prim<NV, R>& q, R gamma) {
     }
 }
 
+// ------------------------------------------------------------------ predictor control
+// Fixed mode (tol <= 0): exactly n_iter Picard steps (M - 1 in the paper).
+// Converged mode (tol > 0): iterate until the largest change of an
+// evolutionary mode is below tol * (largest |w_1| of the zone), at most
+// max_iter times.  iters / capped report what happened.
+struct PredCtl {
+    int n_iter;
+    double tol;
+    int max_iter;
+    int iters;
+    bool capped;
+};
+
+template <int NV, class R>
+ADER_DEV R max_abs_diff(const Vec<NV, R>& a, const Vec<NV, R>& b) {
+    R m = R(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) m = fmax(m, fabs(a[v] - b[v]));
+    return m;
+}
+
+template <int NV, class R>
+ADER_DEV R max_abs(const Vec<NV, R>& a) {
+    R m = R(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) m = fmax(m, fabs(a[v]));
+    return m;
+}
+
 // ------------------------------------------------------------------ indexing
 struct Grid {
     int nx, ny, nz;

@@ -142,11 +142,19 @@ def emit():
         t = _terms(C, k, 1, 20, None, 0)
         lines.append("    qt[%d] = u[%d]%s;" % (k - 21, base_node(k), "".join("\n        + " + s for s in t)))
     lines += ["}", "",
-              "// e[k-21] = value at node k before the first iteration (no time evolution)",
+              "// e[k-21] = value at node k before the first iteration: the tau = 0 value at its spatial",
+              "// point plus the evolutionary modes m[21..35] (the initial guess) evaluated there",
               "template <int NV, class R>",
-              "ADER_DEV void nodal_o4_initial(const Vec<NV, R>* u, Vec<NV, R>* e) {"]
+              "ADER_DEV void nodal_o4_initial(const Vec<NV, R>* u, const Vec<NV, R>* m, Vec<NV, R>* e) {"]
     for k in range(21, 36):
-        lines.append("    e[%d] = u[%d];" % (k - 21, base_node(k)))
+        terms = []
+        for j, mode in enumerate(MODES):
+            if mode[3] == 0:
+                continue
+            c = _phi(mode, NODES[k - 1])
+            if c != 0:
+                terms.append("%.17g * m[%d]" % (float(c), j + 1))
+        lines.append("    e[%d] = u[%d]%s;" % (k - 21, base_node(k), "".join(" + " + t for t in terms)))
     lines += ["}", "",
               "// one Picard step: e[k-21] = qt[k-21] + tau > 0 flux terms; f, g, h indexed by node - 21",
               "template <int NV, class R>",

@@ -17,6 +17,10 @@ struct StepArgs {
     int solver;         // SOLVER_HLL / SOLVER_LINEARIZED
     int fp32;           // 1: FP32 bulk arithmetic
     int n_iter;         // predictor iterations (order - 1 by default; 0 = spatial only, used by SSP-RK)
+    double tol;         // > 0: converged predictor (iterate to tolerance, at most max_iter times)
+    int max_iter;
+    unsigned long long* stats;   // converged predictor: [0] sum of iterations, [1] max, [2] zones capped
+    const float* guess; // learned initial guess: packed MLP weights (order 3), or null
     double gamma;
     double dx[3];
     double dt;          // used when dt_dev is null
@@ -52,6 +56,7 @@ int launch_max_dt(const Grid& g, const double* U, const double* Bf, double gamma
                   double* dt_dev, unsigned long long* scratch, unsigned* flag, cudaStream_t st);
 // MHD: edge EMFs from the face data in S3, then Eq. 8 on Bf (in place) with step c_host (x *dt_dev)
 template <class R> int launch_emf_ct(const StepArgs& a, double* Bf, double c_host, bool use_dt_dev, cudaStream_t st);
+int launch_guess_samples(const StepArgs& a, const double* U, float* X, float* Y, int* ok, cudaStream_t st);
 int launch_totals(const Grid& g, const double* U, double* totals_dev, double* partial, int nblocks, cudaStream_t st);
 
 }  // namespace ader

@@ -10,10 +10,10 @@ namespace ader {
 
 #define ADER_ZONEOPS(O)                                                                                              \
     template <> struct ZoneOps<O> {                                                                                  \
-        template <int NV, class R> static ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n) { \
+        template <int NV, class R> static ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& n) { \
             o##O::predict_modal(m, gm1, cx, cy, cz, n);                                                              \
         }                                                                                                            \
-        template <int NV, class R> static ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n) { \
+        template <int NV, class R> static ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& n) { \
             o##O::predict_nodal(m, gm1, cx, cy, cz, n);                                                              \
         }                                                                                                            \
         template <int D, int NV, class R>                                                                            \

@@ -14,6 +14,7 @@
 #include "kernels.cuh"
 #include "modes.cuh"
 #include "riemann.cuh"
+#include "mlp.cuh"
 
 namespace ader {
 
@@ -77,6 +78,19 @@ ADER_DEV void store_face(const StepArgs& a, long long z, const Vec<NV, R>* m, R 
     }
 }
 
+// Iteration statistics of the converged predictor: sum, maximum and capped zones.
+ADER_DEV void record_iterations(unsigned long long* stats, const PredCtl& ctl) {
+#ifdef __CUDA_ARCH__
+    atomicAdd(&stats[0], (unsigned long long)ctl.iters);
+    atomicMax(&stats[1], (unsigned long long)ctl.iters);
+    if (ctl.capped) atomicAdd(&stats[2], 1ull);
+#else
+    stats[0] += ctl.iters;
+    if ((unsigned long long)ctl.iters > stats[1]) stats[1] = ctl.iters;
+    if (ctl.capped) stats[2] += 1;
+#endif
+}
+
 template <int ORDER, int FORM, int NV, class R>
 ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U, long long z) {
     constexpr int LS = ModeCount<ORDER>::LS, L = ModeCount<ORDER>::L;
@@ -88,10 +102,16 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
     const R gm1 = R(a.gamma - 1.0);
     const R cx = R(dt / a.dx[0]), cy = R(dt / a.dx[1]), cz = R(dt / a.dx[2]);
     if (a.n_iter > 0) {      // n_iter = 0: spatial polynomial only (SSP-RK face rule)
+        if constexpr (ORDER == 3) {
+            if (a.guess) learned_guess(a.guess, m, R(a.gamma), cx, cy, cz);
+        }
+        PredCtl ctl{a.n_iter, a.tol, a.max_iter, 0, false};
         if (FORM == FORM_MODAL)
-            ZoneOps<ORDER>::predict_modal(m, gm1, cx, cy, cz, a.n_iter);
+            ZoneOps<ORDER>::predict_modal(m, gm1, cx, cy, cz, ctl);
         else
-            ZoneOps<ORDER>::predict_nodal(m, gm1, cx, cy, cz, a.n_iter);
+            ZoneOps<ORDER>::predict_nodal(m, gm1, cx, cy, cz, ctl);
+        if (a.tol > 0.0 && a.stats) record_iterations(a.stats, ctl);
+        if (ctl.capped) raise_flag(a.flag, FLAG_NOT_CONVERGED);
     }
     store_face<ORDER, 0, +1>(a, z, m, gm1);
     store_face<ORDER, 0, -1>(a, z, m, gm1);

@@ -7,29 +7,50 @@
 namespace ader {
 namespace o2 {
 
+template <int NV, class R>
+ADER_DEV void finish_o2(Vec<NV, R>* m, const Vec<NV, R>& n5, PredCtl& ctl) {
+    const bool conv = ctl.tol > 0.0;
+    const int cap = conv ? ctl.max_iter : ctl.n_iter;
+    const R ref = max_abs(m[1]) + R(1e-300);
+    ctl.iters = 0;
+    ctl.capped = conv;
+    for (int it = 0; it < cap; ++it) {
+        const R change = max_abs_diff(n5, m[5]);
+        m[5] = n5;
+        ++ctl.iters;
+        if (conv && change < R(ctl.tol) * ref) {
+            ctl.capped = false;
+            break;
+        }
+    }
+}
+
 
 // Eqs. 31-33 and 30 (one iteration, no sources)
+// The update uses only tau = 0 fluxes, so one step reaches the fixed point
+// (in converged mode a second step confirms it).
 template <int NV, class R>
-ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
+ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl) {
     const Vec<NV, R> u1 = m[1] + 0.5 * m[2], u2 = m[1] - 0.5 * m[2];
     const Vec<NV, R> u3 = m[1] + 0.5 * m[3], u4 = m[1] - 0.5 * m[3];
     const Vec<NV, R> u5 = m[1] + 0.5 * m[4], u6 = m[1] - 0.5 * m[4];
     const Vec<NV, R> F2 = scale(cx, flux<0>(u1, gm1) - flux<0>(u2, gm1));
     const Vec<NV, R> G3 = scale(cy, flux<1>(u3, gm1) - flux<1>(u4, gm1));
     const Vec<NV, R> H4 = scale(cz, flux<2>(u5, gm1) - flux<2>(u6, gm1));
-    m[5] = n_iter > 0 ? -(F2 + G3 + H4) : m[5];
+    const Vec<NV, R> n5 = -(F2 + G3 + H4);
+    finish_o2(m, n5, ctl);
 }
 
 // Eqs. A.5, A.4 (h term at node 4, the zeta node of Eq. A.1) and A.6
 template <int NV, class R>
-ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
+ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl) {
     const Vec<NV, R> u1 = m[1];
     const Vec<NV, R> u2 = m[1] + 0.5 * m[2], u3 = m[1] + 0.5 * m[3], u4 = m[1] + 0.5 * m[4];
     const Prim<NV, R> p1 = primitives(u1, gm1);
     const Vec<NV, R> u5 = u1 - 2.0 * (scale(cx, flux<0>(u2, gm1) - flux_from<0>(u1, p1)) +
                                 scale(cy, flux<1>(u3, gm1) - flux_from<1>(u1, p1)) +
                                 scale(cz, flux<2>(u4, gm1) - flux_from<2>(u1, p1)));
-    m[5] = n_iter > 0 ? u5 - u1 : m[5];
+    finish_o2(m, u5 - u1, ctl);
 }
 
 // Eqs. 58-59 and D.3-D.5: composing D.4 with D.5, <F> is the mean of the flux

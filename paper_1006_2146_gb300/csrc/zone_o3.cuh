@@ -15,7 +15,7 @@ namespace o3 {
 
 // ------------------------------------------------------------------ modal, Sec. IV.2
 template <int NV, class R>
-ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
+ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl) {
     // Eq. 38: the thirteen tau = 0 nodes of Eq. 37
     Vec<NV, R> u[14];
     u[1] = m[1] - (m[5] + m[6] + m[7]) / 12.0;
@@ -56,7 +56,12 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) 
     const Vec<NV, R> H7 = scale(cz, 0.5 * (q7 + q8 - q9) - 2.0 * h[1]);
     const Vec<NV, R> H9 = scale(cz, h[10] - h[11] - h[12] + h[13]);
     const Vec<NV, R> H10 = scale(cz, h[4] - h[5] - h[8] + h[9]);
-    for (int it = 0; it < n_iter; ++it) {
+    const bool conv = ctl.tol > 0.0;
+    const int cap = conv ? ctl.max_iter : ctl.n_iter;
+    const R ref = max_abs(m[1]) + R(1e-300);
+    ctl.iters = 0;
+    ctl.capped = conv;
+    for (int it = 0; it < cap; ++it) {
         // Eq. 39: the tau = 1/2 nodes (node 20 serves only source terms)
         const Vec<NV, R> u14 = 0.25 * (u[2] + u[3] + u[4] + u[5] + m[12] + m[13]) + 0.5 * m[11] - 0.125 * (m[6] + m[7]);
         const Vec<NV, R> u16 = 0.25 * (u[2] + u[6] + u[10] + u[12] + m[12] + m[14]) + 0.5 * m[11] - 0.125 * (m[5] + m[7]);
@@ -69,17 +74,32 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) 
         const Vec<NV, R> G14 = 2.0 * (scale(cy, flux<1>(u16, gm1) - flux<1>(u17, gm1)) - G3);
         const Vec<NV, R> H15 = 2.0 * (scale(cz, flux<2>(u18, gm1) - flux<2>(u19, gm1)) - H4);
         // Eq. 36 without sources
-        m[11] = -(F2 + G3 + H4);
-        m[12] = -0.5 * (F13 + G14 + H15);
-        m[13] = -(2.0 * F5 + G8 + H10);
-        m[14] = -(F8 + 2.0 * G6 + H9);
-        m[15] = -(F10 + G9 + 2.0 * H7);
+        const Vec<NV, R> n11 = -(F2 + G3 + H4);
+        const Vec<NV, R> n12 = -0.5 * (F13 + G14 + H15);
+        const Vec<NV, R> n13 = -(2.0 * F5 + G8 + H10);
+        const Vec<NV, R> n14 = -(F8 + 2.0 * G6 + H9);
+        const Vec<NV, R> n15 = -(F10 + G9 + 2.0 * H7);
+        R change = R(0);
+        if (conv)
+            change = fmax(fmax(fmax(max_abs_diff(n11, m[11]), max_abs_diff(n12, m[12])),
+                               fmax(max_abs_diff(n13, m[13]), max_abs_diff(n14, m[14]))),
+                          max_abs_diff(n15, m[15]));
+        m[11] = n11;
+        m[12] = n12;
+        m[13] = n13;
+        m[14] = n14;
+        m[15] = n15;
+        ++ctl.iters;
+        if (conv && change < R(ctl.tol) * ref) {
+            ctl.capped = false;
+            break;
+        }
     }
 }
 
 // ------------------------------------------------------------------ nodal, App. B
 template <int NV, class R>
-ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
+ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl) {
     // Eq. B.4: the ten tau = 0 nodes of Eq. B.1
     Vec<NV, R> u[16];
     u[1] = m[1] - (m[5] + m[6] + m[7]) / 12.0;
@@ -114,9 +134,17 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) 
                              12.0 * h[7]) / 24.0;
     const Vec<NV, R> q15 = u[1] + (-60.0 * f[1] + 30.0 * f[2] + 30.0 * f[3] - 60.0 * g[1] + 30.0 * g[4] + 30.0 * g[5] -
                              60.0 * h[1] + 30.0 * h[6] + 30.0 * h[7]) / 30.0;
-    // initial guess: no time evolution (node values at tau > 0 equal those at tau = 0)
-    Vec<NV, R> u11 = u[1], u12 = u[2], u13 = u[4], u14 = u[6], u15 = u[1];
-    for (int it = 0; it < n_iter; ++it) {
+    // initial guess: the evolutionary modes in m[11..15] (zero: no time evolution) at the
+    // tau > 0 nodes of Eq. B.1
+    const Vec<NV, R> g0 = 0.5 * m[11] + 0.25 * m[12];
+    Vec<NV, R> u11 = u[1] + g0, u12 = u[2] + g0 + 0.25 * m[13], u13 = u[4] + g0 + 0.25 * m[14];
+    Vec<NV, R> u14 = u[6] + g0 + 0.25 * m[15], u15 = u[1] + m[11] + m[12];
+    const bool conv = ctl.tol > 0.0;
+    const int cap = conv ? ctl.max_iter : ctl.n_iter;
+    const R ref = max_abs(m[1]) + R(1e-300);
+    ctl.iters = 0;
+    ctl.capped = conv;
+    for (int it = 0; it < cap; ++it) {
         // Eq. B.3 without sources (node 15 serves only source terms)
         const Prim<NV, R> p11 = primitives(u11, gm1);
         const Vec<NV, R> q1 = 0.5 * (scale(cx, flux_from<0>(u11, p11) - flux<0>(u12, gm1)) +
@@ -127,13 +155,36 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) 
         u13 = q13 + q1;
         u14 = q14 + q1;
         u15 = q15 + 4.0 * q1;
+        ++ctl.iters;
+        if (conv) {
+            // Eq. B.5 each iteration, to measure the change in mode space
+            const Vec<NV, R> n12 = 2.0 * (u15 - 2.0 * u11 + u[1]);
+            const Vec<NV, R> n11 = 2.0 * (u11 - u[1] - 0.25 * n12);
+            const Vec<NV, R> n13 = 4.0 * (u12 - u11 - u[2] + u[1]);
+            const Vec<NV, R> n14 = 4.0 * (u13 - u11 - u[4] + u[1]);
+            const Vec<NV, R> n15 = 4.0 * (u14 - u11 - u[6] + u[1]);
+            const R change = fmax(fmax(fmax(max_abs_diff(n11, m[11]), max_abs_diff(n12, m[12])),
+                                       fmax(max_abs_diff(n13, m[13]), max_abs_diff(n14, m[14]))),
+                                  max_abs_diff(n15, m[15]));
+            m[11] = n11;
+            m[12] = n12;
+            m[13] = n13;
+            m[14] = n14;
+            m[15] = n15;
+            if (change < R(ctl.tol) * ref) {
+                ctl.capped = false;
+                break;
+            }
+        }
     }
-    // Eq. B.5: nodal -> modal
-    m[12] = 2.0 * (u15 - 2.0 * u11 + u[1]);
-    m[11] = 2.0 * (u11 - u[1] - 0.25 * m[12]);
-    m[13] = 4.0 * (u12 - u11 - u[2] + u[1]);
-    m[14] = 4.0 * (u13 - u11 - u[4] + u[1]);
-    m[15] = 4.0 * (u14 - u11 - u[6] + u[1]);
+    if (!conv) {
+        // Eq. B.5: nodal -> modal
+        m[12] = 2.0 * (u15 - 2.0 * u11 + u[1]);
+        m[11] = 2.0 * (u11 - u[1] - 0.25 * m[12]);
+        m[13] = 4.0 * (u12 - u11 - u[2] + u[1]);
+        m[14] = 4.0 * (u13 - u11 - u[4] + u[1]);
+        m[15] = 4.0 * (u14 - u11 - u[6] + u[1]);
+    }
 }
 
 // ------------------------------------------------------------------ x+ face, Sec. V.2 and App. D

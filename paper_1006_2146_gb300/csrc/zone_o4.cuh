@@ -11,7 +11,7 @@ namespace o4 {
 
 // ------------------------------------------------------------------ modal, Sec. IV.3
 template <int NV, class R>
-ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
+ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl) {
     // Eq. 47: the 21 tau = 0 nodes of Eq. 46
     Vec<NV, R> u[22];
     u[1] = m[1] - (m[5] + m[6] + m[7]) / 12.0;
@@ -97,7 +97,12 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) 
     const Vec<NV, R> e25 = -(scale(cx, F8) + scale(cy, 2.0 * G6) + scale(cz, H9));
     const Vec<NV, R> e26 = -(scale(cx, F10) + scale(cy, G9) + scale(cz, 2.0 * H7));
 
-    for (int it = 0; it < n_iter; ++it) {
+    const bool conv = ctl.tol > 0.0;
+    const int cap = conv ? ctl.max_iter : ctl.n_iter;
+    const R ref = max_abs(m[1]) + R(1e-300);
+    ctl.iters = 0;
+    ctl.capped = conv;
+    for (int it = 0; it < cap; ++it) {
         // Eq. 48: nodes 23..41 of Eq. 46 (22 and 42 serve only source terms)
         Vec<NV, R> w[42];
         w[22] = u[1] + (36.0 * m[21] + 12.0 * m[22] + 4.0 * m[23] - 3.0 * m[30] - 3.0 * m[31] - 3.0 * m[32]) / 108.0;
@@ -199,27 +204,63 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) 
             H35 = 3.0 * (h[25] - h[26] - h[29] + h[30]) - 3.0 * H10;
         }
         // Eq. 45 without sources
-        m[21] = e21;
-        m[22] = -0.5 * (scale(cx, F24) + scale(cy, G25) + scale(cz, H26));
-        m[23] = -(1.0 / 3.0) * (scale(cx, F27) + scale(cy, G28) + scale(cz, H29));
-        m[24] = e24;
-        m[25] = e25;
-        m[26] = e26;
-        m[27] = -(scale(cx, F30) + scale(cy, 0.5 * G33) + scale(cz, 0.5 * H35));
-        m[28] = -(scale(cx, 0.5 * F33) + scale(cy, G31) + scale(cz, 0.5 * H34));
-        m[29] = -(scale(cx, 0.5 * F35) + scale(cy, 0.5 * G34) + scale(cz, H32));
-        m[30] = -(scale(cx, 3.0 * F11) + scale(cy, G14) + scale(cz, H15));
-        m[31] = -(scale(cx, F16) + scale(cy, 3.0 * G12) + scale(cz, H17));
-        m[32] = -(scale(cx, F18) + scale(cy, G19) + scale(cz, 3.0 * H13));
-        m[33] = -(scale(cx, 2.0 * F14) + scale(cy, 2.0 * G16) + scale(cz, H20));
-        m[34] = -(scale(cx, F20) + scale(cy, 2.0 * G17) + scale(cz, 2.0 * H19));
-        m[35] = -(scale(cx, 2.0 * F15) + scale(cy, G20) + scale(cz, 2.0 * H18));
+        Vec<NV, R> n[16];
+        n[0] = e21;
+        n[1] = -0.5 * (scale(cx, F24) + scale(cy, G25) + scale(cz, H26));
+        n[2] = -(1.0 / 3.0) * (scale(cx, F27) + scale(cy, G28) + scale(cz, H29));
+        n[3] = e24;
+        n[4] = e25;
+        n[5] = e26;
+        n[6] = -(scale(cx, F30) + scale(cy, 0.5 * G33) + scale(cz, 0.5 * H35));
+        n[7] = -(scale(cx, 0.5 * F33) + scale(cy, G31) + scale(cz, 0.5 * H34));
+        n[8] = -(scale(cx, 0.5 * F35) + scale(cy, 0.5 * G34) + scale(cz, H32));
+        n[9] = -(scale(cx, 3.0 * F11) + scale(cy, G14) + scale(cz, H15));
+        n[10] = -(scale(cx, F16) + scale(cy, 3.0 * G12) + scale(cz, H17));
+        n[11] = -(scale(cx, F18) + scale(cy, G19) + scale(cz, 3.0 * H13));
+        n[12] = -(scale(cx, 2.0 * F14) + scale(cy, 2.0 * G16) + scale(cz, H20));
+        n[13] = -(scale(cx, F20) + scale(cy, 2.0 * G17) + scale(cz, 2.0 * H19));
+        n[14] = -(scale(cx, 2.0 * F15) + scale(cy, G20) + scale(cz, 2.0 * H18));
+        R change = R(0);
+#pragma unroll
+        for (int k = 0; k < 15; ++k) {
+            if (conv) change = fmax(change, max_abs_diff(n[k], m[21 + k]));
+            m[21 + k] = n[k];
+        }
+        ++ctl.iters;
+        if (conv && change < R(ctl.tol) * ref) {
+            ctl.capped = false;
+            break;
+        }
     }
 }
 
 // ------------------------------------------------------------------ nodal, App. C
+// Eq. C.5 (the u35 line with node 26, the zeta node at tau = 1/3; garble G14)
 template <int NV, class R>
-ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) {
+ADER_DEV void nodal_o4_to_modes(const Vec<NV, R>* u, const Vec<NV, R>* e, Vec<NV, R>* m) {
+    const Vec<NV, R>* U = u;
+#define UB(n) ((n) <= 20 ? U[(n)] : e[(n) - 21])
+    m[21] = 0.5 * (-5.0 * UB(1) - UB(3) - UB(4) - UB(5) - UB(6) - UB(7) - UB(8) + 12.0 * UB(21) + UB(22) + UB(23) +
+                   UB(24) + UB(25) + UB(26) + UB(27) - 9.0 * UB(31) + 2.0 * UB(35));
+    m[22] = 4.5 * (2.0 * UB(1) - 5.0 * UB(21) + 4.0 * UB(31) - UB(35));
+    m[23] = -4.5 * (UB(1) - 3.0 * UB(21) + 3.0 * UB(31) - UB(35));
+    m[24] = 3.0 * (UB(1) - 2.0 * UB(3) + UB(4) - 2.0 * UB(21) + 3.0 * UB(22) - UB(23) + UB(31) - UB(32));
+    m[25] = 3.0 * (UB(1) - 2.0 * UB(5) + UB(6) - 2.0 * UB(21) + 3.0 * UB(24) - UB(25) + UB(31) - UB(33));
+    m[26] = 3.0 * (UB(1) - 2.0 * UB(7) + UB(8) - 2.0 * UB(21) + 3.0 * UB(26) - UB(27) + UB(31) - UB(34));
+    m[27] = -9.0 * (UB(1) - UB(3) - 2.0 * UB(21) + 2.0 * UB(22) + UB(31) - UB(32));
+    m[28] = -9.0 * (UB(1) - UB(5) - 2.0 * UB(21) + 2.0 * UB(24) + UB(31) - UB(33));
+    m[29] = -9.0 * (UB(1) - UB(7) - 2.0 * UB(21) + 2.0 * UB(26) + UB(31) - UB(34));
+    m[30] = 6.0 * (2.0 * UB(1) - UB(3) - UB(4) - 2.0 * UB(21) + UB(22) + UB(23));
+    m[31] = 6.0 * (2.0 * UB(1) - UB(5) - UB(6) - 2.0 * UB(21) + UB(24) + UB(25));
+    m[32] = 6.0 * (2.0 * UB(1) - UB(7) - UB(8) - 2.0 * UB(21) + UB(26) + UB(27));
+    m[33] = -12.0 * (UB(1) - UB(3) - UB(5) + UB(13) - UB(21) + UB(22) + UB(24) - UB(30));
+    m[34] = -12.0 * (UB(1) - UB(5) - UB(7) + UB(9) - UB(21) + UB(24) + UB(26) - UB(28));
+    m[35] = -12.0 * (UB(1) - UB(3) - UB(7) + UB(11) - UB(21) + UB(22) + UB(26) - UB(29));
+#undef UB
+}
+
+template <int NV, class R>
+ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl) {
     // Eq. C.4: the twenty tau = 0 nodes of Eq. C.1
     Vec<NV, R> u[21];
     const Vec<NV, R> q1 = 0.25 * m[2] - 0.125 * (m[8] + m[10]) + (-21.0 * m[11] + 40.0 * m[16] + 40.0 * m[18] + 60.0 * m[20]) / 960.0;
@@ -258,10 +299,16 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) 
         }
         nodal_o4_qterms(u, f, g, h, qt);
     }
-    // initial guess: no time evolution; node k >= 21 starts at the tau = 0 value of its spatial point
+    // initial guess: the evolutionary modes in m[21..35] (zero: no time evolution) at the
+    // tau > 0 nodes of Eq. C.1
     Vec<NV, R> e[16];
-    nodal_o4_initial(u, e);
-    for (int it = 0; it < n_iter; ++it) {
+    nodal_o4_initial(u, m, e);
+    const bool conv = ctl.tol > 0.0;
+    const int cap = conv ? ctl.max_iter : ctl.n_iter;
+    const R ref = max_abs(m[1]) + R(1e-300);
+    ctl.iters = 0;
+    ctl.capped = conv;
+    for (int it = 0; it < cap; ++it) {
         Vec<NV, R> f[15], g[15], h[15];          // index k - 21 for nodes 21..34
 #pragma unroll
         for (int k = 0; k < 14; ++k) {
@@ -271,28 +318,25 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, int n_iter) 
             h[k] = scale(cz, flux_from<2>(e[k], q));
         }
         nodal_o4_update(qt, f, g, h, e);   // Eq. C.3 without sources
+        ++ctl.iters;
+        if (conv) {
+            Vec<NV, R> old[15];
+#pragma unroll
+            for (int k = 0; k < 15; ++k) old[k] = m[21 + k];
+            nodal_o4_to_modes(u, e, m);
+            R change = R(0);
+#pragma unroll
+            for (int k = 0; k < 15; ++k) change = fmax(change, max_abs_diff(old[k], m[21 + k]));
+            if (change < R(ctl.tol) * ref) {
+                ctl.capped = false;
+                break;
+            }
+        }
     }
-    // Eq. C.5 (u35 line with node 26, the zeta node at tau = 1/3)
-    const Vec<NV, R>* U = u;
-#define UB(n) ((n) <= 20 ? U[(n)] : e[(n) - 21])
-    m[21] = 0.5 * (-5.0 * UB(1) - UB(3) - UB(4) - UB(5) - UB(6) - UB(7) - UB(8) + 12.0 * UB(21) + UB(22) + UB(23) +
-                   UB(24) + UB(25) + UB(26) + UB(27) - 9.0 * UB(31) + 2.0 * UB(35));
-    m[22] = 4.5 * (2.0 * UB(1) - 5.0 * UB(21) + 4.0 * UB(31) - UB(35));
-    m[23] = -4.5 * (UB(1) - 3.0 * UB(21) + 3.0 * UB(31) - UB(35));
-    m[24] = 3.0 * (UB(1) - 2.0 * UB(3) + UB(4) - 2.0 * UB(21) + 3.0 * UB(22) - UB(23) + UB(31) - UB(32));
-    m[25] = 3.0 * (UB(1) - 2.0 * UB(5) + UB(6) - 2.0 * UB(21) + 3.0 * UB(24) - UB(25) + UB(31) - UB(33));
-    m[26] = 3.0 * (UB(1) - 2.0 * UB(7) + UB(8) - 2.0 * UB(21) + 3.0 * UB(26) - UB(27) + UB(31) - UB(34));
-    m[27] = -9.0 * (UB(1) - UB(3) - 2.0 * UB(21) + 2.0 * UB(22) + UB(31) - UB(32));
-    m[28] = -9.0 * (UB(1) - UB(5) - 2.0 * UB(21) + 2.0 * UB(24) + UB(31) - UB(33));
-    m[29] = -9.0 * (UB(1) - UB(7) - 2.0 * UB(21) + 2.0 * UB(26) + UB(31) - UB(34));
-    m[30] = 6.0 * (2.0 * UB(1) - UB(3) - UB(4) - 2.0 * UB(21) + UB(22) + UB(23));
-    m[31] = 6.0 * (2.0 * UB(1) - UB(5) - UB(6) - 2.0 * UB(21) + UB(24) + UB(25));
-    m[32] = 6.0 * (2.0 * UB(1) - UB(7) - UB(8) - 2.0 * UB(21) + UB(26) + UB(27));
-    m[33] = -12.0 * (UB(1) - UB(3) - UB(5) + UB(13) - UB(21) + UB(22) + UB(24) - UB(30));
-    m[34] = -12.0 * (UB(1) - UB(5) - UB(7) + UB(9) - UB(21) + UB(24) + UB(26) - UB(28));
-    m[35] = -12.0 * (UB(1) - UB(3) - UB(7) + UB(11) - UB(21) + UB(22) + UB(26) - UB(29));
-#undef UB
+    if (!conv) nodal_o4_to_modes(u, e, m);
 }
+
+
 
 // ------------------------------------------------------------------ x+ face, Sec. V.3 and App. D
 // Eqs. 64-65 for u_b and <u>; Eq. D.13 for the facial nodes; composing
