@@ -172,6 +172,26 @@ int ader_mlp_grad(const float* params, const float* X, const float* Y, long long
 const char* ader_last_error(const ader_ctx* ctx);
 void ader_destroy(ader_ctx* ctx);
 
+/* CFL time step that allocates nothing (the paper has no counterpart: this is
+ * a deployment variant of ader_max_dt).  For callers that cannot call
+ * cudaMalloc -- inside someone else's stream capture, real-time loops with a
+ * fixed memory budget, hosts that forbid device allocation after start-up --
+ * it needs no context and keeps its scratch in a file-scope device array of
+ * the library (512 KB; one per device that loads the library, held until the
+ * process exits).
+ *   g, gamma : grid and ratio of specific heats, as for ader_create (Euler)
+ *   U        : device state, layout as above (read only)
+ *   cfl      : Courant number (> 0); dt = cfl / max_zones sum_d (|v_d| + a) / dx_d
+ *   dt_dev   : device output, one double
+ * Grids larger than ADER_STATIC_MAX_ZONES zones return ADER_ERR_ARG.  The
+ * first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the array, so calls that overlap on the GPU race: serialise them.
+ * Returns ADER_OK, ADER_ERR_ARG or ADER_ERR_CUDA; non-physical zones are
+ * skipped (use ader_max_dt / ader_sync_status to have them reported). */
+#define ADER_STATIC_MAX_ZONES 268435456LL
+int ader_max_dt_static(const ader_grid* g, double gamma, const double* U, double cfl, double* dt_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
