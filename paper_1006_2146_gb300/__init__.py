@@ -9,7 +9,9 @@ plus the seeded input generators (``inputs``).
 from . import inputs  # noqa: F401
 from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_FP32_BULK, ADER_HLL, ADER_LINEARIZED, ADER_MHD, ADER_NODAL,  # noqa: F401
                    AderError, ader_create, ader_destroy, ader_diagnostics, ader_last_error, ader_launches_per_step,
-                   ader_max_dt, ader_profile, ader_profile_read, ader_profile_reset, ader_rk_step, ader_step, ader_step_devdt, ader_step_host, ader_sync_status, load)
+                   ader_guess_samples, ader_max_dt, ader_mlp_grad, ader_mlp_shape, ader_mlp_train, ader_predictor_stats,
+                   ader_profile, ader_profile_read, ader_profile_reset, ader_rk_step, ader_set_guess,
+                   ader_set_predictor, ader_step, ader_step_devdt, ader_step_host, ader_sync_status, load)
 
 
 class Solver:
@@ -34,6 +36,15 @@ class Solver:
 
     def rk_step(self, U, dt, stream=None):
         ader_rk_step(self.h, U, None, dt, stream)
+
+    def set_predictor(self, tol, max_iter=50):
+        ader_set_predictor(self.h, tol, max_iter)
+
+    def predictor_stats(self, stream=None):
+        return ader_predictor_stats(self.h, stream)
+
+    def set_guess(self, params):
+        ader_set_guess(self.h, params)
 
     def status(self, stream=None):
         return ader_sync_status(self.h, stream)

@@ -17,7 +17,8 @@ ADER_OK, ADER_ERR_ARG, ADER_ERR_CUDA, ADER_ERR_UNPHYSICAL, ADER_ERR_NONFINITE, A
 
 EXPORTS = ("ader_create", "ader_step", "ader_step_devdt", "ader_max_dt", "ader_rk_step", "ader_step_host",
            "ader_diagnostics", "ader_sync_status", "ader_launches_per_step", "ader_profile", "ader_profile_reset",
-           "ader_profile_read", "ader_last_error", "ader_destroy")
+           "ader_profile_read", "ader_set_predictor", "ader_predictor_stats", "ader_set_guess", "ader_mlp_shape",
+           "ader_guess_samples", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy")
 
 
 class AderError(RuntimeError):
@@ -57,6 +58,15 @@ def load(path=None):
     lib.ader_profile_reset.argtypes = [vp]
     lib.ader_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32),
                                       ctypes.POINTER(dbl), i32]
+    lib.ader_set_predictor.argtypes = [vp, dbl, i32]
+    lib.ader_predictor_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), vp]
+    lib.ader_set_guess.argtypes = [vp, vp]
+    lib.ader_mlp_shape.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                   ctypes.POINTER(ctypes.c_longlong)]
+    lib.ader_guess_samples.argtypes = [vp, vp, vp, dbl, vp, vp, vp, vp]
+    lib.ader_mlp_train.argtypes = [vp, vp, ctypes.c_longlong, i32, i32, i32, ctypes.c_float, ctypes.c_ulonglong,
+                                   vp, ctypes.POINTER(dbl), vp]
+    lib.ader_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_longlong, i32, vp, ctypes.POINTER(dbl), vp]
     lib.ader_last_error.argtypes = [vp]
     lib.ader_last_error.restype = ctypes.c_char_p
     lib.ader_destroy.argtypes = [vp]
@@ -158,6 +168,53 @@ def ader_profile_read(h):
     if n < 0:
         _check(h, n)
     return {names[k].decode(): (counts[k], ms[k]) for k in range(min(n, cap))}
+
+
+def ader_set_predictor(h, tol, max_iter):
+    """Converged predictor: iterate each zone until its change is below tol (tol 0: fixed count)."""
+    return _check(h, load().ader_set_predictor(h, float(tol), int(max_iter)))
+
+
+def ader_predictor_stats(h, stream=None):
+    """(sum of iterations over zones and steps, largest count, zones capped) since the last read."""
+    out = (ctypes.c_ulonglong * 3)()
+    _check(h, load().ader_predictor_stats(h, out, _stream(stream)))
+    return tuple(int(v) for v in out)
+
+
+def ader_set_guess(h, params):
+    """Start the predictor from the MLP guess (FP32 device parameters, kept by pointer); None disables it."""
+    return _check(h, load().ader_set_guess(h, _ptr(params)))
+
+
+def ader_mlp_shape(mhd=False):
+    """(n_in, n_hidden, n_out, n_params) of the guess MLP."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    d = ctypes.c_longlong()
+    _check(None, load().ader_mlp_shape(1 if mhd else 0, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                       ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def ader_guess_samples(h, U, Bface, dt, X, Y, ok, stream=None):
+    return _check(h, load().ader_guess_samples(h, _ptr(U), _ptr(Bface), float(dt), _ptr(X), _ptr(Y), _ptr(ok),
+                                               _stream(stream)))
+
+
+def ader_mlp_train(X, Y, n, params, epochs, batch, lr, seed=0, mhd=False, stream=None):
+    """Adam on the MSE in place on params; returns the last minibatch loss of each epoch."""
+    losses = (ctypes.c_double * epochs)()
+    _check(None, load().ader_mlp_train(_ptr(X), _ptr(Y), int(n), 1 if mhd else 0, int(epochs), int(batch),
+                                       float(lr), int(seed), _ptr(params), losses, _stream(stream)))
+    return list(losses)
+
+
+def ader_mlp_grad(params, X, Y, n, grad, mhd=False, stream=None):
+    """Mean-squared error of the MLP on (X, Y) and its gradient into grad (device); returns the loss."""
+    loss = ctypes.c_double()
+    _check(None, load().ader_mlp_grad(_ptr(params), _ptr(X), _ptr(Y), int(n), 1 if mhd else 0, _ptr(grad),
+                                      ctypes.byref(loss), _stream(stream)))
+    return loss.value
 
 
 def ader_last_error(h):
