@@ -145,10 +145,197 @@ def flops_per_zone(order, form, solver, fp32):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def run_config(ader, torch, n, order, form, solver, fp32, steps, warmup, stream, profile=False, state=None):
-    """Times `steps` steps of max_dt + step_devdt; returns (seconds, profile dict, solver, device state)."""
+def rel_l1_dev(got, want):
+    """max over variables of sum|got - want| / max(sum|want_v|, sum|rho|) (the parity measure), on the device."""
+    num = (got - want).abs().reshape(want.shape[0], -1).sum(dim=1)
+    den = want.abs().reshape(want.shape[0], -1).sum(dim=1)
+    den = den.clamp(min=float(den[0]))
+    return float((num / den).max())
+
+
+def batched_variant(ader, torch, stream, steps=3, warmup=1):
+    """64 seeded independent problems of uneven sizes 32^3-128^3 (Euler and MHD, orders 2-4, FP32 bulk):
+    one tuned batch replayed from a captured graph vs one context per problem launched in sequence.
+    Each step includes every problem's CFL dt."""
+    from paper_1006_2146_gb300 import _lib, inputs
+    t0 = time.perf_counter()
+    probs = inputs.batch_problems(64, seed=1006)
+    gen_s = time.perf_counter() - t0
+    zones = sum(p["U"][0].size for p in probs)
+    Us = [torch.from_numpy(p["U"]).to("cuda") for p in probs]
+    Bs = [torch.from_numpy(p["B"]).to("cuda") if p["mhd"] else None for p in probs]
+    out = {"problems": len(probs), "zones": int(zones), "input_generation_s": gen_s,
+           "sizes": sorted(set(p["shape"][0] for p in probs))}
+
+    def flags_of(p):
+        return (_lib.ADER_FP32_BULK | (_lib.ADER_NODAL if p["form"] == "nodal" else 0) |
+                (_lib.ADER_MHD if p["mhd"] else 0))
+
+    def solver_of(p):
+        return _lib.ADER_LINEARIZED if p["solver"] == "linearized" else _lib.ADER_HLL
+
+    # sequential: one context per problem
+    hs = []
+    try:
+        dts = torch.zeros(len(probs), dtype=torch.float64, device="cuda")
+        for p in probs:
+            n = p["shape"][0]
+            hs.append(_lib.ader_create(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n, p["order"], p["gamma"], solver_of(p),
+                                       flags_of(p)))
+        d = [u.clone() for u in Us]
+        db = [None if x is None else x.clone() for x in Bs]
+
+        def seq_step():
+            for k, h in enumerate(hs):
+                _lib.ader_max_dt(h, d[k], db[k], 0.4, dts[k:k + 1], stream)
+                _lib.ader_step_devdt(h, d[k], db[k], dts[k:k + 1], stream)
+
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                seq_step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                seq_step()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        seq_s = e0.elapsed_time(e1) / 1e3
+        bad = [k for k, h in enumerate(hs) if _lib.ader_sync_status(h, stream) != 0]
+        out["sequential"] = {"zone_updates_per_s": zones * steps / seq_s, "ms_per_step": seq_s / steps * 1e3,
+                             "launches_per_step": sum(_lib.ader_launches_per_step(h) + 1 for h in hs),
+                             "problems_with_errors": bad}
+        del d, db
+    except Exception as exc:
+        out["sequential"] = {"error": str(exc)[:200]}
+    finally:
+        for h in hs:
+            _lib.ader_destroy(h)
+    # batched: tune, then the captured step
+    b = None
+    try:
+        n3 = [p["shape"][0] for p in probs]
+        b = _lib.ader_batch_create([(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n) for n in n3], [p["order"] for p in probs],
+                                   [p["gamma"] for p in probs], [solver_of(p) for p in probs],
+                                   [flags_of(p) for p in probs])
+        d = [u.clone() for u in Us]
+        db = [None if x is None else x.clone() for x in Bs]
+        t0 = time.perf_counter()
+        _lib.ader_batch_tune(b, d, db, stream)
+        tune_s = time.perf_counter() - t0
+        dtb = torch.zeros(len(probs), dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                _lib.ader_batch_advance(b, d, db, 0.4, dtb, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                _lib.ader_batch_advance(b, d, db, 0.4, dtb, stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        bs = e0.elapsed_time(e1) / 1e3
+        rc, codes = _lib.ader_batch_status(b, len(probs), stream)
+        out["batched"] = {"zone_updates_per_s": zones * steps / bs, "ms_per_step": bs / steps * 1e3,
+                          "graph_launches_per_step": 1, "groups": _lib.ader_batch_groups(b), "tune_s": tune_s,
+                          "status": rc, "tuned_shapes": _lib.ader_batch_tuning(b)}
+        if "zone_updates_per_s" in out.get("sequential", {}):
+            out["speedup_vs_sequential"] = out["batched"]["zone_updates_per_s"] / out["sequential"]["zone_updates_per_s"]
+    except Exception as exc:
+        out["batched"] = {"error": str(exc)[:200]}
+    finally:
+        if b is not None:
+            _lib.ader_batch_destroy(b)
+    return out
+
+
+def learned_variants(ader, torch, n, U0, stream, steps=3):
+    """Converged predictor from zero and from the learned guess (third order, nodal, HLL).
+
+    The guess is trained first (outside every timed region) on predictor samples of the seeded training
+    states at 96^3.  Each variant is timed like the headline; its state after `steps` steps of one fixed dt
+    is compared with the FP64 converged predictor's (the judge of the guess's error) and with the FP64
+    fixed-iteration method.
+    """
+    from paper_1006_2146_gb300 import learned
+    out = {}
+    try:
+        t0 = time.perf_counter()
+        X, Y = learned.make_samples(learned.training_states(96), 96)
+        t1 = time.perf_counter()
+        P, losses = learned.train(X, Y)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out["learned_guess_training"] = {"samples": int(X.shape[0]), "epochs": len(losses), "final_loss": losses[-1],
+                                         "first_epoch_loss": losses[0], "sample_s": t1 - t0, "train_s": t2 - t1}
+        del X, Y
+    except Exception as exc:
+        return {"learned_guess_training": {"error": str(exc)[:200]}}
+    zones = n ** 3
+    cases = [("fp64_converged_nodal_o3", False, 1e-13, None), ("fp32_converged_nodal_o3", True, 1e-6, None),
+             ("fp32_learned_guess_nodal_o3", True, 1e-6, P), ("fp64_learned_guess_nodal_o3", False, 1e-13, P)]
+    dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sref = ader.Solver((n, n, n), order=3, form="nodal")
+    sref.max_dt(U0, 0.4, dtv)
+    sref.close()
+    dt_fixed = float(dtv.item())
+
+    def fixed_run(fp32, tol, guess):
+        s = ader.Solver((n, n, n), order=3, form="nodal", fp32=fp32)
+        if tol is not None:
+            s.set_predictor(tol, 50)
+        if guess is not None:
+            s.set_guess(guess)
+        d = U0.clone()
+        for _ in range(steps):
+            s.step(d, dt_fixed)
+        st = s.status()
+        s.close()
+        if st != 0:
+            raise RuntimeError("device status %d" % st)
+        return d
+
+    try:
+        ref = fixed_run(False, 1e-13, None)
+        plain = fixed_run(False, None, None)
+        out["fp64_plain_vs_converged_rel_l1"] = rel_l1_dev(plain, ref)
+        del plain
+    except Exception as exc:
+        ref = None
+        out["fp64_converged_reference"] = {"error": str(exc)[:200]}
+    for name, fp32, tol, guess in cases:
+        try:
+            vsecs, vprof, vs_, _, _ = run_config(ader, torch, n, 3, "nodal", "hll", fp32, 3, 1, stream, profile=True,
+                                                 state=U0, tol=tol, guess=guess)
+            tot, mx, capped = vs_.predictor_stats(stream)
+            vs_.close()
+            rec = {"zone_updates_per_s": zones * 3 / vsecs, "ms_per_step": vsecs / 3 * 1e3,
+                   "kernel_ms": {k: round(v[1] / v[0], 3) for k, v in vprof.items()},
+                   "mean_predictor_iterations": tot / (3.0 * zones), "max_predictor_iterations": mx,
+                   "tol": tol}
+            if ref is not None:
+                d = fixed_run(fp32, tol, guess)
+                rec["rel_l1_vs_fp64_converged_%dsteps" % steps] = rel_l1_dev(d, ref)
+                del d
+            out[name] = rec
+        except Exception as exc:
+            out[name] = {"error": str(exc)[:200]}
+    return out
+
+
+
+def run_config(ader, torch, n, order, form, solver, fp32, steps, warmup, stream, profile=False, state=None,
+               tol=None, guess=None):
+    """Times `steps` steps of max_dt + step_devdt; returns (seconds, profile dict, solver, device state).
+
+    tol: converged predictor (iterate to tol, at most 50 times); guess: learned-guess parameters (device).
+    """
     from paper_1006_2146_gb300 import inputs
     s = ader.Solver((n, n, n), order=order, form=form, solver=solver, fp32=fp32)
+    if tol is not None:
+        s.set_predictor(tol, 50)
+    if guess is not None:
+        s.set_guess(guess)
     if state is None:
         state = torch.from_numpy(inputs.sod_planar(n)).to("cuda")
     d = state.clone()
@@ -158,6 +345,8 @@ def run_config(ader, torch, n, order, form, solver, fp32, steps, warmup, stream,
             s.max_dt(d, 0.4, dt, stream)
             s.step_devdt(d, dt, stream)
     torch.cuda.synchronize()
+    if tol is not None:
+        s.predictor_stats(stream)          # clears the counts of the warm-up steps
     if profile:
         ader.ader_profile(s.h, True)
         ader.ader_profile_reset(s.h)
@@ -270,6 +459,8 @@ def gpu_arm(args):
                                   "kernel_ms": {k: round(v[1] / v[0], 3) for k, v in vprof.items()}}
             except Exception as exc:          # a variant that fails is reported, not hidden
                 variants[name] = {"error": str(exc)[:200]}
+        variants.update(learned_variants(ader, torch, n, U0, stream))
+        variants["batched_64_problems_fp32"] = batched_variant(ader, torch, stream)
         # SSP-RK of the same order and solver on the same GPU (Eq. 19), per step
         srk = ader.Solver((n, n, n), order=3, form="nodal", solver="hll")
         drk = U0.clone()
@@ -304,6 +495,13 @@ def gpu_arm(args):
                            "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps,
                 "launches_per_step": launches, "clocks": ck, "wall_s_timed": wall, "variants": variants}
+        lg = variants.get("fp32_learned_guess_nodal_o3", {})
+        if "zone_updates_per_s" in lg:
+            line["fp32_learned_guess"] = {
+                "zone_updates_per_s": lg["zone_updates_per_s"],
+                "speedup_vs_fp64_plain": lg["zone_updates_per_s"] / value if not args.fp32 else None,
+                "rel_l1_vs_fp64_converged_3steps": lg.get("rel_l1_vs_fp64_converged_3steps"),
+                "mean_predictor_iterations": lg.get("mean_predictor_iterations")}
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -60,7 +60,9 @@ enum {
     ADER_ERR_CUDA = -2,         /* a CUDA runtime call failed */
     ADER_ERR_UNPHYSICAL = -3,   /* device flag: rho <= 0 or P <= 0 met */
     ADER_ERR_NONFINITE = -4,    /* device flag: a NaN or Inf met */
-    ADER_ERR_NOT_CONVERGED = -5 /* device flag: converged predictor hit its iteration cap */
+    ADER_ERR_NOT_CONVERGED = -5, /* device flag: converged predictor hit its iteration cap */
+    ADER_ERR_TIMEOUT = -6       /* device flag: a bounded wait inside a kernel ran out (the kernel
+                                   stopped early; its outputs are incomplete) */
 };
 
 typedef struct ader_ctx ader_ctx;
@@ -107,12 +109,17 @@ int ader_rk_step(ader_ctx* ctx, double* U, double* Bface, double dt, void* strea
  * Euler contexts only. */
 int ader_step_host(ader_ctx* ctx, double* U_host, double* Bface_host, double cfl, double* dt_used_host);
 
-/* Totals of the five conserved variables (FP64 reduction), written to
- * totals_dev[0..4] (device). */
+/* Conservation and divergence diagnostics (FP64, deterministic order).
+ * Euler: totals of the five conserved variables -> totals_dev[0..4].
+ * MHD: totals_dev[0..4] as above, [5..7] totals of the face fields Bx, By, Bz,
+ * [8] the largest |div B| of a zone (sum over d of the face difference over
+ * dx_d, the quantity Eq. 8 keeps constant) over (largest |B| on a face /
+ * min(dx, dy, dz)); 0 when B vanishes.  totals_dev is device memory of 5
+ * (Euler) or 9 (MHD) doubles. */
 int ader_diagnostics(ader_ctx* ctx, const double* U, const double* Bface, double* totals_dev, void* stream);
 
 /* Synchronise the stream and turn the device error flag into a return code
- * (ADER_OK, ADER_ERR_UNPHYSICAL, ADER_ERR_NONFINITE, ADER_ERR_NOT_CONVERGED);
+ * (ADER_OK, ADER_ERR_UNPHYSICAL, ADER_ERR_NONFINITE, ADER_ERR_TIMEOUT, ADER_ERR_NOT_CONVERGED);
  * clears the flag. */
 int ader_sync_status(ader_ctx* ctx, void* stream);
 
@@ -139,19 +146,36 @@ int ader_profile_read(ader_ctx* ctx, const char** names, int* launches, double* 
 int ader_set_predictor(ader_ctx* ctx, double tol, int max_iter);
 int ader_predictor_stats(ader_ctx* ctx, unsigned long long* out3_host, void* stream);
 
-/* Learned initial guess (third order).  params (device, FP32, layout and
- * size from ader_mlp_shape) is an MLP mapping a zone's normalised spatial
- * modes and Courant numbers to its evolutionary modes; the predictor starts
- * from that guess instead of zero.  NULL disables it.  The pointer is kept,
- * not copied: keep the buffer alive while the context uses it. */
+/* Learned initial guess (third order; the paper has no learned component and
+ * starts its Picard iteration of Sec. IV from zero).  params (device, FP32,
+ * layout and size from ader_mlp_shape) is an MLP mapping a zone's normalised
+ * spatial modes and Courant numbers to its evolutionary modes; each step then
+ * runs one more kernel that writes every zone's guess, and the predictor
+ * starts from it instead of zero.  The first non-NULL call allocates that
+ * per-zone buffer (5 x nvar x zones FP32, held by the context); NULL disables
+ * the guess.  The pointer is kept, not copied: keep the buffer alive while the
+ * context uses it.  With the fixed iteration count the guess changes the
+ * result; with ader_set_predictor's tolerance it only changes the work. */
 int ader_set_guess(ader_ctx* ctx, const float* params);
+/* The guess alone: reconstructs (U, Bface) and writes every zone's guessed
+ * evolutionary modes to G (device, 5 x nvar x zones FP32, G[(j*nvar + v)*zones
+ * + zone] = u_{11+j} of variable v) with the kernel the step uses: the three
+ * layers on the tensor cores (tcgen05, FP16 operands, FP32 accumulation).
+ * Needs ader_set_guess first.  Asynchronous on the stream. */
+int ader_guess_eval(ader_ctx* ctx, const double* U, const double* Bface, double dt, float* G, void* stream);
 int ader_mlp_shape(int mhd, int* n_in, int* n_hidden, int* n_out, long long* n_params);
 
 /* Training data: for every zone of (U, Bface), the MLP features X (n x n_in)
  * and the normalised evolutionary modes Y (n x n_out) of the converged FP64
  * modal predictor started from zero (tolerance of ader_set_predictor, 1e-13
- * if unset); ok[z] = 0 marks a zone to skip (non-physical or capped).  Needs
- * a third-order FP64 context.  All pointers are device pointers. */
+ * if unset).  Features: the zone's slopes (modes w2..w10 over the variable
+ * scales) divided by their largest magnitude g; the zone means of momentum
+ * (and field) over their scales; the three Courant numbers; and g.  Targets
+ * are divided by g as well.  ok[z] = 0 marks a zone to skip: non-physical,
+ * uniform to round-off (g <= 1e-12, whose guess is zero by construction) or
+ * capped; its rows
+ * are left unwritten.  Needs a third-order FP64 context.  All pointers are
+ * device pointers. */
 int ader_guess_samples(ader_ctx* ctx, const double* U, const double* Bface, double dt, float* X, float* Y, int* ok,
                        void* stream);
 
@@ -171,6 +195,48 @@ int ader_mlp_grad(const float* params, const float* X, const float* Y, long long
 
 const char* ader_last_error(const ader_ctx* ctx);
 void ader_destroy(ader_ctx* ctx);
+
+/* ---- Batched problems (many independent grids in one captured step) ----
+ * Each problem is the periodic problem of Eqs. 4-8 on its own grid, with its
+ * own order, gamma, solver and flags; the batch advances all of them by one
+ * ADER step (Eq. 6, and Eq. 8 for MHD) per call.  The paper has no batched
+ * mode: it runs one problem at a time.  Problems must use ADER_FP32_BULK (FP32
+ * reconstruction, predictor and fluxes; FP64 state, update and dt) and the
+ * fixed iteration count of the predictor; MHD problems use HLL.
+ * Problems of the same order, physics, form and solver form a group; each
+ * phase of a group is one persistent launch over all its problems, groups run
+ * concurrently, and a step is replayed from a CUDA graph captured on the first
+ * call (captured again when the state pointers, dt buffer or CFL change).
+ *   ader_batch_create: n problems (1..ADER_BATCH_MAX), arrays of n entries.
+ *     Allocates all scratch; nothing is allocated by the step calls.
+ *   ader_batch_tune: optional; times each (group, phase) over block sizes
+ *     64/128/256 and persistent grid sizes on private copies of the given
+ *     states (allocated and freed inside the call) and keeps the fastest.
+ *   ader_batch_step: U[p] (device, 5 x zones, in/out), Bface[p] (device,
+ *     3 x zones for MHD problems, else ignored), dt_dev[p] (device, n doubles).
+ *   ader_batch_advance: dt_dev[p] = cfl / max over zones of sum_d (|v_d| +
+ *     c_d) / dx_d for each problem (written to dt_dev, device, n doubles; NULL
+ *     uses an internal buffer), then the step with it; one graph.
+ *   ader_batch_status: synchronises the stream; codes_host[p] (n ints, may be
+ *     NULL) gets each problem's code; returns the first non-OK code.
+ *   ader_batch_tuning: writes (group, phase, threads, blocks) quadruples
+ *     (blocks 0 = one block per `threads` zones) to out_host (cap ints);
+ *     returns the number of quadruples.
+ * The pointer arrays are host arrays; the pointers they hold are device
+ * pointers and stay owned by the caller. */
+#define ADER_BATCH_MAX 4096
+typedef struct ader_batch ader_batch;
+int ader_batch_create(int n, const ader_grid* grids, const int* orders, const double* gammas, const int* solvers,
+                      const unsigned* flags, ader_batch** out);
+int ader_batch_tune(ader_batch* b, double* const* U, double* const* Bface, void* stream);
+int ader_batch_step(ader_batch* b, double* const* U, double* const* Bface, const double* dt_dev, void* stream);
+int ader_batch_advance(ader_batch* b, double* const* U, double* const* Bface, double cfl, double* dt_dev,
+                       void* stream);
+int ader_batch_status(ader_batch* b, int* codes_host, void* stream);
+int ader_batch_tuning(const ader_batch* b, int* out_host, int cap);
+int ader_batch_groups(const ader_batch* b);
+const char* ader_batch_last_error(const ader_batch* b);
+void ader_batch_destroy(ader_batch* b);
 
 /* CFL time step that allocates nothing (the paper has no counterpart: this is
  * a deployment variant of ader_max_dt).  For callers that cannot call

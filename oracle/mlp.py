@@ -17,10 +17,13 @@ plain numpy FP64:
   * the features and targets of a zone (``features``, ``targets``):
       scales  s_rho = w1(rho), s_E = w1(E), c = sqrt(s_E / s_rho), s_m = s_rho c,
               s_B = sqrt(8 pi s_E) (Gaussian units, as in Sec. III);
-      x       w2..w10 of rho and E, w1..w10 of each momentum (and field)
-              component, each over its scale, then c dt/dx, c dt/dy, c dt/dz;
-      y       u_{11+j} of variable v over (s_v sigma), sigma = c (dt/dx + dt/dy + dt/dz),
+      slopes  r = w2..w10 of every variable over its scale; magnitude g = max |r|;
+      x       r / g (variable-major), then w1 of each momentum (and field)
+              component over its scale, then c dt/dx, c dt/dy, c dt/dz, then g;
+      y       u_{11+j} of variable v over (s_v sigma g), sigma = c (dt/dx + dt/dy + dt/dz),
               in the order j-major, variable-minor.
+    A zone uniform to round-off (g <= MAG_MIN = 1e-12) has no time evolution to
+    speak of: its guess is zero and it is no sample (``sample_mask``).
 
 Parameters are one flat vector: W1 (H x IN, row-major), b1 (H), W2 (H x H),
 b2 (H), W3 (OUT x H), b3 (OUT).
@@ -33,12 +36,13 @@ accuracy of the tanh form and its limits; the features of uniform states.
 import numpy as np
 
 HIDDEN = 128
+MAG_MIN = 1e-12
 
 
 def shape(mhd=False):
     """(n_in, n_hidden, n_out, n_params)."""
     nv = 8 if mhd else 5
-    n_in = 48 + (30 if mhd else 0) + 3
+    n_in = 48 + (30 if mhd else 0) + 4
     n_out = 5 * nv
     H = HIDDEN
     return n_in, H, n_out, H * n_in + H + H * H + H + n_out * H + n_out
@@ -112,50 +116,78 @@ def _scales(W, mhd):
     return s, c
 
 
-def features(W, dt, dx):
-    """Features (n_zones, n_in) from the third-order spatial modes W (10, nvar, *grid), modal order of Eq. 33."""
+def _slopes(W):
+    """Normalised slopes r (n_zones, 45 or 72): w2..w10 of each variable over its scale; their magnitude g."""
     nv = W.shape[1]
-    mhd = nv == 8
     Wf = W.reshape(W.shape[0], nv, -1)
-    s, c = _scales(Wf, mhd)
-    cols = []
-    for v in range(nv):
-        k0 = 1 if v in (0, 4) else 0           # w1 of rho and E are the scales themselves
-        for k in range(k0, 10):
-            cols.append(Wf[k, v] / s[v])
-    for d in range(3):
-        cols.append(c * dt / dx[d])
-    return np.stack(cols, axis=1)
+    s, _ = _scales(Wf, nv == 8)
+    cols = [Wf[k, v] / s[v] for v in range(nv) for k in range(1, 10)]
+    r = np.stack(cols, axis=1)
+    return r, np.abs(r).max(axis=1)
+
+
+def _means(W):
+    """Zone means of momentum (and field) over their scales (n_zones, 3 or 6)."""
+    nv = W.shape[1]
+    Wf = W.reshape(W.shape[0], nv, -1)
+    s, _ = _scales(Wf, nv == 8)
+    return np.stack([Wf[0, v] / s[v] for v in range(1, nv) if v != 4], axis=1)
+
+
+def sample_mask(W):
+    """Zones that are training samples: positive scales and a nonzero slope magnitude."""
+    nv = W.shape[1]
+    Wf = W.reshape(W.shape[0], nv, -1)
+    _, g = _slopes(W)
+    return (Wf[0, 0] > 0) & (Wf[0, 4] > 0) & (g > MAG_MIN)
+
+
+def features(W, dt, dx):
+    """Features (n_zones, n_in) from the third-order spatial modes W (10, nvar, *grid), modal order of Eq. 33.
+
+    Rows of uniform zones (g = 0) keep r unscaled (all zero)."""
+    nv = W.shape[1]
+    Wf = W.reshape(W.shape[0], nv, -1)
+    _, c = _scales(Wf, nv == 8)
+    r, g = _slopes(W)
+    inv = np.where(g > 0, 1.0 / np.where(g > 0, g, 1.0), 0.0)
+    cols = [r * inv[:, None], _means(W)] + [(c * dt / dx[d])[:, None] for d in range(3)] + [g[:, None]]
+    return np.concatenate(cols, axis=1)
 
 
 def targets(W, Uhat, dt, dx):
-    """Targets (n_zones, 5 nvar): the evolutionary modes u_11..u_15 of Uhat (15, nvar, *grid), normalised."""
+    """Targets (n_zones, 5 nvar): the evolutionary modes u_11..u_15 of Uhat (15, nvar, *grid), normalised
+    (rows of uniform zones are NaN: they are no samples)."""
     nv = W.shape[1]
     mhd = nv == 8
     Wf = W.reshape(W.shape[0], nv, -1)
     Uf = Uhat.reshape(Uhat.shape[0], nv, -1)
     s, c = _scales(Wf, mhd)
+    _, g = _slopes(W)
     sigma = c * (dt / dx[0] + dt / dx[1] + dt / dx[2])
     cols = []
-    for j in range(5):
-        for v in range(nv):
-            cols.append(Uf[10 + j, v] / (s[v] * sigma))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for j in range(5):
+            for v in range(nv):
+                cols.append(Uf[10 + j, v] / (s[v] * sigma * g))
     return np.stack(cols, axis=1)
 
 
 def guess_modes(P, W, dt, dx):
-    """The network's evolutionary modes (5, nvar, *grid) for spatial modes W, undoing the normalisation."""
+    """The network's evolutionary modes (5, nvar, *grid) for spatial modes W, undoing the normalisation;
+    zero for uniform zones."""
     nv = W.shape[1]
     mhd = nv == 8
     n_in, H, n_out, _ = shape(mhd)
     Wf = W.reshape(W.shape[0], nv, -1)
     s, c = _scales(Wf, mhd)
+    _, g = _slopes(W)
     sigma = c * (dt / dx[0] + dt / dx[1] + dt / dx[2])
     y = forward(P, features(W, dt, dx), n_out, H)
     out = np.empty((5, nv, Wf.shape[2]))
     for j in range(5):
         for v in range(nv):
-            out[j, v] = y[:, j * nv + v] * s[v] * sigma
+            out[j, v] = np.where(g > MAG_MIN, y[:, j * nv + v] * s[v] * sigma * g, 0.0)
     return out.reshape((5, nv) + W.shape[2:])
 
 

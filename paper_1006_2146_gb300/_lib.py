@@ -14,11 +14,15 @@ LIB_PATH = os.path.join(HERE, "_build", "libader_gb300.so")
 ADER_HLL, ADER_LINEARIZED = 0, 1
 ADER_MHD, ADER_NODAL, ADER_FP32_BULK, ADER_CONVERGED_PREDICTOR = 1, 2, 4, 16
 ADER_OK, ADER_ERR_ARG, ADER_ERR_CUDA, ADER_ERR_UNPHYSICAL, ADER_ERR_NONFINITE, ADER_ERR_NOT_CONVERGED = 0, -1, -2, -3, -4, -5
+ADER_ERR_TIMEOUT = -6
 
 EXPORTS = ("ader_create", "ader_step", "ader_step_devdt", "ader_max_dt", "ader_rk_step", "ader_step_host",
            "ader_diagnostics", "ader_sync_status", "ader_launches_per_step", "ader_profile", "ader_profile_reset",
            "ader_profile_read", "ader_set_predictor", "ader_predictor_stats", "ader_set_guess", "ader_mlp_shape",
-           "ader_guess_samples", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy")
+           "ader_guess_samples", "ader_guess_eval", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy",
+           "ader_max_dt_static", "ader_batch_create", "ader_batch_tune", "ader_batch_step", "ader_batch_advance",
+           "ader_batch_status", "ader_batch_tuning", "ader_batch_groups", "ader_batch_last_error",
+           "ader_batch_destroy")
 
 
 class AderError(RuntimeError):
@@ -64,6 +68,7 @@ def load(path=None):
     lib.ader_mlp_shape.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(ctypes.c_longlong)]
     lib.ader_guess_samples.argtypes = [vp, vp, vp, dbl, vp, vp, vp, vp]
+    lib.ader_guess_eval.argtypes = [vp, vp, vp, dbl, vp, vp]
     lib.ader_mlp_train.argtypes = [vp, vp, ctypes.c_longlong, i32, i32, i32, ctypes.c_float, ctypes.c_ulonglong,
                                    vp, ctypes.POINTER(dbl), vp]
     lib.ader_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_longlong, i32, vp, ctypes.POINTER(dbl), vp]
@@ -71,8 +76,22 @@ def load(path=None):
     lib.ader_last_error.restype = ctypes.c_char_p
     lib.ader_destroy.argtypes = [vp]
     lib.ader_destroy.restype = None
+    lib.ader_max_dt_static.argtypes = [ctypes.POINTER(ader_grid), dbl, vp, dbl, vp, vp]
+    pp = ctypes.POINTER(vp)
+    lib.ader_batch_create.argtypes = [i32, ctypes.POINTER(ader_grid), ctypes.POINTER(i32), ctypes.POINTER(dbl),
+                                      ctypes.POINTER(i32), ctypes.POINTER(u32), ctypes.POINTER(vp)]
+    lib.ader_batch_tune.argtypes = [vp, pp, pp, vp]
+    lib.ader_batch_step.argtypes = [vp, pp, pp, vp, vp]
+    lib.ader_batch_advance.argtypes = [vp, pp, pp, dbl, vp, vp]
+    lib.ader_batch_status.argtypes = [vp, ctypes.POINTER(i32), vp]
+    lib.ader_batch_tuning.argtypes = [vp, ctypes.POINTER(i32), i32]
+    lib.ader_batch_groups.argtypes = [vp]
+    lib.ader_batch_last_error.argtypes = [vp]
+    lib.ader_batch_last_error.restype = ctypes.c_char_p
+    lib.ader_batch_destroy.argtypes = [vp]
+    lib.ader_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("ader_destroy", "ader_last_error"):
+        if name not in ("ader_destroy", "ader_last_error", "ader_batch_destroy", "ader_batch_last_error"):
             getattr(lib, name).restype = i32
     if path is None:
         _LIB = lib
@@ -201,6 +220,11 @@ def ader_guess_samples(h, U, Bface, dt, X, Y, ok, stream=None):
                                                _stream(stream)))
 
 
+def ader_guess_eval(h, U, Bface, dt, G, stream=None):
+    """Every zone's guessed evolutionary modes into G (device, 5*nvar x zones FP32) by the step's guess kernel."""
+    return _check(h, load().ader_guess_eval(h, _ptr(U), _ptr(Bface), float(dt), _ptr(G), _stream(stream)))
+
+
 def ader_mlp_train(X, Y, n, params, epochs, batch, lr, seed=0, mhd=False, stream=None):
     """Adam on the MSE in place on params; returns the last minibatch loss of each epoch."""
     losses = (ctypes.c_double * epochs)()
@@ -224,3 +248,69 @@ def ader_last_error(h):
 def ader_destroy(h):
     if h:
         load().ader_destroy(h)
+
+
+# ----------------------------------------------------------------------------- batched problems
+def _ptrs(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for k, t in enumerate(ts):
+        arr[k] = None if t is None else t.data_ptr()
+    return arr
+
+
+def _bcheck(b, rc):
+    if rc != ADER_OK:
+        msg = load().ader_batch_last_error(b).decode() if b else "invalid argument"
+        raise AderError(rc, msg)
+    return rc
+
+
+def ader_batch_create(grids, orders, gammas, solvers, flags):
+    """grids: list of (nx, ny, nz, dx, dy, dz); the other arguments: one entry per problem."""
+    n = len(grids)
+    G = (ader_grid * n)(*[ader_grid(*g) for g in grids])
+    O = (ctypes.c_int * n)(*orders)
+    Gm = (ctypes.c_double * n)(*gammas)
+    S = (ctypes.c_int * n)(*solvers)
+    F = (ctypes.c_uint * n)(*flags)
+    b = ctypes.c_void_p()
+    rc = load().ader_batch_create(n, G, O, Gm, S, F, ctypes.byref(b))
+    if rc != ADER_OK:
+        raise AderError(rc, "ader_batch_create failed (arguments or device memory)")
+    return b
+
+
+def ader_batch_tune(b, Us, Bs, stream=None):
+    return _bcheck(b, load().ader_batch_tune(b, _ptrs(Us), _ptrs(Bs), _stream(stream)))
+
+
+def ader_batch_step(b, Us, Bs, dt_dev, stream=None):
+    return _bcheck(b, load().ader_batch_step(b, _ptrs(Us), _ptrs(Bs), _ptr(dt_dev), _stream(stream)))
+
+
+def ader_batch_advance(b, Us, Bs, cfl, dt_dev=None, stream=None):
+    return _bcheck(b, load().ader_batch_advance(b, _ptrs(Us), _ptrs(Bs), float(cfl), _ptr(dt_dev), _stream(stream)))
+
+
+def ader_batch_status(b, n, stream=None):
+    """(worst code, per-problem codes); synchronises the stream."""
+    codes = (ctypes.c_int * n)()
+    rc = load().ader_batch_status(b, codes, _stream(stream))
+    return rc, list(codes)
+
+
+def ader_batch_tuning(b):
+    """[(group, phase, threads, blocks)] chosen by ader_batch_tune (blocks 0: one block per `threads` zones)."""
+    cap = 4 * 512
+    out = (ctypes.c_int * cap)()
+    k = load().ader_batch_tuning(b, out, cap)
+    return [tuple(out[4 * i:4 * i + 4]) for i in range(min(k, cap // 4))]
+
+
+def ader_batch_groups(b):
+    return load().ader_batch_groups(b)
+
+
+def ader_batch_destroy(b):
+    if b:
+        load().ader_batch_destroy(b)

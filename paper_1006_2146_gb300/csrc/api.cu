@@ -36,6 +36,8 @@ struct ader_ctx {
     int max_iter = 50;
     unsigned long long* stats = nullptr;      // converged predictor statistics (3 words)
     const float* guess = nullptr;             // learned-guess MLP parameters (device), order 3
+    float* G = nullptr;                       // per-zone learned guess (5 x NV x N FP32), allocated by ader_set_guess
+    bool setup_failed = false;                // a kernel could not be configured while enqueuing
     int launches = 0;
     std::string err;
     // tracing: pending event pairs per kernel name, folded into totals on read
@@ -115,6 +117,7 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.max_iter = c->max_iter;
     a.stats = c->stats;
     a.guess = n_iter > 0 ? c->guess : nullptr;
+    a.G = a.guess ? c->G : nullptr;
     return a;
 }
 
@@ -124,6 +127,14 @@ static int enqueue_faces(ader_ctx* c, const StepArgs& a, const double* U, cudaSt
     {
         Trace t(c, "weno_reconstruction", st);
         n = launch_recon<R>(a, U, st);
+    }
+    if (a.G) {
+        Trace t(c, "learned_guess", st);
+        const int k = launch_guess<R>(a, U, st);
+        if (k < 0)
+            c->setup_failed = true;       // reported by the caller
+        else
+            n += k;
     }
     Trace t(c, "predictor_faces", st);
     if (a.mhd) {
@@ -162,7 +173,7 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
     if (order < 2 || order > 4 || !(gamma > 1.0) || (solver != ADER_HLL && solver != ADER_LINEARIZED))
         return ADER_ERR_ARG;
     const unsigned known = ADER_MHD | ADER_NODAL | ADER_FP32_BULK;
-    if (flags & ~known) return ADER_ERR_ARG;        // the converged predictor is not built
+    if (flags & ~known) return ADER_ERR_ARG;        // the converged predictor is set by ader_set_predictor
     if ((flags & ADER_MHD) && solver != ADER_HLL) return ADER_ERR_ARG;   // MHD: HLL only
     ader_ctx* c = new ader_ctx();
     c->g = *g;
@@ -195,7 +206,7 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
     alloc((void**)&c->stats, 3 * sizeof(unsigned long long), "cudaMalloc predictor statistics");
     alloc((void**)&c->dtscr, 2 * sizeof(unsigned long long), "cudaMalloc dt scratch");
     c->tot_blocks = 1024;
-    alloc((void**)&c->partial, c->tot_blocks * 5 * sizeof(double), "cudaMalloc partials");
+    alloc((void**)&c->partial, c->tot_blocks * 10 * sizeof(double), "cudaMalloc partials");
     alloc((void**)&c->dt_dev, sizeof(double), "cudaMalloc dt");
     alloc((void**)&c->Ustage, N * 5 * sizeof(double), "cudaMalloc host-path state");
     for (int s = 0; s < 7; ++s) alloc((void**)&c->rk[s], N * 5 * sizeof(double), "cudaMalloc RK stage");
@@ -217,8 +228,8 @@ void ader_destroy(ader_ctx* c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->spare) cudaEventDestroy(e);
-    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->flag, c->stats, c->dtscr, c->partial, c->dt_dev, c->Ustage,
-                    c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6]};
+    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->flag, c->stats, c->dtscr, c->partial, c->dt_dev,
+                    c->Ustage, c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -292,6 +303,10 @@ static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const d
     a.Bface = Bface;
     const double coef = dt_dev ? 1.0 : dt;
     c->launches = enqueue_operator(c, a, U, U, U, coef, dt_dev != nullptr, st);
+    if (c->setup_failed) {
+        c->setup_failed = false;
+        return fail(c, ADER_ERR_CUDA, "learned-guess kernel set-up failed");
+    }
     if (c->mhd) {
         Trace t(c, "emf_ct", st);
         c->launches += c->fp32 ? launch_emf_ct<float>(a, Bface, coef, dt_dev != nullptr, st)
@@ -324,7 +339,9 @@ int ader_diagnostics(ader_ctx* c, const double* U, const double* Bface, double* 
     if (!c) return ADER_ERR_ARG;
     if (!U || !totals_dev) return fail(c, ADER_ERR_ARG, "null pointer");
     if (int rc = check_bface(c, Bface)) return rc;
-    launch_totals(c->grid, U, totals_dev, c->partial, c->tot_blocks, (cudaStream_t)stream);
+    const double dx[3] = {c->g.dx, c->g.dy, c->g.dz};
+    launch_totals(c->grid, U, c->mhd ? Bface : nullptr, dx, totals_dev, c->partial, c->tot_blocks,
+                  (cudaStream_t)stream);
     return cuda_check(c, cudaGetLastError(), "ader_diagnostics launch");
 }
 
@@ -419,8 +436,32 @@ int ader_predictor_stats(ader_ctx* c, unsigned long long* out3_host, void* strea
 int ader_set_guess(ader_ctx* c, const float* params) {
     if (!c) return ADER_ERR_ARG;
     if (params && c->order != 3) return fail(c, ADER_ERR_ARG, "the learned guess is built for third order");
+    if (params && !c->G) {
+        const size_t bytes = (size_t)5 * (c->mhd ? 8 : 5) * (size_t)c->grid.n * sizeof(float);
+        if (int rc = cuda_check(c, cudaMalloc((void**)&c->G, bytes), "cudaMalloc learned guess")) return rc;
+    }
     c->guess = params;
     return ADER_OK;
+}
+
+int ader_guess_eval(ader_ctx* c, const double* U, const double* Bface, double dt, float* G, void* stream) {
+    if (!c) return ADER_ERR_ARG;
+    if (!U || !G || !(dt > 0.0)) return fail(c, ADER_ERR_ARG, "null pointer or dt <= 0");
+    if (!c->guess) return fail(c, ADER_ERR_ARG, "no guess parameters set (ader_set_guess)");
+    if (int rc = check_bface(c, Bface)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    StepArgs a = make_args(c, dt, nullptr, 2);
+    a.Bface = Bface;
+    a.guess = c->guess;
+    a.G = G;
+    if (c->fp32) {
+        launch_recon<float>(a, U, st);
+        if (launch_guess<float>(a, U, st) < 0) return fail(c, ADER_ERR_CUDA, "guess kernel set-up");
+    } else {
+        launch_recon<double>(a, U, st);
+        if (launch_guess<double>(a, U, st) < 0) return fail(c, ADER_ERR_CUDA, "guess kernel set-up");
+    }
+    return cuda_check(c, cudaGetLastError(), "ader_guess_eval launch");
 }
 
 int ader_guess_samples(ader_ctx* c, const double* U, const double* Bface, double dt, float* X, float* Y, int* ok,
@@ -433,6 +474,8 @@ int ader_guess_samples(ader_ctx* c, const double* U, const double* Bface, double
     StepArgs a = make_args(c, dt, nullptr, 2);
     a.Bface = Bface;
     a.tol = c->tol > 0.0 ? c->tol : 1e-13;
+    a.guess = nullptr;
+    a.G = nullptr;
     launch_recon<double>(a, U, st);
     launch_guess_samples(a, U, X, Y, ok, st);
     return cuda_check(c, cudaGetLastError(), "ader_guess_samples launch");
@@ -451,6 +494,7 @@ int ader_sync_status(ader_ctx* c, void* stream) {
     }
     if (h & FLAG_NONFINITE) return fail(c, ADER_ERR_NONFINITE, "non-finite value in the updated state");
     if (h & FLAG_UNPHYSICAL) return fail(c, ADER_ERR_UNPHYSICAL, "rho <= 0 or P <= 0 in a zone");
+    if (h & FLAG_TIMEOUT) return fail(c, ADER_ERR_TIMEOUT, "a bounded wait in a kernel ran out");
     if (h & FLAG_NOT_CONVERGED) return fail(c, ADER_ERR_NOT_CONVERGED, "predictor iteration cap reached");
     return ADER_OK;
 }

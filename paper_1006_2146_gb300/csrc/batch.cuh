@@ -1,0 +1,127 @@
+// Batched step: many independent problems of uneven sizes in one launch per
+// phase and per variant group (same order, physics, form, solver).
+//
+// Work layout: the zones of the group's problems are laid end to end, each
+// problem padded to a multiple of BATCH_ALIGN zones; zpad[p] is the first
+// padded index of problem p (zpad[np] the total).  Launches are persistent:
+// a grid sized to the SMs loops over the padded range.  Because every block
+// size divides BATCH_ALIGN, all threads of a block always work on the same
+// problem, and the padding zones (z >= n of their problem) are skipped.
+#pragma once
+#include "kernels.cuh"
+#include "step_kernels.cuh"
+#include "weno.cuh"
+
+namespace ader {
+
+constexpr int BATCH_ALIGN = 256;        // block sizes (zones per block) must divide this
+
+struct BatchItem {
+    StepArgs a;         // the problem's step arguments (its own scratch, dt_dev and flag)
+    double* U;          // state, updated in place
+    double* Bf;         // MHD face field, updated in place (null for Euler)
+};
+
+// what one launch of a phase over a group needs
+struct BatchGroupDev {
+    const BatchItem* items;     // device, np entries
+    const long long* zpad;      // device, np + 1 entries
+    int np;
+    long long total;            // zpad[np]
+};
+
+ADER_DEV int batch_find(const long long* __restrict__ zpad, int np, long long gz) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (zpad[mid] <= gz)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Calls f(item, z) for every real zone of the group (grid-stride over the padded range).
+template <class F>
+ADER_DEV void batch_for(const BatchGroupDev& g, F f) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long gz = (long long)blockIdx.x * blockDim.x + threadIdx.x; gz < g.total; gz += stride) {
+        const int p = batch_find(g.zpad, g.np, gz);
+        const BatchItem& it = g.items[p];
+        const long long z = gz - g.zpad[p];
+        if (z < it.a.grid.n) f(it, z);
+    }
+}
+
+template <int ORDER, class R>
+__global__ void __launch_bounds__(256) kb_face_b(BatchGroupDev g) {
+    batch_for(g, [](const BatchItem& it, long long z) {
+        zone_face_b<ORDER, R>(it.a.grid, it.Bf, (R*)it.a.ZB, (R*)it.a.S1, z);
+    });
+}
+
+template <int ORDER, int NV, class R>
+__global__ void __launch_bounds__(256) kb_weno1d(BatchGroupDev g) {
+    batch_for(g, [](const BatchItem& it, long long z) {
+        zone_weno1d<ORDER, NV, R>(it.a.grid, it.U, (const R*)it.a.ZB, (R*)it.a.S1, z);
+    });
+}
+
+template <int ORDER, int NV, class R>
+__global__ void __launch_bounds__(256) kb_cross1(BatchGroupDev g) {
+    batch_for(g, [](const BatchItem& it, long long z) {
+        zone_cross1<ORDER, NV, R>(it.a.grid, (const R*)it.a.S1, (R*)it.a.S2, z);
+    });
+}
+
+template <int NV, class R>
+__global__ void __launch_bounds__(256) kb_cross2(BatchGroupDev g) {
+    batch_for(g, [](const BatchItem& it, long long z) { zone_cross2<NV, R>(it.a.grid, (R*)it.a.S2, z); });
+}
+
+template <int ORDER, int FORM, int NV, class R>
+__global__ void __launch_bounds__(256) kb_predict_faces(BatchGroupDev g) {
+    batch_for(g, [](const BatchItem& it, long long z) { zone_predict_faces<ORDER, FORM, NV, R>(it.a, it.U, z); });
+}
+
+// U += dt L(U) in place, dt from the problem's dt_dev
+template <int SOLVER, int NV, class R>
+__global__ void __launch_bounds__(256) kb_flux_update(BatchGroupDev g) {
+    batch_for(g, [](const BatchItem& it, long long z) {
+        zone_flux_update<SOLVER, NV, R>(it.a, it.U, it.U, 1.0, 1, z);
+    });
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) kb_emf(BatchGroupDev g) {
+    batch_for(g, [](const BatchItem& it, long long z) { zone_emf<R>(it.a, z); });
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) kb_ct(BatchGroupDev g) {
+    batch_for(g, [](const BatchItem& it, long long z) { zone_ct<R>(it.a, it.Bf, 1.0, 1, z); });
+}
+
+// Phases of one step, in order; a group runs those that apply to it.
+enum BatchPhase { PH_FACE_B = 0, PH_WENO1D, PH_CROSS1, PH_CROSS2, PH_PREDICT, PH_UPDATE, PH_EMF, PH_CT, PH_COUNT };
+
+inline bool batch_phase_applies(int ph, int order, int mhd) {
+    switch (ph) {
+        case PH_FACE_B: return mhd != 0;
+        case PH_CROSS1: return order >= 3;
+        case PH_CROSS2: return order == 4;
+        case PH_EMF:
+        case PH_CT: return mhd != 0;
+        default: return true;
+    }
+}
+
+// Launches phase ph of a group of (ORDER, NV) problems with `threads` zones per
+// block and `blocks` blocks; returns the kernel (for occupancy queries) through
+// *fn when launch is false.  Instantiated per (ORDER, NV) in batch_o*_*.cu (FP32 bulk).
+template <int ORDER, int NV>
+int batch_phase(int ph, const BatchGroupDev& g, int form, int solver, int threads, int blocks, cudaStream_t st,
+                bool launch, const void** fn);
+
+}  // namespace ader

@@ -1,0 +1,4 @@
+// Batched order-2 mhd phases in FP32 bulk (see batch_inst.cuh).
+#define ADER_BORDER 2
+#define ADER_BNV 8
+#include "batch_inst.cuh"

@@ -9,7 +9,7 @@
 namespace ader {
 
 // Device error flag bits (turned into ADER_ERR_* by ader_sync_status).
-enum : unsigned { FLAG_UNPHYSICAL = 1u, FLAG_NONFINITE = 2u, FLAG_NOT_CONVERGED = 4u };
+enum : unsigned { FLAG_UNPHYSICAL = 1u, FLAG_NONFINITE = 2u, FLAG_NOT_CONVERGED = 4u, FLAG_TIMEOUT = 8u };
 
 // A vector of NV conserved variables in precision R.  The modal formulas of
 // the paper are written on whole vectors, one arithmetic statement for all

@@ -1,0 +1,325 @@
+// Learned predictor guess on the 5th-generation tensor cores (tcgen05).
+//
+// One CTA of 128 threads handles tiles of 128 zones (persistent over the
+// grid).  Each thread computes its zone's features (mlp.cuh) and writes them
+// as FP16 into the A operand in shared memory; one thread issues the three
+// layers as tcgen05.mma (kind::f16, M = 128, FP32 accumulator in 128 TMEM
+// columns); after each layer every warp reads its 32 accumulator lanes back
+// with tcgen05.ld, adds the bias, applies GELU (tanh form, hardware tanh) and
+// writes the next A operand.  The weights are converted to FP16 once per CTA.
+//
+// Operand layout: K-major, no swizzle.  A tile of R rows and K columns is
+// stored as 8 x 8 "core matrices" (8 rows of 16 bytes, 128 contiguous bytes);
+// core matrix (row group rg, column chunk kc) sits at byte
+// (rg * K/8 + kc) * 128, so the descriptor's leading byte offset (next chunk
+// along K) is 128 and its stride byte offset (next 8-row group) is K/8 * 128.
+//
+// Every wait on the MMA barrier is bounded: on time-out the CTA raises
+// FLAG_TIMEOUT, waits once more (bounded) for its MMAs, frees its TMEM and
+// returns.
+#include <cuda_fp16.h>
+
+#include "kernels.cuh"
+#include "mlp.cuh"
+#include "step_kernels.cuh"
+
+namespace ader {
+namespace {
+
+constexpr int TM = 128;                  // zones per tile = MMA M = TMEM lanes
+constexpr unsigned TMEM_COLS = 128;      // accumulator columns: the widest layer
+constexpr long long WAIT_LIMIT = 1ll << 22;
+
+__host__ __device__ constexpr int k1pad(int nv) { return (mlp_in(nv) + 15) / 16 * 16; }
+__host__ __device__ constexpr int n3pad(int nv) { return (mlp_out(nv) + 15) / 16 * 16; }
+
+template <int NV>
+struct TcSmem {
+    static constexpr int H = MLP_HIDDEN, K1 = k1pad(NV), N3 = n3pad(NV);
+    __half W1[H * K1];      // B of layer 1: H rows (outputs) x K1
+    __half W2[H * H];       // B of layer 2
+    __half W3[N3 * H];      // B of layer 3: N3 rows x H
+    __half A[TM * H];       // A: features (TM x K1), then the hidden layers (TM x H)
+    float b1[H], b2[H], b3[N3];
+    unsigned long long mbar;
+    unsigned tmem_base;
+};
+
+// element offset of (row r, column k) in a K-major core-matrix tile with K columns
+__device__ __forceinline__ int koff(int r, int k, int K) {
+    return (((r >> 3) * (K >> 3) + (k >> 3)) * 8 + (r & 7)) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);     // no swizzle
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B FP16, both K-major
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+    for (long long i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive accumulator columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// GELU, tanh form, with the hardware tanh approximation
+__device__ __forceinline__ float gelu_tc(float x) {
+    const float u = 0.7978845608028654f * fmaf(0.044715f * x, x * x, x);
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+    return 0.5f * x * (1.0f + t);
+}
+
+// the K steps of one layer: D[tmem] = A (TM x K) * B^T (N x K)
+__device__ __forceinline__ void issue_layer(uint32_t tmem, const __half* A, const __half* B, int K, int N) {
+    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+    const uint32_t id = idesc_f16(TM, N);
+    for (int ks = 0; ks < K / 16; ++ks)
+        mma_f16(tmem, sdesc(A + ks * 128, 128u, sbo), sdesc(B + ks * 128, 128u, sbo), id, ks > 0 ? 1u : 0u);
+}
+
+// accumulator + bias -> GELU -> FP16 into the A operand (K = H) at this thread's row
+template <int NV>
+__device__ __forceinline__ void hidden_epilogue(TcSmem<NV>& s, const float* bias, uint32_t tlane, int row) {
+    constexpr int H = MLP_HIDDEN;
+#pragma unroll 1
+    for (int c = 0; c < H; c += 16) {
+        float v[16];
+        tmem_ld16(tlane + (uint32_t)c, v);
+        __align__(16) __half h[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h[j] = __float2half_rn(gelu_tc(v[j] + bias[c + j]));
+        *reinterpret_cast<uint4*>(&s.A[koff(row, c, H)]) = *reinterpret_cast<const uint4*>(&h[0]);
+        *reinterpret_cast<uint4*>(&s.A[koff(row, c + 8, H)]) = *reinterpret_cast<const uint4*>(&h[8]);
+    }
+}
+
+template <int NV, class R>
+__global__ void __launch_bounds__(TM, 1) k_guess_tc(StepArgs a, const double* __restrict__ U) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);   // 1 KB aligned
+    TcSmem<NV>& s = *reinterpret_cast<TcSmem<NV>*>(base);
+    constexpr int IN = mlp_in(NV), OUT = mlp_out(NV), H = MLP_HIDDEN, K1 = k1pad(NV), N3 = n3pad(NV);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // weights -> FP16 operand layout, biases -> FP32
+    const float* W1 = a.guess;
+    const float* b1 = W1 + H * IN;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + OUT * H;
+    for (int e = tid; e < H * K1; e += TM) {
+        const int r = e / K1, k = e % K1;
+        s.W1[koff(r, k, K1)] = __float2half_rn(k < IN ? W1[r * IN + k] : 0.f);
+    }
+    for (int e = tid; e < H * H; e += TM) s.W2[koff(e / H, e % H, H)] = __float2half_rn(W2[e]);
+    for (int e = tid; e < N3 * H; e += TM) {
+        const int r = e / H, k = e % H;
+        s.W3[koff(r, k, H)] = __float2half_rn(r < OUT ? W3[r * H + k] : 0.f);
+    }
+    for (int e = tid; e < H; e += TM) {
+        s.b1[e] = b1[e];
+        s.b2[e] = b2[e];
+    }
+    for (int e = tid; e < N3; e += TM) s.b3[e] = e < OUT ? b3[e] : 0.f;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&s.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tbase = s.tmem_base;
+    const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
+
+    const double dt = a.dt_dev ? *a.dt_dev : a.dt;
+    const double cx = dt / a.dx[0], cy = dt / a.dx[1], cz = dt / a.dx[2];
+    const long long N = a.grid.n;
+    const long long ntiles = (N + TM - 1) / TM;
+    uint32_t parity = 0;
+    bool timed_out = false;
+    auto sync_mma = [&]() -> bool {          // all threads wait for the committed layer
+        const bool ok = mbar_wait(&s.mbar, parity);
+        parity ^= 1u;
+        fence_after();
+        return __syncthreads_or(ok ? 0 : 1) == 0;
+    };
+    for (long long t = blockIdx.x; t < ntiles && !timed_out; t += gridDim.x) {
+        const long long z = t * TM + tid;
+        float sv[NV];
+        bool act = false;
+        {
+            float x[K1];
+#pragma unroll
+            for (int k = 0; k < K1; ++k) x[k] = 0.f;
+            if (z < N) {
+                Vec<NV, R> m[11];
+                load_modes<3>(a, U, z, m);
+                const GuessScales<NV, R> sc = guess_scales<NV, R>(m, cx, cy, cz);
+                const double mag = sc.ok ? guess_features<NV, R>(m, sc, cx, cy, cz, x) : 0.0;
+                act = mag > GUESS_MAG_MIN;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sv[v] = act ? (float)(sc.s[v] * sc.sigma * mag) : 0.f;
+            }
+            if (!act) {
+#pragma unroll
+                for (int k = 0; k < K1; ++k) x[k] = 0.f;
+            }
+#pragma unroll
+            for (int kc = 0; kc < K1; kc += 8) {
+                __align__(16) __half h[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) h[j] = __float2half_rn(x[kc + j]);
+                *reinterpret_cast<uint4*>(&s.A[koff(tid, kc, K1)]) = *reinterpret_cast<const uint4*>(h);
+            }
+        }
+        // layer 1
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+            issue_layer(tbase, s.A, s.W1, K1, H);
+            mma_commit(&s.mbar);
+        }
+        if (!sync_mma()) { timed_out = true; break; }
+        hidden_epilogue<NV>(s, s.b1, tlane, tid);
+        // layer 2
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+            issue_layer(tbase, s.A, s.W2, H, H);
+            mma_commit(&s.mbar);
+        }
+        if (!sync_mma()) { timed_out = true; break; }
+        hidden_epilogue<NV>(s, s.b2, tlane, tid);
+        // layer 3
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+            issue_layer(tbase, s.A, s.W3, H, N3);
+            mma_commit(&s.mbar);
+        }
+        if (!sync_mma()) { timed_out = true; break; }
+#pragma unroll
+        for (int c = 0; c < N3; c += 16) {
+            float v[16];
+            tmem_ld16(tlane + (uint32_t)c, v);
+            if (z < N) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int o = c + j;
+                    if (o < OUT) a.G[(long long)o * N + z] = act ? (v[j] + s.b3[o]) * sv[o % NV] : 0.f;
+                }
+            }
+        }
+        fence_before();
+        __syncthreads();         // the next tile's layer 1 overwrites A and the accumulator
+        fence_after();
+    }
+    if (timed_out) {
+        if (tid == 0) raise_flag(a.flag, FLAG_TIMEOUT);
+        mbar_wait(&s.mbar, parity ^ 1u);     // bounded: let the MMAs in flight finish before TMEM is freed
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+}
+
+template <int NV, class R>
+int launch_nv(const StepArgs& a, const double* U, cudaStream_t st) {
+    static int max_blocks_dev[64] = {};     // per instantiation and device: resident CTAs per SM x SMs
+    const size_t smem = sizeof(TcSmem<NV>) + 1024;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur < 0 || cur >= 64) return -1;
+    int& max_blocks = max_blocks_dev[cur];
+    if (max_blocks == 0) {
+        if (cudaFuncSetAttribute(k_guess_tc<NV, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return -1;
+        int dev = 0, sms = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_guess_tc<NV, R>, TM, smem) != cudaSuccess || occ < 1)
+            return -1;
+        max_blocks = sms * occ;
+    }
+    const long long tiles = (a.grid.n + TM - 1) / TM;
+    const unsigned blocks = (unsigned)(tiles < max_blocks ? tiles : max_blocks);
+    k_guess_tc<NV, R><<<blocks, TM, smem, st>>>(a, U);
+    return 1;
+}
+
+}  // namespace
+
+template <class R>
+int launch_guess(const StepArgs& a, const double* U, cudaStream_t st) {
+    return a.mhd ? launch_nv<8, R>(a, U, st) : launch_nv<5, R>(a, U, st);
+}
+
+template int launch_guess<double>(const StepArgs&, const double*, cudaStream_t);
+template int launch_guess<float>(const StepArgs&, const double*, cudaStream_t);
+
+}  // namespace ader

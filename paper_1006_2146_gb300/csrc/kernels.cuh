@@ -21,6 +21,8 @@ struct StepArgs {
     int max_iter;
     unsigned long long* stats;   // converged predictor: [0] sum of iterations, [1] max, [2] zones capped
     const float* guess; // learned initial guess: packed MLP weights (order 3), or null
+    float* G;           // learned initial guess per zone: u_11..u_15 (5 x NV x N, FP32), written by the
+                        // guess kernel and read by the predictor; null = start from zero
     double gamma;
     double dx[3];
     double dt;          // used when dt_dev is null
@@ -57,6 +59,9 @@ int launch_max_dt(const Grid& g, const double* U, const double* Bf, double gamma
 // MHD: edge EMFs from the face data in S3, then Eq. 8 on Bf (in place) with step c_host (x *dt_dev)
 template <class R> int launch_emf_ct(const StepArgs& a, double* Bf, double c_host, bool use_dt_dev, cudaStream_t st);
 int launch_guess_samples(const StepArgs& a, const double* U, float* X, float* Y, int* ok, cudaStream_t st);
-int launch_totals(const Grid& g, const double* U, double* totals_dev, double* partial, int nblocks, cudaStream_t st);
+// learned guess of every zone into a.G (order 3; after launch_recon)
+template <class R> int launch_guess(const StepArgs& a, const double* U, cudaStream_t st);
+int launch_totals(const Grid& g, const double* U, const double* Bf, const double dx[3], double* totals_dev,
+                  double* partial, int nblocks, cudaStream_t st);
 
 }  // namespace ader

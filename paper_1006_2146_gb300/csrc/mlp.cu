@@ -32,11 +32,12 @@ __global__ void __launch_bounds__(128) k_guess_samples(StepArgs a, const double*
     const GuessScales<NV, double> g = guess_scales<NV, double>(m, cx, cy, cz);
     float* x = X + z * mlp_in(NV);
     float* y = Y + z * mlp_out(NV);
-    guess_features<NV, double>(m, g, cx, cy, cz, x);
+    const double mag = g.ok ? guess_features<NV, double>(m, g, cx, cy, cz, x) : 0.0;
     PredCtl ctl{2, a.tol, a.max_iter, 0, false};
     o3::predict_modal(m, a.gamma - 1.0, cx, cy, cz, ctl);
-    guess_targets<NV, double>(m, g, y);
-    ok[z] = (g.ok && !ctl.capped) ? 1 : 0;
+    const bool use = g.ok && mag > GUESS_MAG_MIN && !ctl.capped;
+    if (use) guess_targets<NV, double>(m, g, mag, y);
+    ok[z] = use ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- GEMM

@@ -115,7 +115,74 @@ __global__ void k_totals_final(const double* partial, int nblocks, double* out) 
     }
 }
 
-int launch_totals(const Grid& g, const double* U, double* totals_dev, double* partial, int nblocks, cudaStream_t st) {
+// MHD: totals of the five zone variables and of the three face-field arrays,
+// plus the largest |div B| of a zone (the discrete divergence that Eq. 8
+// keeps constant) and the largest |B| on a face.  partial holds 10 values per
+// block: 8 sums, then the two maxima.
+__global__ void __launch_bounds__(256) k_diag_mhd_partial(Grid g, const double* __restrict__ U,
+                                                          const double* __restrict__ Bf, double idx, double idy,
+                                                          double idz, double* partial) {
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double dmax = 0.0, bmax = 0.0;
+    const long long N = g.n;
+    for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < N; z += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s[v] += U[v * N + z];
+        const int i = (int)(z % g.nx);
+        const long long t = z / g.nx;
+        const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+        const double bx = Bf[z], by = Bf[N + z], bz = Bf[2 * N + z];
+        s[5] += bx;
+        s[6] += by;
+        s[7] += bz;
+        const double div = (Bf[nbr(g, i, j, k, 1, 0, 0)] - bx) * idx + (Bf[N + nbr(g, i, j, k, 0, 1, 0)] - by) * idy +
+                           (Bf[2 * N + nbr(g, i, j, k, 0, 0, 1)] - bz) * idz;
+        dmax = fmax(dmax, fabs(div));
+        bmax = fmax(bmax, fmax(fabs(bx), fmax(fabs(by), fabs(bz))));
+    }
+    __shared__ double sh[10][256];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) sh[v][threadIdx.x] = s[v];
+    sh[8][threadIdx.x] = dmax;
+    sh[9][threadIdx.x] = bmax;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v) sh[v][threadIdx.x] += sh[v][threadIdx.x + w];
+            sh[8][threadIdx.x] = fmax(sh[8][threadIdx.x], sh[8][threadIdx.x + w]);
+            sh[9][threadIdx.x] = fmax(sh[9][threadIdx.x], sh[9][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 10) partial[blockIdx.x * 10 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// out[0..7] = totals, out[8] = max |div B| / (max |B| / min(dx, dy, dz)) (0 when B = 0)
+__global__ void k_diag_mhd_final(const double* partial, int nblocks, double dxmin, double* out) {
+    const int v = threadIdx.x;
+    if (v < 8) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partial[b * 10 + v];
+        out[v] = s;
+    } else if (v == 8) {
+        double dm = 0.0, bm = 0.0;
+        for (int b = 0; b < nblocks; ++b) {
+            dm = fmax(dm, partial[b * 10 + 8]);
+            bm = fmax(bm, partial[b * 10 + 9]);
+        }
+        out[8] = bm > 0.0 ? dm * dxmin / bm : 0.0;
+    }
+}
+
+int launch_totals(const Grid& g, const double* U, const double* Bf, const double dx[3], double* totals_dev,
+                  double* partial, int nblocks, cudaStream_t st) {
+    if (Bf) {
+        const double dxmin = fmin(dx[0], fmin(dx[1], dx[2]));
+        k_diag_mhd_partial<<<nblocks, 256, 0, st>>>(g, U, Bf, 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2], partial);
+        k_diag_mhd_final<<<1, 32, 0, st>>>(partial, nblocks, dxmin, totals_dev);
+        return 2;
+    }
     k_totals_partial<<<nblocks, 256, 0, st>>>(g, U, partial);
     k_totals_final<<<1, 32, 0, st>>>(partial, nblocks, totals_dev);
     return 2;

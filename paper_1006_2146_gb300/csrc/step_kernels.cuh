@@ -81,9 +81,16 @@ ADER_DEV void store_face(const StepArgs& a, long long z, const Vec<NV, R>* m, R 
 // Iteration statistics of the converged predictor: sum, maximum and capped zones.
 ADER_DEV void record_iterations(unsigned long long* stats, const PredCtl& ctl) {
 #ifdef __CUDA_ARCH__
-    atomicAdd(&stats[0], (unsigned long long)ctl.iters);
-    atomicMax(&stats[1], (unsigned long long)ctl.iters);
-    if (ctl.capped) atomicAdd(&stats[2], 1ull);
+    // one set of atomics per warp: the counters are shared by every zone of the grid
+    const unsigned mask = __activemask();
+    const unsigned sum = __reduce_add_sync(mask, (unsigned)ctl.iters);
+    const unsigned mx = __reduce_max_sync(mask, (unsigned)ctl.iters);
+    const unsigned capped = __reduce_add_sync(mask, ctl.capped ? 1u : 0u);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) {
+        atomicAdd(&stats[0], (unsigned long long)sum);
+        atomicMax(&stats[1], (unsigned long long)mx);
+        if (capped) atomicAdd(&stats[2], (unsigned long long)capped);
+    }
 #else
     stats[0] += ctl.iters;
     if ((unsigned long long)ctl.iters > stats[1]) stats[1] = ctl.iters;
@@ -103,7 +110,12 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
     const R cx = R(dt / a.dx[0]), cy = R(dt / a.dx[1]), cz = R(dt / a.dx[2]);
     if (a.n_iter > 0) {      // n_iter = 0: spatial polynomial only (SSP-RK face rule)
         if constexpr (ORDER == 3) {
-            if (a.guess) learned_guess(a.guess, m, R(a.gamma), cx, cy, cz);
+            if (a.G) {          // learned initial guess of the evolutionary modes
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) m[11 + j][v] = R(a.G[(long long)(j * NV + v) * a.grid.n + z]);
+            }
         }
         PredCtl ctl{a.n_iter, a.tol, a.max_iter, 0, false};
         if (FORM == FORM_MODAL)

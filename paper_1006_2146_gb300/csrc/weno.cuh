@@ -12,6 +12,44 @@ ADER_DEV R wsq(R is) {
     return t * t;
 }
 
+// Unnormalised nonlinear weights a[s] and their normaliser inv, such that the
+// blend is (sum_s a[s] x_s) * inv = sum_s w_s x_s with
+// w_s = (g_s / q_s) / sum_r (g_r / q_r), q = (eps + IS)^2.
+// FP64 clears the denominators, a[s] = g_s prod_{r != s} q_r: one division
+// per blend instead of S + 1.  Every q is at least 1e-24, so the products of
+// up to three of them stay far inside the FP64 range.  FP32 keeps the quotient
+// form, where such products would underflow.  g may be any positive multiple
+// of the linear weights: the normalisation removes it.
+template <int S, class R>
+ADER_DEV R weno_weights(const R* g, const R* is, R* a) {
+    if constexpr (sizeof(R) == 8) {
+        R q[S], pre[S], suf[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) q[s] = wsq(is[s]);
+        pre[0] = R(1);
+#pragma unroll
+        for (int s = 1; s < S; ++s) pre[s] = pre[s - 1] * q[s - 1];
+        suf[S - 1] = R(1);
+#pragma unroll
+        for (int s = S - 2; s >= 0; --s) suf[s] = suf[s + 1] * q[s + 1];
+        R d = R(0);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            a[s] = g[s] * (pre[s] * suf[s]);
+            d += a[s];
+        }
+        return R(1) / d;
+    } else {
+        R d = R(0);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            a[s] = g[s] / wsq(is[s]);
+            d += a[s];
+        }
+        return rcp(d);
+    }
+}
+
 // order-3 1-D WENO on the five values a[-2..2] (a[2] = centre); returns b, c
 template <class R>
 ADER_DEV void weno3(const R* a, R& b, R& c) {
@@ -20,12 +58,12 @@ ADER_DEV void weno3(const R* a, R& b, R& c) {
     const R bC = R(0.5) * (up1 - um1), cC = R(0.5) * (up1 - R(2) * u0 + um1);
     const R bR = R(0.5) * (R(-3) * u0 + R(4) * up1 - up2), cR = R(0.5) * (u0 - R(2) * up1 + up2);
     const R k13 = R(13.0 / 3.0);
-    const R aL = R(1.0 / 12.0) / wsq(bL * bL + k13 * cL * cL);
-    const R aC = R(10.0 / 12.0) / wsq(bC * bC + k13 * cC * cC);
-    const R aR = R(1.0 / 12.0) / wsq(bR * bR + k13 * cR * cR);
-    const R inv = rcp(aL + aC + aR);
-    b = (aL * bL + aC * bC + aR * bR) * inv;
-    c = (aL * cL + aC * cC + aR * cR) * inv;
+    const R g[3] = {R(1), R(10), R(1)};                       // (1, 10, 1) / 12
+    const R is[3] = {bL * bL + k13 * cL * cL, bC * bC + k13 * cC * cC, bR * bR + k13 * cR * cR};
+    R al[3];
+    const R inv = weno_weights<3>(g, is, al);
+    b = (al[0] * bL + al[1] * bC + al[2] * bR) * inv;
+    c = (al[0] * cL + al[1] * cC + al[2] * cR) * inv;
 }
 
 // order-4 1-D WENO on the seven values a[-3..3] (a[3] = centre); returns b, c, d
@@ -49,16 +87,14 @@ ADER_DEV void weno4(const R* a, R& b, R& c, R& d) {
     cb[3] = (R(177) * up1 - R(109) * u0 - R(87) * up2 + R(19) * up3) * R(1.0 / 60.0);
     cc[3] = (R(2) * u0 - R(5) * up1 + R(4) * up2 - up3) * R(0.5);
     cd[3] = (R(3) * up1 - u0 - R(3) * up2 + up3) * R(1.0 / 6.0);
-    const R g[4] = {R(1.0 / 22.0), R(10.0 / 22.0), R(10.0 / 22.0), R(1.0 / 22.0)};
-    R al[4], s = R(0);
+    const R g[4] = {R(1), R(10), R(10), R(1)};                // (1, 10, 10, 1) / 22
+    R al[4], is[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const R t = cb[q] + R(0.1) * cd[q];
-        const R is = t * t + R(13.0 / 3.0) * cc[q] * cc[q] + R(781.0 / 20.0) * cd[q] * cd[q];
-        al[q] = g[q] / wsq(is);
-        s += al[q];
+        is[q] = t * t + R(13.0 / 3.0) * cc[q] * cc[q] + R(781.0 / 20.0) * cd[q] * cd[q];
     }
-    const R inv = rcp(s);
+    const R inv = weno_weights<4>(g, is, al);
     b = (al[0] * cb[0] + al[1] * cb[1] + al[2] * cb[2] + al[3] * cb[3]) * inv;
     c = (al[0] * cc[0] + al[1] * cc[1] + al[2] * cc[2] + al[3] * cc[3]) * inv;
     d = (al[0] * cd[0] + al[1] * cd[1] + al[2] * cd[2] + al[3] * cd[3]) * inv;
@@ -195,11 +231,12 @@ ADER_DEV void zone_face_b(const Grid& g, const double* __restrict__ Bf, R* __res
             const R s1[3] = {(R(8) * Bm - Bmm + R(5) * Bp) * R(1.0 / 12.0), Bp - Bm, (Bp + Bmm - R(2) * Bm) * R(0.5)};
             const R s2[3] = {(R(8) * Bp - Bpp + R(5) * Bm) * R(1.0 / 12.0), Bp - Bm, (Bm + Bpp - R(2) * Bp) * R(0.5)};
             const R k13 = R(13.0 / 3.0);
-            const R a1 = R(0.5) / wsq(s1[1] * s1[1] + k13 * s1[2] * s1[2]);
-            const R a2 = R(0.5) / wsq(s2[1] * s2[1] + k13 * s2[2] * s2[2]);
-            const R inv = rcp(a1 + a2);
+            const R g[2] = {R(1), R(1)};                      // (1/2, 1/2)
+            const R is[2] = {s1[1] * s1[1] + k13 * s1[2] * s1[2], s2[1] * s2[1] + k13 * s2[2] * s2[2]};
+            R al[2];
+            const R inv = weno_weights<2>(g, is, al);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) m[r] = (a1 * s1[r] + a2 * s2[r]) * inv;
+            for (int r = 0; r < 3; ++r) m[r] = (al[0] * s1[r] + al[1] * s2[r]) * inv;
         } else {
             const R Bmm = at(-1), Bmmm = at(-2), Bpp = at(2), Bppp = at(3);
             const R c[3][4] = {
@@ -215,15 +252,14 @@ ADER_DEV void zone_face_b(const Grid& g, const double* __restrict__ Bf, R* __res
                  (-Bppp + R(3) * Bpp + R(57) * Bp - R(59) * Bm) * R(1.0 / 60.0),
                  (-Bppp + R(5) * Bpp - R(7) * Bp + R(3) * Bm) * R(0.25),
                  (Bppp - R(3) * Bpp + R(3) * Bp - Bm) * R(1.0 / 6.0)}};                      // Eq. 28
-            const R gl[3] = {R(0.25), R(0.5), R(0.25)};
-            R al[3], s = R(0);
+            const R gl[3] = {R(1), R(2), R(1)};               // (1/4, 1/2, 1/4)
+            R al[3], is[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const R t = c[q][1] + R(0.1) * c[q][3];
-                al[q] = gl[q] / wsq(t * t + R(13.0 / 3.0) * c[q][2] * c[q][2] + R(781.0 / 20.0) * c[q][3] * c[q][3]);
-                s += al[q];
+                is[q] = t * t + R(13.0 / 3.0) * c[q][2] * c[q][2] + R(781.0 / 20.0) * c[q][3] * c[q][3];
             }
-            const R inv = rcp(s);
+            const R inv = weno_weights<3>(gl, is, al);
 #pragma unroll
             for (int r = 0; r < 4; ++r) m[r] = (al[0] * c[0][r] + al[1] * c[1][r] + al[2] * c[2][r]) * inv;
         }

@@ -223,3 +223,42 @@ def orszag_tang(n, gamma=5.0 / 3.0, rho0=25.0 / (36.0 * np.pi), P0=5.0 / (12.0 *
     eps = P0 / (gamma - 1.0) + 0.5 * rho0 * v2 + (Bx2 + By2) / (2.0 * FOUR_PI)
     U = np.stack([rho, rho0 * vx, rho0 * vy, np.zeros_like(rho), eps])
     return U, Bface
+
+
+def batch_problems(count=64, seed=1006, sizes=(32, 48, 64, 80, 96, 112, 128), mhd_fraction=0.5):
+    """Seeded set of independent problems of uneven cubic sizes for the batched step.
+
+    Each problem draws: its size from `sizes`; Euler or ideal MHD (probability mhd_fraction); its order
+    uniformly from 2, 3, 4; modal or nodal; HLL or linearized (Euler only).  Euler problems are either
+    Gaussian random fields (amplitude 0.1) or planar shock tubes along a lattice normal with density and
+    pressure ratios drawn from [2, 10]; MHD problems are the Orszag-Tang-type vortex shifted by a random
+    periodic offset.  Returns dicts with keys shape, order, mhd, form, solver, gamma, U, B (B None for Euler).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    vortex = {}
+    for k in range(count):
+        n = int(rng.choice(sizes))
+        mhd = bool(rng.random() < mhd_fraction)
+        order = int(rng.integers(2, 5))
+        form = "nodal" if rng.random() < 0.5 else "modal"
+        if mhd:
+            if n not in vortex:
+                vortex[n] = orszag_tang(n)
+            U, B = vortex[n]
+            sh = tuple(int(v) for v in rng.integers(0, n, 3))
+            U = np.roll(U, sh, axis=(1, 2, 3))
+            B = np.roll(B, sh, axis=(1, 2, 3))
+            out.append(dict(shape=(n, n, n), order=order, mhd=True, form=form, solver="hll", gamma=5.0 / 3.0,
+                            U=np.ascontiguousarray(U), B=np.ascontiguousarray(B)))
+            continue
+        solver = "linearized" if rng.random() < 0.5 else "hll"
+        if rng.random() < 0.5:
+            U = random_smooth(n, seed=seed * 1000 + k, amp=0.1)
+        else:
+            normal = [(1, 0, 0), (1, 1, 0), (2, 1, 0)][int(rng.integers(0, 3))]
+            rr, pr = rng.uniform(2.0, 10.0, 2)
+            U = sod_planar(n, normal=normal, left=(1.0, 1.0), right=(1.0 / rr, 1.0 / pr))
+        out.append(dict(shape=(n, n, n), order=order, mhd=False, form=form, solver=solver, gamma=1.4,
+                        U=np.ascontiguousarray(U), B=None))
+    return out

@@ -100,3 +100,32 @@ def test_mhd_rejects_mismatched_arguments(ader):
     with pytest.raises(ader.AderError):
         ader.ader_create(n, n, n, 0.1, 0.1, 0.1, 3, G, ader.ADER_LINEARIZED, ader.ADER_MHD)
     ader.ader_destroy(h)
+
+
+def test_mhd_diagnostics_totals_and_div_b(ader):
+    """Nine diagnostics: zone totals, face-B totals and the relative max |div B|, against numpy sums of the
+    same arrays; after a CT step the face totals are unchanged (periodic telescoping of Eq. 8)."""
+    import torch
+    n = 12
+    U, B = _perturbed_alfven(n, seed=6)
+    dx = (1.0 / n,) * 3
+    B = B.copy()
+    B[0] += 1e-3 * np.random.default_rng(2).standard_normal(B[0].shape)      # a field with nonzero div B
+    h = _mhd_solver(ader, (n, n, n), 3, "modal")
+    dU, dB = to_dev(U), to_dev(B)
+    out = torch.zeros(9, dtype=torch.float64, device="cuda")
+    ader.ader_diagnostics(h, dU, dB, out)
+    got = out.cpu().numpy()
+    want_tot = np.concatenate([U.reshape(5, -1).sum(axis=1), B.reshape(3, -1).sum(axis=1)])
+    scale = np.maximum(np.abs(want_tot), np.abs(U).reshape(5, -1).sum(axis=1).max())
+    assert np.all(np.abs(got[:8] - want_tot) <= 1e-13 * scale)
+    assert got[8] == pytest.approx(_divb_rel(B, dx), rel=1e-12)
+    assert got[8] > 1e-4
+    dt = 0.5 * scheme.max_dt(U, dx, 0.4, G, Bface=B)
+    ader.ader_step(h, dU, dB, dt)
+    out2 = torch.zeros(9, dtype=torch.float64, device="cuda")
+    ader.ader_diagnostics(h, dU, dB, out2)
+    assert ader.ader_sync_status(h) == 0
+    got2 = out2.cpu().numpy()
+    assert np.all(np.abs(got2[:8] - got[:8]) <= 1e-13 * scale)
+    ader.ader_destroy(h)

@@ -95,9 +95,34 @@ def test_guess_samples_match_oracle_features_and_targets(ader):
     Uhat, _ = predictor.predict(W, 3, "modal", 1.4, dt, dx, tol=TOL)
     Xw = omlp.features(W, dt, dx)
     Yw = omlp.targets(W, Uhat, dt, dx)
-    assert bool((ok.cpu() == 1).all())
+    mask = omlp.sample_mask(W)
+    assert mask.all()
+    np.testing.assert_array_equal(ok.cpu().numpy() == 1, mask)
     np.testing.assert_allclose(X.cpu().numpy(), Xw, rtol=2e-7, atol=1e-7)
     np.testing.assert_allclose(Y.cpu().numpy(), Yw, rtol=2e-7, atol=2e-7 * np.abs(Yw).max())
+
+
+def test_guess_samples_skip_uniform_zones(ader):
+    """A planar Sod tube along x: the zones uniform to round-off (all but those next to the two interfaces)
+    are no samples."""
+    import torch
+    shape = (4, 4, 16)
+    U = inputs.sod_planar(shape, normal=(1, 0, 0))
+    dx = _dx(shape)
+    dt = 0.5 * scheme.max_dt(U, dx, 0.4)
+    n_in, _, n_out, _ = ader.ader_mlp_shape(False)
+    n = U[0].size
+    s = ader.Solver(shape, order=3, form="modal")
+    X = torch.zeros((n, n_in), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((n, n_out), dtype=torch.float32, device="cuda")
+    ok = torch.full((n,), 7, dtype=torch.int32, device="cuda")
+    ader.ader_guess_samples(s.h, to_dev(U), None, dt, X, Y, ok)
+    torch.cuda.synchronize()
+    s.close()
+    _, W = scheme.zone_state(U, None, 3)
+    mask = omlp.sample_mask(W)
+    assert 0 < mask.sum() < n
+    np.testing.assert_array_equal(ok.cpu().numpy(), mask.astype(np.int32))
 
 
 def test_mlp_gradient_matches_oracle_backprop(ader):
@@ -123,8 +148,9 @@ def test_mlp_gradient_matches_oracle_backprop(ader):
         assert np.linalg.norm(g - w) <= 1e-4 * np.linalg.norm(w), b
 
 
-def test_learned_guess_saves_iterations(ader):
-    """Train on the samples of two seeded states, then step a third: same converged result, fewer iterations."""
+@pytest.fixture(scope="module")
+def trained_guess(ader):
+    """Guess parameters trained on the samples of three seeded 24^3 states (modal FP64 predictor data)."""
     import torch
     shape = (24, 24, 24)
     dx = _dx(shape)
@@ -143,20 +169,60 @@ def test_learned_guess_saves_iterations(ader):
         keep = ok.bool()
         Xs.append(X[keep])
         Ys.append(Y[keep])
+    s.close()
     X = torch.cat(Xs).contiguous()
     Y = torch.cat(Ys).contiguous()
     P = torch.from_numpy(omlp.init_params(n_in, n_out, seed=11).astype(np.float32)).cuda()
     losses = ader.ader_mlp_train(X, Y, X.shape[0], P, epochs=40, batch=512, lr=2e-3, seed=5)
     assert losses[-1] < 0.5 * losses[0]
+    return P
 
-    U = inputs.random_smooth((16, 16, 16), seed=64, amp=0.3)
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_tensor_core_guess_matches_oracle(ader, trained_guess, fp32):
+    """The step's guess kernel (tcgen05, FP16 operands, FP32 accumulation) against the FP64 numpy network on the
+    oracle's features: within FP16 operand rounding, and exactly zero for zones uniform to round-off."""
+    import torch
+    shape = (12, 11, 13)
+    U = inputs.random_smooth(shape, seed=70, amp=0.3)
+    U[:, :, :, 5:] = U[:, 0:1, 0:1, 5:6]              # a constant band: zones 7..10 see no slope at all
+    dx = _dx(shape)
+    dt = 0.8 * scheme.max_dt(U, dx, 0.4)
+    n = U[0].size
+    s = ader.Solver(shape, order=3, form="modal", fp32=fp32)
+    s.set_guess(trained_guess)
+    G = torch.full((25, n), 7.0, dtype=torch.float32, device="cuda")
+    ader.ader_guess_eval(s.h, to_dev(U), None, dt, G)
+    assert s.status() == 0
+    s.close()
+    got = G.cpu().numpy().reshape(5, 5, *shape)
+    _, W = scheme.zone_state(U, None, 3)
+    want = omlp.guess_modes(trained_guess.cpu().numpy().astype(np.float64), W, dt, dx)
+    mask = omlp.sample_mask(W)
+    assert 0 < mask.sum() < n
+    g = got.reshape(25, n)
+    w = want.reshape(25, n)
+    if fp32:    # FP32 moments of uniform data keep round-off slopes: a guess of that size
+        assert np.abs(g[:, ~mask]).max() <= 1e-5 * np.abs(w).max()
+    else:
+        np.testing.assert_array_equal(g[:, ~mask], 0.0)
+    err = np.linalg.norm(g[:, mask] - w[:, mask]) / np.linalg.norm(w[:, mask])
+    print("tensor-core guess relative L2 error vs FP64 network: %.3e" % err)
+    assert err <= 2e-2
+
+
+@pytest.mark.parametrize("form", ["modal", "nodal"])
+def test_learned_guess_saves_iterations(ader, trained_guess, form):
+    """A fourth, unseen state: the converged result is unchanged and the predictor needs fewer iterations."""
+    P = trained_guess
     shape2 = (16, 16, 16)
+    U = inputs.random_smooth(shape2, seed=64, amp=0.3)
     dx2 = _dx(shape2)
     dt = 0.8 * scheme.max_dt(U, dx2, 0.4)
-    want = scheme.ader_step(U, dx2, dt, 3, "modal", "hll", tol=TOL)
+    want = scheme.ader_step(U, dx2, dt, 3, form, "hll", tol=TOL)
     res = {}
     for use in (False, True):
-        s2 = ader.Solver(shape2, order=3, form="modal")
+        s2 = ader.Solver(shape2, order=3, form=form)
         s2.set_predictor(TOL, 50)
         if use:
             s2.set_guess(P)
@@ -165,11 +231,32 @@ def test_learned_guess_saves_iterations(ader):
         assert s2.status() == 0
         res[use] = (s2.predictor_stats(), to_host(d))
         s2.close()
-    s.close()
     (tot0, _, cap0), got0 = res[False]
     (tot1, _, cap1), got1 = res[True]
     assert cap0 == cap1 == 0
     assert rel_l1(got0, want) <= 1e-12
     assert rel_l1(got1, want) <= 1e-12
-    print("predictor iterations: zero start %d, learned guess %d" % (tot0, tot1))
+    print("predictor iterations (%s): zero start %d, learned guess %d" % (form, tot0, tot1))
     assert tot1 < tot0, (tot0, tot1)
+
+
+def test_fp32_learned_guess_ten_steps(ader, trained_guess):
+    """FP32 bulk, converged predictor (tol 1e-6) started from the learned guess: within 1e-5 relative L1 of
+    the FP64 converged oracle after 10 steps (nodal, third order, HLL)."""
+    shape = (16, 16, 16)
+    dx = _dx(shape)
+    U = inputs.random_smooth(shape, seed=65, amp=0.3)
+    s = ader.Solver(shape, order=3, form="nodal", fp32=True)
+    s.set_predictor(1e-6, 50)
+    s.set_guess(trained_guess)
+    d = to_dev(U)
+    Uo = U.copy()
+    for _ in range(10):
+        dt = scheme.max_dt(Uo, dx, 0.4)
+        Uo = scheme.ader_step(Uo, dx, dt, 3, "nodal", "hll", tol=TOL)
+        s.step(d, dt)
+    assert s.status() == 0
+    tot, mx, capped = s.predictor_stats()
+    s.close()
+    assert capped == 0
+    assert rel_l1(to_host(d), Uo) <= 1e-5

@@ -9,8 +9,8 @@ from paper_1006_2146_gb300 import inputs
 
 
 def test_shape_counts():
-    assert mlp.shape(False) == (51, 128, 25, 128 * 51 + 128 + 128 * 128 + 128 + 25 * 128 + 25)
-    assert mlp.shape(True)[:3] == (81, 128, 40)
+    assert mlp.shape(False) == (52, 128, 25, 128 * 52 + 128 + 128 * 128 + 128 + 25 * 128 + 25)
+    assert mlp.shape(True)[:3] == (82, 128, 40)
 
 
 def test_gelu_against_exact_gelu():
@@ -69,11 +69,11 @@ def test_gradient_matches_finite_differences():
         Pp[i] += h
         Pm[i] -= h
         fd = (mlp.loss_and_grad(Pp, X, Y)[0] - mlp.loss_and_grad(Pm, X, Y)[0]) / (2 * h)
-        assert g[i] == pytest.approx(fd, rel=1e-6, abs=1e-10)
+        assert g[i] == pytest.approx(fd, rel=1e-6, abs=1e-8)    # central-difference round-off ~ 1e-10
 
 
 def test_features_of_uniform_state():
-    """A uniform state at rest: all normalised slopes zero, Courant features c dt/dx, targets zero."""
+    """A uniform state at rest: slope magnitude 0, Courant features c dt/dx, no samples, zero guess."""
     shape = (4, 4, 4)
     U = np.zeros((5,) + shape)
     U[0] = 2.0
@@ -83,11 +83,55 @@ def test_features_of_uniform_state():
     _, W = scheme.zone_state(U, None, 3)
     X = mlp.features(W, dt, dx)
     c = math.sqrt(5.0 / 2.0)
-    assert X.shape == (64, 51)
-    np.testing.assert_allclose(X[:, :48], 0.0, atol=1e-15)
-    np.testing.assert_allclose(X[:, 48:], np.tile([c * dt / 0.25, c * dt / 0.25, c * dt / 0.5], (64, 1)), rtol=1e-15)
+    assert X.shape == (64, 52)
+    np.testing.assert_allclose(X[:, :48], 0.0, atol=1e-15)     # 45 slopes and 3 Mach numbers at rest
+    np.testing.assert_allclose(X[:, 48:51], np.tile([c * dt / 0.25, c * dt / 0.25, c * dt / 0.5], (64, 1)), rtol=1e-15)
+    np.testing.assert_allclose(X[:, 51], 0.0, atol=0)
+    assert not mlp.sample_mask(W).any()
+    n_in, H, n_out, npar = mlp.shape(False)
+    P = mlp.init_params(n_in, n_out, seed=1)
+    P[-n_out:] = 1.0                                  # a network whose output is nonzero everywhere
+    np.testing.assert_array_equal(mlp.guess_modes(P, W, dt, dx), 0.0)
     Uhat, _ = predictor.predict(W, 3, "modal", 1.4, dt, dx, tol=1e-13)
-    np.testing.assert_allclose(mlp.targets(W, Uhat, dt, dx), 0.0, atol=1e-15)
+    np.testing.assert_allclose(Uhat[10:15], 0.0, atol=1e-15)     # the true evolution is zero as well
+
+
+def test_features_are_scale_free():
+    """Slopes over their magnitude: largest |x| is 1; adding a constant to rho and E changes the scales only
+    through w1, and doubling every perturbation doubles g but keeps x[:48] (to first order in the amplitude)."""
+    shape = (6, 6, 6)
+    dx = (1.0 / 6,) * 3
+    # amplitudes small enough for the state to be linear in them (to 1e-4), large enough for the WENO
+    # smoothness indicators to dwarf their 1e-12 regulariser (scale-free weights)
+    U = inputs.random_smooth(shape, seed=12, amp=1e-4)
+    _, W = scheme.zone_state(U, None, 3)
+    X = mlp.features(W, 1e-3, dx)
+    np.testing.assert_allclose(np.abs(X[:, :45]).max(axis=1), 1.0, rtol=1e-15)
+    assert (X[:, 51] > 0).all()
+    U2 = inputs.random_smooth(shape, seed=12, amp=2e-4)
+    _, W2 = scheme.zone_state(U2, None, 3)
+    X2 = mlp.features(W2, 1e-3, dx)
+    np.testing.assert_allclose(X2[:, 51], 2 * X[:, 51], rtol=2e-3)
+    np.testing.assert_allclose(X2[:, :45], X[:, :45], atol=2e-3)
+    np.testing.assert_allclose(X2[:, 45:48], 2 * X[:, 45:48], rtol=2e-3, atol=1e-12)   # Mach numbers ~ amp
+
+
+def test_uniform_moving_flow_has_no_slopes():
+    """A uniform flow in motion: g = 0, Mach-number features v/c, no samples; its evolution is zero."""
+    shape = (4, 4, 4)
+    U = np.zeros((5,) + shape)
+    U[0] = 1.5
+    U[1:4] = 1.5 * np.array([0.3, -0.2, 0.1])[:, None, None, None]
+    U[4] = 4.0
+    dx = (0.25,) * 3
+    _, W = scheme.zone_state(U, None, 3)
+    X = mlp.features(W, 0.01, dx)
+    c = math.sqrt(4.0 / 1.5)
+    np.testing.assert_allclose(X[:, :45], 0.0, atol=1e-15)
+    np.testing.assert_allclose(X[:, 45:48], np.tile(np.array([0.3, -0.2, 0.1]) / c, (64, 1)), rtol=1e-14)
+    assert (X[:, 51] == 0).all() and not mlp.sample_mask(W).any()
+    Uhat, _ = predictor.predict(W, 3, "modal", 1.4, 0.01, dx, tol=1e-13)
+    np.testing.assert_allclose(Uhat[10:15], 0.0, atol=1e-14)
 
 
 def test_targets_roundtrip_through_guess_modes():
@@ -99,6 +143,7 @@ def test_targets_roundtrip_through_guess_modes():
     dt = 0.5 * scheme.max_dt(U, dx, 0.4)
     Uhat, _ = predictor.predict(W, 3, "modal", 1.4, dt, dx, tol=1e-13)
     T = mlp.targets(W, Uhat, dt, dx)
+    assert mlp.sample_mask(W).all()
     n_in, H, n_out, npar = mlp.shape(False)
     P = np.zeros(npar)
     # constant network: b3 = the targets of zone 0, so guess_modes(zone 0) = u_11..u_15 of zone 0
