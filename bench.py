@@ -38,6 +38,11 @@ def parse():
     p.add_argument("--form", default="nodal", choices=["modal", "nodal"])
     p.add_argument("--solver", default="hll", choices=["hll", "linearized"])
     p.add_argument("--fp32", action="store_true")
+    p.add_argument("--converged", type=float, default=None,
+                   help="converged predictor with this tolerance instead of the fixed M-1 iterations")
+    p.add_argument("--learned-guess", action="store_true",
+                   help="train the third-order predictor guess first (untimed), then start the converged "
+                        "predictor from it (tolerance 1e-6 in FP32, 1e-13 in FP64 unless --converged)")
     p.add_argument("--no-variants", action="store_true", help="skip the per-variant table")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -390,13 +395,26 @@ def gpu_arm(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    tol, guess, train_info = args.converged, None, None
+    if args.learned_guess:
+        from paper_1006_2146_gb300 import learned
+        t0 = time.perf_counter()
+        X, Y = learned.make_samples(learned.training_states(96), 96)
+        guess, losses = learned.train(X, Y)
+        torch.cuda.synchronize()
+        train_info = {"samples": int(X.shape[0]), "train_s": time.perf_counter() - t0, "final_loss": losses[-1]}
+        del X, Y
+        if tol is None:
+            tol = 1e-6 if args.fp32 else 1e-13
+
     # headline: timed region bracketed by barrier + synchronize
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
     t0 = time.perf_counter()
     secs, prof, s, d, launches = run_config(ader, torch, n, args.order, args.form, args.solver, args.fp32,
-                                            args.steps, args.warmup, stream, profile=True, state=U0)
+                                            args.steps, args.warmup, stream, profile=True, state=U0, tol=tol,
+                                            guess=guess)
     barrier()
     wall = time.perf_counter() - t0
     ck = clocks.stop()
@@ -407,18 +425,26 @@ def gpu_arm(args):
         secs = float(tt.item())
     value = zones * args.steps * world / secs
 
-    # dominant kernel roofline (ALU-bound: FLOPs per zone x zones / mean launch time)
+    # dominant kernel roofline: FLOPs per zone x zones / mean launch time.  The plain kernels are bound by
+    # the FP64 (or FP32) ALUs; the learned-guess kernel is a dense contraction on the tensor cores.
     fpz = flops_per_zone(args.order, args.form, args.solver, args.fp32)
+    fpz["learned_guess"] = 2.0 * (52 * 128 + 128 * 128 + 128 * 25)       # the MLP's multiply-adds per zone
     kname, (kl, kms) = max(((k, v) for k, v in prof.items()), key=lambda kv: kv[1][1])
     k_avg = kms / kl / 1e3
     achieved = fpz[kname] * zones / k_avg / 1e12 if kname in fpz else None
     sm_mhz = ck.get("sm_mhz") or 2070.0
-    peak = alu_peak_tflops(args.fp32, 2070.0)
+    if kname == "learned_guess":
+        bound, peak = "tensor", peaks().get("bf16_tflops", 1940.9)
+        basis = "measured dense bf16 burst (MEASURED_PEAKS.json); FP16 operands run at the bf16 rate"
+    else:
+        bound, peak = "alu", alu_peak_tflops(args.fp32, 2070.0)
+        basis = "derived: 152 SM x %s at 2070 MHz max clock" % (
+            "128 FFMA/clk" if args.fp32 else "2 DFMA/clk (1.25 TFLOP/s nominal FP64)")
     total_ms = sum(v[1] for v in prof.values())
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    roofline = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
                 "traffic": traffic_per_launch(kname, args.order, args.form, args.fp32, zones),
-                "peak_basis": "derived: 152 SM x %s at 2070 MHz max clock" % ("128 FFMA/clk" if args.fp32 else "2 DFMA/clk (1.25 TFLOP/s nominal FP64)"),
+                "peak_basis": basis,
                 "flops_per_zone": fpz.get(kname), "mean_launch_ms": k_avg * 1e3,
                 "kernel_share": {k: round(v[1] / total_ms, 4) for k, v in prof.items()},
                 "hbm": {"algorithmic_bytes_per_zone_update": 80,
@@ -491,6 +517,8 @@ def gpu_arm(args):
                                        % (n, args.order, args.form, args.solver.upper()),
                            "grid": n, "order": args.order, "form": args.form, "solver": args.solver,
                            "precision": "fp32 bulk + fp64 update" if args.fp32 else "fp64",
+                           "predictor": ("converged, tol %g" % tol if tol else "fixed M-1 iterations") +
+                                        (", learned initial guess" if guess is not None else ""),
                            "l2": "state 671 MB > L2 129 MB (no flush needed)",
                            "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps,
@@ -502,6 +530,8 @@ def gpu_arm(args):
                 "speedup_vs_fp64_plain": lg["zone_updates_per_s"] / value if not args.fp32 else None,
                 "rel_l1_vs_fp64_converged_3steps": lg.get("rel_l1_vs_fp64_converged_3steps"),
                 "mean_predictor_iterations": lg.get("mean_predictor_iterations")}
+        if train_info:
+            line["learned_guess_training"] = train_info
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

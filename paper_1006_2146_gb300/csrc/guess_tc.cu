@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(TM, 1) k_guess_tc(StepArgs a, const double* __
     const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
 
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
-    const double cx = dt / a.dx[0], cy = dt / a.dx[1], cz = dt / a.dx[2];
+    const float cx = (float)(dt / a.dx[0]), cy = (float)(dt / a.dx[1]), cz = (float)(dt / a.dx[2]);
     const long long N = a.grid.n;
     const long long ntiles = (N + TM - 1) / TM;
     uint32_t parity = 0;
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(TM, 1) k_guess_tc(StepArgs a, const double* __
     };
     for (long long t = blockIdx.x; t < ntiles && !timed_out; t += gridDim.x) {
         const long long z = t * TM + tid;
-        float sv[NV];
+        float sv[NV] = {};
         bool act = false;
         {
             float x[K1];
@@ -210,11 +210,8 @@ __global__ void __launch_bounds__(TM, 1) k_guess_tc(StepArgs a, const double* __
             if (z < N) {
                 Vec<NV, R> m[11];
                 load_modes<3>(a, U, z, m);
-                const GuessScales<NV, R> sc = guess_scales<NV, R>(m, cx, cy, cz);
-                const double mag = sc.ok ? guess_features<NV, R>(m, sc, cx, cy, cz, x) : 0.0;
-                act = mag > GUESS_MAG_MIN;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) sv[v] = act ? (float)(sc.s[v] * sc.sigma * mag) : 0.f;
+                const float mag = guess_features_f32<NV, R>(m, cx, cy, cz, x, sv);
+                act = mag > (float)GUESS_MAG_MIN;
             }
             if (!act) {
 #pragma unroll
@@ -297,6 +294,10 @@ int launch_nv(const StepArgs& a, const double* U, cudaStream_t st) {
     int& max_blocks = max_blocks_dev[cur];
     if (max_blocks == 0) {
         if (cudaFuncSetAttribute(k_guess_tc<NV, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return -1;
+        // all of the SM's unified L1/shared storage as shared memory: two CTAs (two tiles) per SM
+        if (cudaFuncSetAttribute(k_guess_tc<NV, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
             cudaSuccess)
             return -1;
         int dev = 0, sms = 0, occ = 0;

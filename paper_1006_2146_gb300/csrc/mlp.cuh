@@ -102,6 +102,47 @@ ADER_DEV double guess_features(const Vec<NV, R>* m, const GuessScales<NV, R>& g,
     return mag;
 }
 
+// The same features in FP32 arithmetic (inference: they feed FP16 operands),
+// plus the output scale of each variable, s_v sigma g, in sv.  Returns g, or
+// 0 where the scales are not positive.
+template <int NV, class R>
+ADER_DEV float guess_features_f32(const Vec<NV, R>* m, float cx, float cy, float cz, float* x, float* sv) {
+    const float rho = (float)m[1][0], E = (float)m[1][4];
+    if (!(rho > 0.f) || !(E > 0.f)) return 0.f;
+    const float c = sqrtf(E / rho);
+    float s[NV];
+    s[0] = rho;
+    s[1] = s[2] = s[3] = rho * c;
+    s[4] = E;
+    if constexpr (NV == 8) s[5] = s[6] = s[7] = sqrtf(8.0f * 3.14159265358979f * E);
+    float inv[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) inv[v] = 1.0f / s[v];
+    float mag = 0.f;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int k = 2; k <= 10; ++k) {
+            x[v * 9 + k - 2] = (float)m[k][v] * inv[v];
+            mag = fmaxf(mag, fabsf(x[v * 9 + k - 2]));
+        }
+    const float im = mag > 0.f ? 1.0f / mag : 0.f;
+#pragma unroll
+    for (int q = 0; q < 9 * NV; ++q) x[q] *= im;
+    int n = 9 * NV;
+#pragma unroll
+    for (int v = 1; v < NV; ++v)
+        if (v != 4) x[n++] = (float)m[1][v] * inv[v];
+    x[n++] = c * cx;
+    x[n++] = c * cy;
+    x[n++] = c * cz;
+    x[n] = mag;
+    const float sigma = c * (cx + cy + cz);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sv[v] = s[v] * sigma * mag;
+    return mag;
+}
+
 // normalised targets of a zone: t[j*NV + v] = u_{11+j}[v] / (s_v sigma g)
 template <int NV, class R>
 ADER_DEV void guess_targets(const Vec<NV, R>* m, const GuessScales<NV, R>& g, double mag, float* t) {
