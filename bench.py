@@ -158,6 +158,54 @@ def rel_l1_dev(got, want):
     return float((num / den).max())
 
 
+def mhd_variants(ader, torch, stream, n=128, steps=3, warmup=1):
+    """Ideal MHD, Orszag-Tang-type vortex extruded in z (n^3, gamma 5/3, third order, modal): zone-updates/s
+    per configuration, and the relative max |div B| after the timed steps (ader_diagnostics)."""
+    from paper_1006_2146_gb300 import _lib, inputs
+    out = {}
+    try:
+        U0, B0 = inputs.orszag_tang(n)
+    except Exception as exc:
+        return {"mhd_inputs": {"error": str(exc)[:200]}}
+    U0 = torch.from_numpy(U0).to("cuda")
+    B0 = torch.from_numpy(B0).to("cuda")
+    zones = n ** 3
+    for name, fp32, solver in (("mhd_ot_fp32_linearized_o3", True, "linearized"),
+                               ("mhd_ot_fp32_hll_o3", True, "hll"),
+                               ("mhd_ot_fp64_linearized_o3", False, "linearized")):
+        h = None
+        try:
+            flags = _lib.ADER_MHD | (_lib.ADER_FP32_BULK if fp32 else 0)
+            h = _lib.ader_create(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n, 3, 5.0 / 3.0,
+                                 _lib.ADER_LINEARIZED if solver == "linearized" else _lib.ADER_HLL, flags)
+            d, b = U0.clone(), B0.clone()
+            dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+            with torch.cuda.stream(stream):
+                for _ in range(warmup):
+                    _lib.ader_max_dt(h, d, b, 0.4, dt, stream)
+                    _lib.ader_step_devdt(h, d, b, dt, stream)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(steps):
+                    _lib.ader_max_dt(h, d, b, 0.4, dt, stream)
+                    _lib.ader_step_devdt(h, d, b, dt, stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            secs = e0.elapsed_time(e1) / 1e3
+            diag = torch.zeros(9, dtype=torch.float64, device="cuda")
+            _lib.ader_diagnostics(h, d, b, diag, stream)
+            st = _lib.ader_sync_status(h, stream)
+            out[name] = {"zone_updates_per_s": zones * steps / secs, "ms_per_step": secs / steps * 1e3,
+                         "grid": n, "status": st, "div_b_rel_after": float(diag[8].item())}
+        except Exception as exc:
+            out[name] = {"error": str(exc)[:200]}
+        finally:
+            if h is not None:
+                _lib.ader_destroy(h)
+    return out
+
+
 def batched_variant(ader, torch, stream, steps=3, warmup=1):
     """64 seeded independent problems of uneven sizes 32^3-128^3 (Euler and MHD, orders 2-4, FP32 bulk):
     one tuned batch replayed from a captured graph vs one context per problem launched in sequence.
@@ -486,6 +534,7 @@ def gpu_arm(args):
             except Exception as exc:          # a variant that fails is reported, not hidden
                 variants[name] = {"error": str(exc)[:200]}
         variants.update(learned_variants(ader, torch, n, U0, stream))
+        variants.update(mhd_variants(ader, torch, stream))
         variants["batched_64_problems_fp32"] = batched_variant(ader, torch, stream)
         # SSP-RK of the same order and solver on the same GPU (Eq. 19), per step
         srk = ader.Solver((n, n, n), order=3, form="nodal", solver="hll")

@@ -43,12 +43,15 @@ typedef struct {
     double dx, dy, dz;       /* zone sizes */
 } ader_grid;
 
-/* Riemann solver at the faces (Sec. II.3, Eq. 56). */
+/* Riemann solver at the faces (Sec. II.3, Eq. 56): HLL, or the linearized
+ * solver with the eigen-structure of the flux Jacobian at the mean of the two
+ * barycentre states (for MHD the seven-wave system; the edge electric fields
+ * of Eq. 7 then use the same solver on the edge-averaged states). */
 enum { ADER_HLL = 0, ADER_LINEARIZED = 1 };
 
 /* Option flags for ader_create. */
 enum {
-    ADER_MHD = 1u << 0,                 /* ideal MHD with face-centred B and constrained transport (HLL only) */
+    ADER_MHD = 1u << 0,                 /* ideal MHD with face-centred B and constrained transport */
     ADER_NODAL = 1u << 1,               /* nodal predictor (Apps. A-C); default modal (Sec. IV) */
     ADER_FP32_BULK = 1u << 2,           /* FP32 reconstruction/predictor/fluxes, FP64 update and reductions */
     ADER_CONVERGED_PREDICTOR = 1u << 4  /* iterate the predictor to tolerance instead of M-1 times */
@@ -72,7 +75,8 @@ typedef struct ader_ctx ader_ctx;
  *            modes, L = 5/15/35 space-time modes, Eqs. 10-16)
  *   gamma  : ratio of specific heats (> 1)
  *   solver : ADER_HLL or ADER_LINEARIZED
- *   flags  : bitwise OR of ADER_NODAL, ADER_FP32_BULK, ADER_CONVERGED_PREDICTOR
+ *   flags  : bitwise OR of ADER_MHD, ADER_NODAL, ADER_FP32_BULK (ADER_CONVERGED_PREDICTOR is
+ *            rejected: use ader_set_predictor)
  * Allocates the device scratch for one step of this grid on the current
  * device.  *out receives the context; on failure *out is NULL. */
 int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigned flags, ader_ctx** out);
@@ -202,7 +206,7 @@ void ader_destroy(ader_ctx* ctx);
  * ADER step (Eq. 6, and Eq. 8 for MHD) per call.  The paper has no batched
  * mode: it runs one problem at a time.  Problems must use ADER_FP32_BULK (FP32
  * reconstruction, predictor and fluxes; FP64 state, update and dt) and the
- * fixed iteration count of the predictor; MHD problems use HLL.
+ * fixed iteration count of the predictor.
  * Problems of the same order, physics, form and solver form a group; each
  * phase of a group is one persistent launch over all its problems, groups run
  * concurrently, and a step is replayed from a CUDA graph captured on the first

@@ -80,10 +80,51 @@ def abs_jacobian(Ustar, gamma, d):
                     P = P @ ((A - lam[:, j, None, None] * eye) / (lam[:, i] - lam[:, j])[:, None, None])
             absA += np.abs(lam[:, i])[:, None, None] * P
         return absA, keep
-    lam, R = np.linalg.eig(A)
-    Rinv = np.linalg.inv(R)
-    absA = np.einsum("nij,nj,njk->nik", R, np.abs(lam), Rinv)
-    return absA.real, keep
+    return _mhd_abs_jacobian(Ustar, gamma, d, A, keep), keep
+
+
+def _mhd_abs_jacobian(Ustar, gamma, d, A, keep):
+    """|A| of the seven-wave MHD system (the row and column of B_d removed), by symmetrisation.
+
+    In primitive variables W = (rho, v, P, B_t1, B_t2) the Jacobian is A_W = M^-1 A M with M = dU/dW.
+    Replacing rho by s = P - a^2 rho separates the entropy wave (eigenvalue v_d); the remaining six rows
+    (v, P, B_t) become symmetric under S = diag(rho, rho, rho, 1/(gamma P), 1/(4 pi), 1/(4 pi)).  So
+    |A| = M T^-1 diag(|v_d|, S^-1/2 |S^1/2 A6 S^-1/2| S^1/2) T M^-1, with the absolute value of the symmetric
+    matrix taken from its orthonormal eigen-decomposition (well conditioned also where wave speeds coincide).
+    """
+    n = Ustar.shape[1]
+    rho = Ustar[0]
+    v = [Ustar[1 + c] / rho for c in range(3)]
+    P = physics.pressure(Ustar, gamma)
+    B = [Ustar[5 + c] for c in range(3)]
+    W = np.stack([rho, v[0], v[1], v[2], P, B[0], B[1], B[2]])          # (8, n)
+    M = np.empty((n, 8, 8))
+    step = 1e-30
+    for j in range(8):
+        Wc = W.astype(np.complex128)
+        Wc[j] += 1j * step
+        Uc = physics.prim_to_cons(Wc[0], Wc[1], Wc[2], Wc[3], Wc[4], gamma, (Wc[5], Wc[6], Wc[7]))
+        M[:, :, j] = (Uc.imag / step).T
+    M = M[:, keep][:, :, keep]
+    AW = np.linalg.solve(M, A @ M)
+    a2 = gamma * P / rho
+    T = np.broadcast_to(np.eye(7), (n, 7, 7)).copy()
+    T[:, 0, 0] = -a2
+    T[:, 0, 4] = 1.0
+    Ti = np.broadcast_to(np.eye(7), (n, 7, 7)).copy()
+    Ti[:, 0, 0] = -1.0 / a2
+    Ti[:, 0, 4] = 1.0 / a2
+    Ap = T @ AW @ Ti
+    sq = np.stack([np.sqrt(rho)] * 3 + [1.0 / np.sqrt(gamma * P)] + [np.full(n, 1.0 / np.sqrt(4.0 * np.pi))] * 2,
+                  axis=1)                                               # S^1/2 of (v, P, B_t1, B_t2)
+    X = sq[:, :, None] * Ap[:, 1:, 1:] / sq[:, None, :]
+    X = 0.5 * (X + np.swapaxes(X, 1, 2))
+    lam, Q = np.linalg.eigh(X)
+    absX = np.einsum("nij,nj,nkj->nik", Q, np.abs(lam), Q)
+    absAp = np.zeros((n, 7, 7))
+    absAp[:, 0, 0] = np.abs(Ap[:, 0, 0])
+    absAp[:, 1:, 1:] = absX / sq[:, :, None] * sq[:, None, :]
+    return M @ (Ti @ absAp @ T) @ np.linalg.inv(M)
 
 
 def linearized(d, gamma, ubL, ubR, uL, uR, FL, FR, zL, zR):

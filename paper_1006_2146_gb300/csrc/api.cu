@@ -174,7 +174,6 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
         return ADER_ERR_ARG;
     const unsigned known = ADER_MHD | ADER_NODAL | ADER_FP32_BULK;
     if (flags & ~known) return ADER_ERR_ARG;        // the converged predictor is set by ader_set_predictor
-    if ((flags & ADER_MHD) && solver != ADER_HLL) return ADER_ERR_ARG;   // MHD: HLL only
     ader_ctx* c = new ader_ctx();
     c->g = *g;
     c->grid.nx = g->nx;
@@ -197,7 +196,7 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
     };
     alloc(&c->S1, N * s1_per_zone(order, mh) * c->rsize, "cudaMalloc S1");
     alloc(&c->S2, N * (s2_per_zone(order, mh) ? s2_per_zone(order, mh) : 1) * c->rsize, "cudaMalloc S2");
-    alloc(&c->S3, N * s3_per_zone(mh) * c->rsize, "cudaMalloc S3");
+    alloc(&c->S3, N * s3_per_zone(mh, solver == ADER_LINEARIZED) * c->rsize, "cudaMalloc S3");
     if (c->mhd) {
         alloc(&c->ZB, N * 3 * c->rsize, "cudaMalloc zone B");
         alloc(&c->E, N * 3 * c->rsize, "cudaMalloc EMF");

@@ -312,7 +312,6 @@ int ader_batch_create(int n, const ader_grid* grids, const int* orders, const do
         if (orders[p] < 2 || orders[p] > 4 || !(gammas[p] > 1.0)) return ADER_ERR_ARG;
         if (solvers[p] != ADER_HLL && solvers[p] != ADER_LINEARIZED) return ADER_ERR_ARG;
         if ((flags[p] & ~known) || !(flags[p] & ADER_FP32_BULK)) return ADER_ERR_ARG;   // FP32 bulk only
-        if ((flags[p] & ADER_MHD) && solvers[p] != ADER_HLL) return ADER_ERR_ARG;
     }
     ader_batch* b = new ader_batch();
     b->n = n;
@@ -334,7 +333,7 @@ int ader_batch_create(int n, const ader_grid* grids, const int* orders, const do
         off[p] = bytes;
         const int m = b->mhd[p];
         const size_t per = (size_t)(s1_per_zone(orders[p], m) + std::max(1, s2_per_zone(orders[p], m)) +
-                                    s3_per_zone(m)) + (m ? 6 : 0);
+                                    s3_per_zone(m, solvers[p] == ADER_LINEARIZED)) + (m ? 6 : 0);
         bytes += align(per * (size_t)N * sizeof(float) + 5 * 256);
     }
     bool ok = cudaMalloc(&b->arena, bytes) == cudaSuccess;
@@ -379,7 +378,7 @@ int ader_batch_create(int n, const ader_grid* grids, const int* orders, const do
         };
         a.S1 = take((size_t)s1_per_zone(orders[p], m) * N);
         a.S2 = take((size_t)std::max(1, s2_per_zone(orders[p], m)) * N);
-        a.S3 = take((size_t)s3_per_zone(m) * N);
+        a.S3 = take((size_t)s3_per_zone(m, solvers[p] == ADER_LINEARIZED) * N);
         a.ZB = m ? take((size_t)3 * N) : nullptr;
         a.E = m ? take((size_t)3 * N) : nullptr;
         b->items.push_back(it);

@@ -28,7 +28,8 @@ int batch_phase(int ph, const BatchGroupDev& g, int form, int solver, int thread
             break;
         case PH_UPDATE:
             if constexpr (NV == 8)
-                k = (const void*)kb_flux_update<SOLVER_HLL, 8, R>;
+                k = solver == SOLVER_LINEARIZED ? (const void*)kb_flux_update<SOLVER_LINEARIZED, 8, R>
+                                                : (const void*)kb_flux_update<SOLVER_HLL, 8, R>;
             else
                 k = solver == SOLVER_LINEARIZED ? (const void*)kb_flux_update<SOLVER_LINEARIZED, 5, R>
                                                 : (const void*)kb_flux_update<SOLVER_HLL, 5, R>;

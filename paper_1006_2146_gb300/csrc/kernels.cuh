@@ -43,7 +43,12 @@ inline int s1_per_zone(int order, int mhd) { return nvar(mhd) * 3 * (order - 1);
 inline int s2_per_zone(int order, int mhd) { return order == 2 ? 0 : nvar(mhd) * (order == 3 ? 3 : 10); }
 // face-side values per side: u_b, <u>, <F> (NV each) and, for MHD, 4 edges x (<u_c>, <F_c>)
 ADER_DEV constexpr int side_values(int nv) { return 3 * nv + (nv == 8 ? 8 : 0); }
-inline int s3_per_zone(int mhd) { return 6 * side_values(nvar(mhd)); }
+// MHD with the linearized solver also keeps every edge's full averaged state: a second block of
+// 6 sides x 4 edges x 8 components after the 6 x side_values(8) of the first
+constexpr int EDGE_STATE_VALUES = 4 * 8;
+inline int s3_per_zone(int mhd, int linearized = 0) {
+    return 6 * side_values(nvar(mhd)) + (mhd && linearized ? 6 * EDGE_STATE_VALUES : 0);
+}
 
 template <class R> int launch_recon(const StepArgs& a, const double* U, cudaStream_t st);
 template <int ORDER, int NV, class R> int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st);

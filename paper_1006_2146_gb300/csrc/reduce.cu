@@ -222,8 +222,10 @@ int launch_flux_update(const StepArgs& a, double* out, const double* base, doubl
     const int T = 128;
     const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
     const int dd = use_dt_dev ? 1 : 0;
-    if (a.mhd)
+    if (a.mhd && a.solver == SOLVER_HLL)
         k_flux_update<SOLVER_HLL, 8, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+    else if (a.mhd)
+        k_flux_update<SOLVER_LINEARIZED, 8, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
     else if (a.solver == SOLVER_HLL)
         k_flux_update<SOLVER_HLL, 5, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
     else

@@ -25,6 +25,10 @@ namespace ader {
                                       R* ef) {                                                                       \
             o##O::face_mhd<D>(p, gm1, ub, avg, Fa, eu, ef);                                                           \
         }                                                                                                            \
+        template <int D, class R>                                                                                    \
+        static ADER_DEV void edge_states(const Vec<8, R>* p, const Vec<8, R>& ub, const Vec<8, R>& avg, Vec<8, R>* e) { \
+            o##O::edge_states<D>(p, ub, avg, e);                                                                      \
+        }                                                                                                            \
     };
 
 #ifndef ADER_ZONEOPS_DEFINED

@@ -75,6 +75,15 @@ ADER_DEV void store_face(const StepArgs& a, long long z, const Vec<NV, R>* m, R 
             S3[(side * NQ + 3 * NV + 2 * e) * N + z] = eu[e];
             S3[(side * NQ + 3 * NV + 2 * e + 1) * N + z] = ef[e];
         }
+        if (a.solver == SOLVER_LINEARIZED) {      // the linearized edge fluxes need every component
+            Vec<8, R> es[4];
+            ZoneOps<ORDER>::template edge_states<D>(p, ub, avg, es);
+            R* X = S3 + (long long)6 * NQ * N;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) X[(side * EDGE_STATE_VALUES + e * 8 + v) * N + z] = es[e][v];
+        }
     }
 }
 
@@ -227,6 +236,36 @@ ADER_DEV R edge_hll(const StepArgs& a, long long zl, long long zr, int e, R gamm
     return (lamR * FL - lamL * FR + lamR * lamL * (uR - uL)) / (lamR - lamL);
 }
 
+// The same flux with the linearized solver: |A| at the mean of the face's two
+// barycentre states applied to the jump of the full edge-averaged states.
+template <int D, class R>
+ADER_DEV R edge_linearized(const StepArgs& a, long long zl, long long zr, int e, R gamma, R gm1) {
+    constexpr int NQ = side_values(8);
+    constexpr int T1 = D == 0 ? 1 : 0, T2 = D == 2 ? 1 : 2;
+    const R* S3 = (const R*)a.S3;
+    const R* X = S3 + (long long)6 * NQ * a.grid.n;
+    const long long N = a.grid.n;
+    const int sl = 2 * D, sr = 2 * D + 1;
+    Vec<8, R> ubl, ubr, dU;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        ubl[v] = S3[(sl * NQ + v) * N + zl];
+        ubr[v] = S3[(sr * NQ + v) * N + zr];
+        dU[v] = X[(sr * EDGE_STATE_VALUES + e * 8 + v) * N + zr] - X[(sl * EDGE_STATE_VALUES + e * 8 + v) * N + zl];
+    }
+    const MeanState<R> m = mhd_mean_state(ubl, ubr, gm1);
+    const Vec<8, R> diss = mhd_abs_jacobian_apply<D, R>(m.rho, m.v, m.p, m.B, gamma, gm1, dU);
+    const int c = 5 + (e < 2 ? T1 : T2);
+    const R FL = S3[(sl * NQ + 25 + 2 * e) * N + zl], FR = S3[(sr * NQ + 25 + 2 * e) * N + zr];
+    return R(0.5) * (FL + FR) - R(0.5) * diss[c];
+}
+
+template <int D, class R>
+ADER_DEV R edge_flux(const StepArgs& a, long long zl, long long zr, int e, R gamma, R gm1) {
+    return a.solver == SOLVER_LINEARIZED ? edge_linearized<D, R>(a, zl, zr, e, gamma, gm1)
+                                         : edge_hll<D, R>(a, zl, zr, e, gamma, gm1);
+}
+
 // EMFs at the three upper edges of zone (i, j, k): Ez on (i+1/2, j+1/2),
 // Ey on (i+1/2, k+1/2), Ex on (j+1/2, k+1/2); each the mean of the four
 // adjacent faces' edge fluxes with Eq. 7's signs (Ez = -F7 = G6,
@@ -241,12 +280,12 @@ ADER_DEV void zone_emf(const StepArgs& a, long long z) {
     const long long zx = nbr(g, i, j, k, 1, 0, 0), zy = nbr(g, i, j, k, 0, 1, 0), zz = nbr(g, i, j, k, 0, 0, 1);
     const long long zxy = nbr(g, i, j, k, 1, 1, 0), zxz = nbr(g, i, j, k, 1, 0, 1), zyz = nbr(g, i, j, k, 0, 1, 1);
     // x-faces: t1 = y (slots 0, 1), t2 = z (2, 3); y-faces: t1 = x, t2 = z; z-faces: t1 = x, t2 = y
-    const R Ez = R(0.25) * (-edge_hll<0, R>(a, z, zx, 0, gamma, gm1) - edge_hll<0, R>(a, zy, zxy, 1, gamma, gm1) +
-                            edge_hll<1, R>(a, z, zy, 0, gamma, gm1) + edge_hll<1, R>(a, zx, zxy, 1, gamma, gm1));
-    const R Ey = R(0.25) * (edge_hll<0, R>(a, z, zx, 2, gamma, gm1) + edge_hll<0, R>(a, zz, zxz, 3, gamma, gm1) -
-                            edge_hll<2, R>(a, z, zz, 0, gamma, gm1) - edge_hll<2, R>(a, zx, zxz, 1, gamma, gm1));
-    const R Ex = R(0.25) * (-edge_hll<1, R>(a, z, zy, 2, gamma, gm1) - edge_hll<1, R>(a, zz, zyz, 3, gamma, gm1) +
-                            edge_hll<2, R>(a, z, zz, 2, gamma, gm1) + edge_hll<2, R>(a, zy, zyz, 3, gamma, gm1));
+    const R Ez = R(0.25) * (-edge_flux<0, R>(a, z, zx, 0, gamma, gm1) - edge_flux<0, R>(a, zy, zxy, 1, gamma, gm1) +
+                            edge_flux<1, R>(a, z, zy, 0, gamma, gm1) + edge_flux<1, R>(a, zx, zxy, 1, gamma, gm1));
+    const R Ey = R(0.25) * (edge_flux<0, R>(a, z, zx, 2, gamma, gm1) + edge_flux<0, R>(a, zz, zxz, 3, gamma, gm1) -
+                            edge_flux<2, R>(a, z, zz, 0, gamma, gm1) - edge_flux<2, R>(a, zx, zxz, 1, gamma, gm1));
+    const R Ex = R(0.25) * (-edge_flux<1, R>(a, z, zy, 2, gamma, gm1) - edge_flux<1, R>(a, zz, zyz, 3, gamma, gm1) +
+                            edge_flux<2, R>(a, z, zz, 2, gamma, gm1) + edge_flux<2, R>(a, zy, zyz, 3, gamma, gm1));
     R* E = (R*)a.E;
     E[z] = Ex;
     E[g.n + z] = Ey;

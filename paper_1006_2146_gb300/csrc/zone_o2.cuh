@@ -93,5 +93,16 @@ ADER_DEV void face_mhd(const Vec<8, R>* p, R gm1, Vec<8, R>& ub, Vec<8, R>& avg,
     }
 }
 
+// Full edge-averaged states (all eight components; Eq. 60) for the
+// linearized edge fluxes.  Slots as in face_mhd.
+template <int D, class R>
+ADER_DEV void edge_states(const Vec<8, R>* p, const Vec<8, R>& ub, const Vec<8, R>& avg, Vec<8, R>* e) {
+    (void)avg;
+    e[0] = ub + 0.5 * p[3];
+    e[1] = ub - 0.5 * p[3];
+    e[2] = ub + 0.5 * p[4];
+    e[3] = ub - 0.5 * p[4];
+}
+
 }  // namespace o2
 }  // namespace ader

@@ -267,5 +267,18 @@ ADER_DEV void face_mhd(const Vec<8, R>* p, R gm1, Vec<8, R>& ub, Vec<8, R>& avg,
     }
 }
 
+// Full edge-averaged states (all eight components; Eq. 63) for the
+// linearized edge fluxes.  Slots as in face_mhd.
+template <int D, class R>
+ADER_DEV void edge_states(const Vec<8, R>* p, const Vec<8, R>& ub, const Vec<8, R>& avg, Vec<8, R>* e) {
+    (void)ub;
+    const Vec<8, R> q1 = 0.5 * p[3] + 0.25 * (p[8] + p[14]), q2 = 0.5 * p[4] + 0.25 * (p[10] + p[15]);
+    const Vec<8, R> u1 = avg + p[6] / 6.0 + q1, u2 = avg + p[7] / 6.0 + q2;
+    e[0] = u1;
+    e[1] = u1 - 2.0 * q1;
+    e[2] = u2;
+    e[3] = u2 - 2.0 * q2;
+}
+
 }  // namespace o3
 }  // namespace ader

@@ -467,5 +467,20 @@ ADER_DEV void face_mhd(const Vec<8, R>* p, R gm1, Vec<8, R>& ub, Vec<8, R>& avg,
     }
 }
 
+// Full edge-averaged states (all eight components; Eq. 66) for the
+// linearized edge fluxes.  Slots as in face_mhd.
+template <int D, class R>
+ADER_DEV void edge_states(const Vec<8, R>* p, const Vec<8, R>& ub, const Vec<8, R>& avg, Vec<8, R>* e) {
+    (void)ub;
+    const Vec<8, R> q1 = p[3] + 0.5 * (p[8] + p[25]) + 0.25 * p[33] + 0.1 * p[12] + (p[14] + 2.0 * p[28]) / 6.0;
+    const Vec<8, R> q2 = p[4] + 0.5 * (p[10] + p[26]) + 0.25 * p[35] + 0.1 * p[13] + (p[15] + 2.0 * p[29]) / 6.0;
+    const Vec<8, R> u1 = avg + (2.0 * p[6] + p[16] + p[31]) / 12.0 + 0.5 * q1;
+    const Vec<8, R> u2 = avg + (2.0 * p[7] + p[18] + p[32]) / 12.0 + 0.5 * q2;
+    e[0] = u1;
+    e[1] = u1 - q1;
+    e[2] = u2;
+    e[3] = u2 - q2;
+}
+
 }  // namespace o4
 }  // namespace ader

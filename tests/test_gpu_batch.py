@@ -20,7 +20,7 @@ MIX = [((8, 9, 10), 3, "euler", "nodal", "hll", 1),
        ((5, 16, 7), 4, "euler", "modal", "hll", 3),
        ((10, 6, 8), 3, "euler", "nodal", "hll", 4),          # same group as the first problem
        ((8, 8, 8), 3, "mhd", "modal", "hll", 5),
-       ((6, 7, 9), 2, "mhd", "nodal", "hll", 6),
+       ((6, 7, 9), 2, "mhd", "nodal", "linearized", 6),
        ((9, 9, 9), 4, "mhd", "nodal", "hll", 7),
        ((4, 13, 11), 3, "euler", "modal", "linearized", 8)]
 
@@ -177,7 +177,5 @@ def test_batch_rejects_unsupported_problems(ader):
     g = [(8, 8, 8, 0.125, 0.125, 0.125)]
     with pytest.raises(_lib.AderError):                 # FP64 bulk is not batched
         _lib.ader_batch_create(g, [3], [1.4], [_lib.ADER_HLL], [0])
-    with pytest.raises(_lib.AderError):                 # MHD uses HLL
-        _lib.ader_batch_create(g, [3], [G_MHD], [_lib.ADER_LINEARIZED], [_lib.ADER_FP32_BULK | _lib.ADER_MHD])
     with pytest.raises(_lib.AderError):
         _lib.ader_batch_create(g, [5], [1.4], [_lib.ADER_HLL], [_lib.ADER_FP32_BULK])

@@ -25,8 +25,9 @@ def test_initial_fields_are_divergence_free():
         assert np.abs(scheme.div_b(B, (1.0 / n,) * 3)).max() < 1e-12
 
 
+@pytest.mark.parametrize("solver", ["hll", "linearized"])
 @pytest.mark.parametrize("order", [2, 3, 4])
-def test_constrained_transport_keeps_div_b_and_conserves(order):
+def test_constrained_transport_keeps_div_b_and_conserves(order, solver):
     """Eq. 8 changes every zone's discrete div B by round-off only; hydro totals and face-B totals are conserved."""
     rng = np.random.default_rng(order)
     n = 8
@@ -36,7 +37,7 @@ def test_constrained_transport_keeps_div_b_and_conserves(order):
     U[4] += 0.5
     d0 = scheme.div_b(B, dx)
     dt = 0.5 * scheme.max_dt(U, dx, 0.4, G, Bface=B)
-    U1, B1 = scheme.ader_step(U, dx, dt, order, "nodal", "hll", G, Bface=B)
+    U1, B1 = scheme.ader_step(U, dx, dt, order, "nodal", solver, G, Bface=B)
     scale = np.abs(B).max() / dx[0]
     assert np.abs(scheme.div_b(B1, dx) - d0).max() <= 1e-13 * scale
     assert np.abs(B1 - B).max() > 1e-6
@@ -44,26 +45,27 @@ def test_constrained_transport_keeps_div_b_and_conserves(order):
     np.testing.assert_allclose(U1.reshape(5, -1).sum(axis=1), U.reshape(5, -1).sum(axis=1), atol=1e-12 * np.abs(U).sum())
 
 
-def test_uniform_magnetised_flow_is_unchanged():
+@pytest.mark.parametrize("solver", ["hll", "linearized"])
+def test_uniform_magnetised_flow_is_unchanged(solver):
     n = 6
     dx = (1.0 / n,) * 3
     B = np.stack([np.full((n, n, n), b) for b in (0.7, -0.4, 1.1)])
     rho = np.ones((n, n, n))
     v = [0.3 * rho, -0.2 * rho, 0.1 * rho]
     U = physics.prim_to_cons(rho, *v, rho, G, B=(B[0], B[1], B[2]))[:5]
-    U1, B1 = scheme.ader_step(U, dx, 0.01, 3, "modal", "hll", G, Bface=B)
+    U1, B1 = scheme.ader_step(U, dx, 0.01, 3, "modal", solver, G, Bface=B)
     np.testing.assert_allclose(U1, U, atol=1e-13)
     np.testing.assert_allclose(B1, B, atol=1e-13)
 
 
-@pytest.mark.parametrize("order", [2, 3])
-def test_alfven_wave_convergence(order):
+@pytest.mark.parametrize("order,solver", [(2, "hll"), (3, "hll"), (3, "linearized")])
+def test_alfven_wave_convergence(order, solver):
     """Config 3: the circularly polarised Alfven wave translates exactly; L1 order within 0.2 of M."""
     errs = []
     for n in (8, 16):
         U, B = inputs.alfven_wave(n)
         dx = (1.0 / n,) * 3
-        U, B = _run(U, B, dx, 0.05, order)
+        U, B = _run(U, B, dx, 0.05, order, solver=solver)
         Ue, Be = inputs.alfven_wave(n, t=0.05)
         errs.append(np.abs(B - Be).mean() + np.abs(U[1:4] - Ue[1:4]).mean())
     assert np.log2(errs[0] / errs[1]) >= order - 0.2

@@ -101,6 +101,27 @@ def test_absolute_jacobian(mhd):
                                np.sort(np.abs(np.linalg.eigvals(A).real)), atol=1e-8)
 
 
+@pytest.mark.parametrize("case", ["no_normal_field", "no_transverse_field", "triple_umbilic"])
+def test_absolute_jacobian_degenerate_mhd_states(case):
+    """Where MHD wave speeds coincide (B_n = 0: slow = Alfven = entropy; B_t = 0: Alfven = fast or slow;
+    B_t = 0 and c_A = a: all three at one speed) |A| still satisfies |A|^2 = A^2, commutes with A and has
+    the eigenvalues |lambda|."""
+    g = 5.0 / 3.0
+    rho, P = 1.3, 0.9
+    B = {"no_normal_field": (0.0, 0.8, -0.5), "no_transverse_field": (1.7, 0.0, 0.0),
+         "triple_umbilic": (np.sqrt(4 * np.pi * g * P), 0.0, 0.0)}[case]
+    U = physics.prim_to_cons(np.array([rho]), np.array([0.4]), np.array([-0.3]), np.array([0.2]),
+                             np.array([P]), g, tuple(np.array([b]) for b in B))
+    absA, keep = riemann.abs_jacobian(U, g, 0)
+    A = physics.jacobian(U[:, 0], g, 0)[np.ix_(keep, keep)]
+    assert np.isfinite(absA).all()
+    scale = np.abs(A @ A).max()
+    np.testing.assert_allclose(absA[0] @ absA[0], A @ A, atol=1e-10 * scale)
+    np.testing.assert_allclose(absA[0] @ A, A @ absA[0], atol=1e-10 * scale)
+    np.testing.assert_allclose(np.sort(np.linalg.eigvals(absA[0]).real),
+                               np.sort(np.abs(np.linalg.eigvals(A).real)), atol=1e-6)
+
+
 def test_hll_upwinds_supersonic_flow():
     """Supersonic flow to the right: HLL returns the left averaged flux (lambda_L = 0 after the reset)."""
     U = physics.prim_to_cons(np.array([1.0]), np.array([5.0]), np.array([0.0]), np.array([0.0]), np.array([1.0]), 1.4)
