@@ -206,13 +206,13 @@ def mhd_variants(ader, torch, stream, n=128, steps=3, warmup=1):
     return out
 
 
-def batched_variant(ader, torch, stream, steps=3, warmup=1):
-    """64 seeded independent problems of uneven sizes 32^3-128^3 (Euler and MHD, orders 2-4, FP32 bulk):
+def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32, 48, 64, 80, 96, 112, 128)):
+    """`count` seeded independent problems of uneven cubic sizes (Euler and MHD, orders 2-4, FP32 bulk):
     one tuned batch replayed from a captured graph vs one context per problem launched in sequence.
     Each step includes every problem's CFL dt."""
     from paper_1006_2146_gb300 import _lib, inputs
     t0 = time.perf_counter()
-    probs = inputs.batch_problems(64, seed=1006)
+    probs = inputs.batch_problems(count, seed=1006, sizes=sizes)
     gen_s = time.perf_counter() - t0
     zones = sum(p["U"][0].size for p in probs)
     Us = [torch.from_numpy(p["U"]).to("cuda") for p in probs]
@@ -302,6 +302,56 @@ def batched_variant(ader, torch, stream, steps=3, warmup=1):
     return out
 
 
+def blast_evaluation(ader, torch, P, stream, n=256, steps=3):
+    """The learned guess on the 256^3 hydrodynamic blast (Sec. VIII.3 set-up: rho = 1, P 1000 inside r < 0.1,
+    0.1 outside): FP32 converged predictor (tol 1e-6) from zero and from the guess, timed, with the mean
+    iteration count and the error after `steps` steps of one fixed dt against the FP64 converged predictor."""
+    from paper_1006_2146_gb300 import inputs
+    out = {}
+    try:
+        U0 = torch.from_numpy(inputs.blast(n, sub=2)).to("cuda")
+        s = ader.Solver((n, n, n), order=3, form="nodal")
+        dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+        s.max_dt(U0, 0.4, dtv)
+        s.close()
+        dt = float(dtv.item())
+
+        def run(fp32, tol, guess, timed):
+            s = ader.Solver((n, n, n), order=3, form="nodal", fp32=fp32)
+            s.set_predictor(tol, 50)
+            if guess is not None:
+                s.set_guess(guess)
+            d = U0.clone()
+            s.step(d, dt, stream)                       # warm-up step, discarded counts
+            torch.cuda.synchronize()
+            s.predictor_stats(stream)
+            d = U0.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(steps):
+                    s.step(d, dt, stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            tot, mx, capped = s.predictor_stats(stream)
+            st = s.status(stream)
+            s.close()
+            rec = {"ms_per_step": e0.elapsed_time(e1) / steps, "zone_updates_per_s": n ** 3 * steps /
+                   (e0.elapsed_time(e1) / 1e3), "mean_predictor_iterations": tot / (steps * n ** 3),
+                   "max_predictor_iterations": mx, "capped": capped, "status": st}
+            return d, rec
+
+        ref, rec = run(False, 1e-13, None, True)
+        out["fp64_converged"] = rec
+        for name, guess in (("fp32_converged", None), ("fp32_converged_learned_guess", P)):
+            d, rec = run(True, 1e-6, guess, True)
+            rec["rel_l1_vs_fp64_converged_%dsteps" % steps] = rel_l1_dev(d, ref)
+            out[name] = rec
+    except Exception as exc:
+        out["error"] = str(exc)[:200]
+    return out
+
+
 def learned_variants(ader, torch, n, U0, stream, steps=3):
     """Converged predictor from zero and from the learned guess (third order, nodal, HLL).
 
@@ -356,6 +406,7 @@ def learned_variants(ader, torch, n, U0, stream, steps=3):
     except Exception as exc:
         ref = None
         out["fp64_converged_reference"] = {"error": str(exc)[:200]}
+    out["learned_guess_on_blast_256"] = blast_evaluation(ader, torch, P, stream)
     for name, fp32, tol, guess in cases:
         try:
             vsecs, vprof, vs_, _, _ = run_config(ader, torch, n, 3, "nodal", "hll", fp32, 3, 1, stream, profile=True,
@@ -536,6 +587,8 @@ def gpu_arm(args):
         variants.update(learned_variants(ader, torch, n, U0, stream))
         variants.update(mhd_variants(ader, torch, stream))
         variants["batched_64_problems_fp32"] = batched_variant(ader, torch, stream)
+        variants["batched_512_small_problems_fp32"] = batched_variant(ader, torch, stream, count=512,
+                                                                      sizes=(16, 24, 32))
         # SSP-RK of the same order and solver on the same GPU (Eq. 19), per step
         srk = ader.Solver((n, n, n), order=3, form="nodal", solver="hll")
         drk = U0.clone()
