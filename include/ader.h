@@ -98,7 +98,8 @@ int ader_step_devdt(ader_ctx* ctx, double* U, double* Bface, const double* dt_de
  *   dt = cfl / max over zones of sum_d (|v_d| + c_d) / dx_d,
  * c_d the sound speed (MHD: the fast speed with the zone field taken as the
  * mean of its two face values; Bface as for ader_step).  Written to dt_dev (one double, device).  Reduction
- * in FP64 with warp shuffles. */
+ * in FP64 with warp shuffles; FP32-bulk contexts compute each zone's signal speed in FP32 (dt then agrees
+ * with the FP64 rule to about 1e-7 relative). */
 int ader_max_dt(ader_ctx* ctx, const double* U, const double* Bface, double cfl, double* dt_dev, void* stream);
 
 /* One SSP-RK step of the context's order (Eq. 18 for order 2, Eq. 19 for
@@ -220,7 +221,8 @@ void ader_destroy(ader_ctx* ctx);
  *     3 x zones for MHD problems, else ignored), dt_dev[p] (device, n doubles).
  *   ader_batch_advance: dt_dev[p] = cfl / max over zones of sum_d (|v_d| +
  *     c_d) / dx_d for each problem (written to dt_dev, device, n doubles; NULL
- *     uses an internal buffer), then the step with it; one graph.
+ *     uses an internal buffer; signal speeds in FP32, maximum in FP64), then
+ *     the step with it; one graph.
  *   ader_batch_status: synchronises the stream; codes_host[p] (n ints, may be
  *     NULL) gets each problem's code; returns the first non-OK code.
  *   ader_batch_tuning: writes (group, phase, threads, blocks) quadruples

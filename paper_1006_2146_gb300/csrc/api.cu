@@ -330,7 +330,7 @@ int ader_max_dt(ader_ctx* c, const double* U, const double* Bface, double cfl, d
     if (!(cfl > 0.0)) return fail(c, ADER_ERR_ARG, "cfl must be positive");
     const double dx[3] = {c->g.dx, c->g.dy, c->g.dz};
     Trace t(c, "max_dt", (cudaStream_t)stream);
-    launch_max_dt(c->grid, U, Bface, c->gamma, dx, cfl, dt_dev, c->dtscr, c->flag, (cudaStream_t)stream);
+    launch_max_dt(c->grid, U, Bface, c->gamma, dx, cfl, dt_dev, c->dtscr, c->flag, c->fp32, (cudaStream_t)stream);
     return cuda_check(c, cudaGetLastError(), "ader_max_dt launch");
 }
 

@@ -35,36 +35,38 @@ __global__ void __launch_bounds__(256) kb_max_dt(BatchGroupDev g, unsigned long 
         const Grid& gr = it.a.grid;
         const long long z = gz - g.zpad[p];
         double s = 0.0;
-        if (z < gr.n) {
+        if (z < gr.n) {      // signal speed in FP32 (every batched problem is FP32 bulk); maximum in FP64
+            using F = float;
             const long long N = gr.n;
             const double* U = it.U;
-            const double gamma = it.a.gamma;
-            const double rho = U[z], mx = U[N + z], my = U[2 * N + z], mz = U[3 * N + z], E = U[4 * N + z];
-            const double ir = 1.0 / rho;
-            const double vx = mx * ir, vy = my * ir, vz = mz * ir;
-            const double idx = 1.0 / it.a.dx[0], idy = 1.0 / it.a.dx[1], idz = 1.0 / it.a.dx[2];
+            const F gamma = F(it.a.gamma);
+            const F rho = F(U[z]), mx = F(U[N + z]), my = F(U[2 * N + z]), mz = F(U[3 * N + z]), E = F(U[4 * N + z]);
+            const F ir = F(1) / rho;
+            const F vx = mx * ir, vy = my * ir, vz = mz * ir;
+            const F idx = F(1.0 / it.a.dx[0]), idy = F(1.0 / it.a.dx[1]), idz = F(1.0 / it.a.dx[2]);
             bool bad;
             if (it.Bf) {
                 const int i = (int)(z % gr.nx);
                 const long long t = z / gr.nx;
                 const int j = (int)(t % gr.ny), k = (int)(t / gr.ny);
                 const double* Bf = it.Bf;
-                Vec<8, double> u;
+                Vec<8, F> u;
                 u[0] = rho; u[1] = mx; u[2] = my; u[3] = mz; u[4] = E;
-                u[5] = 0.5 * (Bf[z] + Bf[nbr(gr, i, j, k, 1, 0, 0)]);
-                u[6] = 0.5 * (Bf[N + z] + Bf[N + nbr(gr, i, j, k, 0, 1, 0)]);
-                u[7] = 0.5 * (Bf[2 * N + z] + Bf[2 * N + nbr(gr, i, j, k, 0, 0, 1)]);
-                const Prim<8, double> q = primitives(u, gamma - 1.0);
-                bad = !(rho > 0.0) || !(q.p > 0.0);
+                u[5] = F(0.5 * (Bf[z] + Bf[nbr(gr, i, j, k, 1, 0, 0)]));
+                u[6] = F(0.5 * (Bf[N + z] + Bf[N + nbr(gr, i, j, k, 0, 1, 0)]));
+                u[7] = F(0.5 * (Bf[2 * N + z] + Bf[2 * N + nbr(gr, i, j, k, 0, 0, 1)]));
+                const Prim<8, F> q = primitives(u, gamma - F(1));
+                bad = !(rho > F(0)) || !(q.p > F(0));
                 if (!bad)
-                    s = (fabs(vx) + fast_speed<0>(u, q, gamma)) * idx + (fabs(vy) + fast_speed<1>(u, q, gamma)) * idy +
-                        (fabs(vz) + fast_speed<2>(u, q, gamma)) * idz;
+                    s = (double)((fabsf(vx) + fast_speed<0>(u, q, gamma)) * idx +
+                                 (fabsf(vy) + fast_speed<1>(u, q, gamma)) * idy +
+                                 (fabsf(vz) + fast_speed<2>(u, q, gamma)) * idz);
             } else {
-                const double pr = (gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy + mz * vz));
-                bad = !(rho > 0.0) || !(pr > 0.0);
+                const F pr = (gamma - F(1)) * (E - F(0.5) * (mx * vx + my * vy + mz * vz));
+                bad = !(rho > F(0)) || !(pr > F(0));
                 if (!bad) {
-                    const double a = sqrt(gamma * pr * ir);
-                    s = (fabs(vx) + a) * idx + (fabs(vy) + a) * idy + (fabs(vz) + a) * idz;
+                    const F a = sqrtf(gamma * pr * ir);
+                    s = (double)((fabsf(vx) + a) * idx + (fabsf(vy) + a) * idy + (fabsf(vz) + a) * idz);
                 }
             }
             if (bad) raise_flag(it.a.flag, FLAG_UNPHYSICAL);

@@ -76,6 +76,25 @@ ADER_DEV Vec<NV, R> scale(R s, const Vec<NV, R>& a) {
 
 template <class R> ADER_DEV R rcp(R x) { return R(1) / x; }
 
+// FP64 reciprocal by Newton-Raphson: the hardware's approximate reciprocal
+// seeds r, and two steps of r <- r + r (1 - x r) take it to about one unit in
+// the last place (the seed's error squares at each step).  On GB300 the FP64
+// units are scarce; this costs one seed and four FMAs instead of a correctly
+// rounded division.  Zero, infinite and subnormal arguments do not occur where
+// it is used (densities, positive sums of weights and wave-speed spans).
+template <> ADER_DEV double rcp<double>(double x) {
+#ifdef __CUDA_ARCH__
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+#else
+    return 1.0 / x;
+#endif
+}
+
 // ------------------------------------------------------------------ physics, Eq. 3 (Gaussian units)
 // NV = 5: Euler (rho, rho v, eps).  NV = 8: ideal MHD (rho, rho v, eps, B) with
 // eps = rho v^2/2 + P/(gamma-1) + B^2/(8 pi).

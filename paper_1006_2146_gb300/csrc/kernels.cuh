@@ -59,8 +59,9 @@ template <class R> int launch_flux_update(const StepArgs& a, double* out, const 
 // out = sum_i c[i] X[i], i < n (n <= 6)
 int launch_lincomb(double* out, int n, const double* const* X, const double* c, long long count, cudaStream_t st);
 
+// fp32: per-zone signal speeds in FP32 (FP32-bulk contexts); the reduction and dt are FP64 either way
 int launch_max_dt(const Grid& g, const double* U, const double* Bf, double gamma, const double dx[3], double cfl,
-                  double* dt_dev, unsigned long long* scratch, unsigned* flag, cudaStream_t st);
+                  double* dt_dev, unsigned long long* scratch, unsigned* flag, bool fp32, cudaStream_t st);
 // MHD: edge EMFs from the face data in S3, then Eq. 8 on Bf (in place) with step c_host (x *dt_dev)
 template <class R> int launch_emf_ct(const StepArgs& a, double* Bf, double c_host, bool use_dt_dev, cudaStream_t st);
 int launch_guess_samples(const StepArgs& a, const double* U, float* X, float* Y, int* ok, cudaStream_t st);

@@ -12,43 +12,48 @@ namespace ader {
 // block to finish writes dt and resets both words for the next call.
 // For MHD (Bf non-null) c_d is the fast speed of the zone state whose field is the mean of the
 // two face values (Sec. III, opening).
+// S is the precision of the per-zone signal speed: FP64, or FP32 for FP32-bulk
+// contexts (there FP64's division and square root would dominate the kernel);
+// the maximum, its reduction and dt are FP64 in both.
+template <class S>
 __global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict__ U, const double* __restrict__ Bf,
                                                 double gamma, double idx, double idy, double idz, double cfl,
                                                 double* dt_out, unsigned long long* scratch, unsigned* flag) {
     double s = 0.0;
     bool bad = false;
     const long long N = g.n;
+    const S gm = S(gamma), ix = S(idx), iy = S(idy), iz = S(idz);
     for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < N; z += (long long)gridDim.x * blockDim.x) {
-        const double rho = U[z], mx = U[N + z], my = U[2 * N + z], mz = U[3 * N + z], E = U[4 * N + z];
-        const double ir = 1.0 / rho;
-        const double vx = mx * ir, vy = my * ir, vz = mz * ir;
-        double v;
+        const S rho = S(U[z]), mx = S(U[N + z]), my = S(U[2 * N + z]), mz = S(U[3 * N + z]), E = S(U[4 * N + z]);
+        const S ir = S(1) / rho;
+        const S vx = mx * ir, vy = my * ir, vz = mz * ir;
+        S v;
         if (Bf) {
             const int i = (int)(z % g.nx);
             const long long t = z / g.nx;
             const int j = (int)(t % g.ny), k = (int)(t / g.ny);
-            Vec<8, double> u;
+            Vec<8, S> u;
             u[0] = rho; u[1] = mx; u[2] = my; u[3] = mz; u[4] = E;
-            u[5] = 0.5 * (Bf[z] + Bf[nbr(g, i, j, k, 1, 0, 0)]);
-            u[6] = 0.5 * (Bf[N + z] + Bf[N + nbr(g, i, j, k, 0, 1, 0)]);
-            u[7] = 0.5 * (Bf[2 * N + z] + Bf[2 * N + nbr(g, i, j, k, 0, 0, 1)]);
-            const Prim<8, double> q = primitives(u, gamma - 1.0);
-            if (!(rho > 0.0) || !(q.p > 0.0)) {
+            u[5] = S(0.5 * (Bf[z] + Bf[nbr(g, i, j, k, 1, 0, 0)]));
+            u[6] = S(0.5 * (Bf[N + z] + Bf[N + nbr(g, i, j, k, 0, 1, 0)]));
+            u[7] = S(0.5 * (Bf[2 * N + z] + Bf[2 * N + nbr(g, i, j, k, 0, 0, 1)]));
+            const Prim<8, S> q = primitives(u, gm - S(1));
+            if (!(rho > S(0)) || !(q.p > S(0))) {
                 bad = true;
                 continue;
             }
-            v = (fabs(vx) + fast_speed<0>(u, q, gamma)) * idx + (fabs(vy) + fast_speed<1>(u, q, gamma)) * idy +
-                (fabs(vz) + fast_speed<2>(u, q, gamma)) * idz;
+            v = (fabs(vx) + fast_speed<0>(u, q, gm)) * ix + (fabs(vy) + fast_speed<1>(u, q, gm)) * iy +
+                (fabs(vz) + fast_speed<2>(u, q, gm)) * iz;
         } else {
-            const double p = (gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy + mz * vz));
-            if (!(rho > 0.0) || !(p > 0.0)) {
+            const S p = (gm - S(1)) * (E - S(0.5) * (mx * vx + my * vy + mz * vz));
+            if (!(rho > S(0)) || !(p > S(0))) {
                 bad = true;
                 continue;
             }
-            const double a = sqrt(gamma * p * ir);
-            v = (fabs(vx) + a) * idx + (fabs(vy) + a) * idy + (fabs(vz) + a) * idz;
+            const S a = sqrt(gm * p * ir);
+            v = (fabs(vx) + a) * ix + (fabs(vy) + a) * iy + (fabs(vz) + a) * iz;
         }
-        s = fmax(s, v);
+        s = fmax(s, (double)v);
     }
     if (bad) raise_flag(flag, FLAG_UNPHYSICAL);
 #pragma unroll
@@ -76,14 +81,19 @@ __global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict
 }
 
 int launch_max_dt(const Grid& g, const double* U, const double* Bf, double gamma, const double dx[3], double cfl,
-                  double* dt_dev, unsigned long long* scratch, unsigned* flag, cudaStream_t st) {
+                  double* dt_dev, unsigned long long* scratch, unsigned* flag, bool fp32, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long want = (g.n + 255) / 256;
     const long long cap = (long long)sms * 8;
     const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
-    k_max_dt<<<blocks, 256, 0, st>>>(g, U, Bf, gamma, 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2], cfl, dt_dev, scratch, flag);
+    if (fp32)
+        k_max_dt<float><<<blocks, 256, 0, st>>>(g, U, Bf, gamma, 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2], cfl, dt_dev,
+                                                scratch, flag);
+    else
+        k_max_dt<double><<<blocks, 256, 0, st>>>(g, U, Bf, gamma, 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2], cfl, dt_dev,
+                                                 scratch, flag);
     return 1;
 }
 

@@ -173,7 +173,7 @@ ADER_DEV void flux_difference(const StepArgs& a, long long z, int i, int j, int 
     const long long zm = nbr(a.grid, i, j, k, -(D == 0), -(D == 1), -(D == 2));
     const Vec<NV, R> Fp = riemann<SOLVER, D>(load_side<NV, R>(a, 2 * D, z), load_side<NV, R>(a, 2 * D + 1, zp), gamma, gm1);
     const Vec<NV, R> Fm = riemann<SOLVER, D>(load_side<NV, R>(a, 2 * D, zm), load_side<NV, R>(a, 2 * D + 1, z), gamma, gm1);
-    const double inv = 1.0 / a.dx[D];
+    const double inv = rcp(a.dx[D]);
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] -= ((double)Fp[v] - (double)Fm[v]) * inv;
 }

@@ -38,7 +38,7 @@ ADER_DEV R weno_weights(const R* g, const R* is, R* a) {
             a[s] = g[s] * (pre[s] * suf[s]);
             d += a[s];
         }
-        return R(1) / d;
+        return rcp(d);
     } else {
         R d = R(0);
 #pragma unroll

@@ -96,7 +96,7 @@ def test_batch_matches_single_contexts_and_oracle(ader):
         nz, ny, nx = p["shape"]
         dx = (1.0 / nx, 1.0 / ny, 1.0 / nz)
         want_dt = scheme.max_dt(p["U"], dx, 0.4, p["gamma"], Bface=p["B"])
-        assert dts[k] == pytest.approx(want_dt, rel=1e-14), k
+        assert dts[k] == pytest.approx(want_dt, rel=1e-6), k      # FP32 signal speeds, FP64 reduction
         # the same step through a single context
         Us1 = to_dev(p["U"])
         Bs1 = to_dev(p["B"]) if p["mhd"] else None

@@ -218,7 +218,8 @@ def test_full_size_sampled_parity(ader, fp32):
     s.step_devdt(d, dt)
     got = to_host(d)
     dtv = float(dt.item())
-    assert dtv == pytest.approx(scheme.max_dt(U, (1.0 / n,) * 3, 0.4), rel=1e-14)
+    # FP32-bulk contexts compute the per-zone signal speeds in FP32 (reduction in FP64)
+    assert dtv == pytest.approx(scheme.max_dt(U, (1.0 / n,) * 3, 0.4), rel=1e-6 if fp32 else 1e-14)
     rng = np.random.default_rng(42)
     samples = [(0, 0, 0), (255, 255, 255), (128, 64, 63)] + [tuple(rng.integers(0, n, 3)) for _ in range(9)]
     # include zones on the shock planes x + y = 1/2 and 1
