@@ -1,12 +1,15 @@
 // Learned predictor guess on the 5th-generation tensor cores (tcgen05).
 //
-// One CTA of 128 threads handles tiles of 128 zones (persistent over the
-// grid).  Each thread computes its zone's features (mlp.cuh) and writes them
-// as FP16 into the A operand in shared memory; one thread issues the three
-// layers as tcgen05.mma (kind::f16, M = 128, FP32 accumulator in 128 TMEM
-// columns); after each layer every warp reads its 32 accumulator lanes back
-// with tcgen05.ld, adds the bias, applies GELU (tanh form, hardware tanh) and
-// writes the next A operand.  The weights are converted to FP16 once per CTA.
+// One CTA per SM runs GROUPS independent pipelines of 128 threads, each over
+// tiles of 128 zones (persistent over the grid); the FP16 weights in shared
+// memory serve all of them.  In a pipeline each thread computes its zone's
+// features (mlp.cuh) and writes them as FP16 into the group's A operand; one
+// thread issues the three layers as tcgen05.mma (kind::f16, M = 128, FP32
+// accumulator in the group's 128 TMEM columns); after each layer every warp
+// reads its 32 accumulator lanes back with tcgen05.ld, adds the bias, applies
+// GELU (tanh form, hardware tanh) and writes the next A operand.  The groups
+// synchronise on their own named barriers, so while one waits on memory or on
+// its MMAs the others compute.
 //
 // Operand layout: K-major, no swizzle.  A tile of R rows and K columns is
 // stored as 8 x 8 "core matrices" (8 rows of 16 bytes, 128 contiguous bytes);
@@ -26,8 +29,9 @@
 namespace ader {
 namespace {
 
-constexpr int TM = 128;                  // zones per tile = MMA M = TMEM lanes
-constexpr unsigned TMEM_COLS = 128;      // accumulator columns: the widest layer
+constexpr int TM = 128;                  // zones per tile = MMA M = TMEM lanes = threads per group
+constexpr int GROUPS = 4;                // pipelines per CTA (512 threads)
+constexpr unsigned TMEM_COLS = 128;      // accumulator columns per group: the widest layer
 constexpr long long WAIT_LIMIT = 1ll << 22;
 
 __host__ __device__ constexpr int k1pad(int nv) { return (mlp_in(nv) + 15) / 16 * 16; }
@@ -39,9 +43,9 @@ struct TcSmem {
     __half W1[H * K1];      // B of layer 1: H rows (outputs) x K1
     __half W2[H * H];       // B of layer 2
     __half W3[N3 * H];      // B of layer 3: N3 rows x H
-    __half A[TM * H];       // A: features (TM x K1), then the hidden layers (TM x H)
+    __half A[GROUPS][TM * H];   // per group A: features (TM x K1), then the hidden layers (TM x H)
     float b1[H], b2[H], b3[N3];
-    unsigned long long mbar;
+    unsigned long long mbar[GROUPS];
     unsigned tmem_base;
 };
 
@@ -126,8 +130,7 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, const __half* A, cons
 }
 
 // accumulator + bias -> GELU -> FP16 into the A operand (K = H) at this thread's row
-template <int NV>
-__device__ __forceinline__ void hidden_epilogue(TcSmem<NV>& s, const float* bias, uint32_t tlane, int row) {
+__device__ __forceinline__ void hidden_epilogue(__half* A, const float* bias, uint32_t tlane, int row) {
     constexpr int H = MLP_HIDDEN;
 #pragma unroll 1
     for (int c = 0; c < H; c += 16) {
@@ -136,47 +139,64 @@ __device__ __forceinline__ void hidden_epilogue(TcSmem<NV>& s, const float* bias
         __align__(16) __half h[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) h[j] = __float2half_rn(gelu_tc(v[j] + bias[c + j]));
-        *reinterpret_cast<uint4*>(&s.A[koff(row, c, H)]) = *reinterpret_cast<const uint4*>(&h[0]);
-        *reinterpret_cast<uint4*>(&s.A[koff(row, c + 8, H)]) = *reinterpret_cast<const uint4*>(&h[8]);
+        *reinterpret_cast<uint4*>(&A[koff(row, c, H)]) = *reinterpret_cast<const uint4*>(&h[0]);
+        *reinterpret_cast<uint4*>(&A[koff(row, c + 8, H)]) = *reinterpret_cast<const uint4*>(&h[8]);
     }
 }
 
+// named barrier of one group (ids 1..GROUPS; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(TM) : "memory"); }
+
+// the same barrier, returning whether any thread of the group passed true
+__device__ __forceinline__ bool group_sync_or(int id, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"(v ? 1u : 0u), "r"(id), "r"(TM)
+        : "memory");
+    return r != 0;
+}
+
 template <int NV, class R>
-__global__ void __launch_bounds__(TM, 1) k_guess_tc(StepArgs a, const double* __restrict__ U) {
+__global__ void __launch_bounds__(TM * GROUPS, 1) k_guess_tc(StepArgs a, const double* __restrict__ U) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);   // 1 KB aligned
     TcSmem<NV>& s = *reinterpret_cast<TcSmem<NV>*>(base);
     constexpr int IN = mlp_in(NV), OUT = mlp_out(NV), H = MLP_HIDDEN, K1 = k1pad(NV), N3 = n3pad(NV);
+    constexpr int NT = TM * GROUPS;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = tid / TM, row = tid % TM;          // pipeline and its tile row
 
-    // weights -> FP16 operand layout, biases -> FP32
+    // weights -> FP16 operand layout, biases -> FP32 (all pipelines share them)
     const float* W1 = a.guess;
     const float* b1 = W1 + H * IN;
     const float* W2 = b1 + H;
     const float* b2 = W2 + H * H;
     const float* W3 = b2 + H;
     const float* b3 = W3 + OUT * H;
-    for (int e = tid; e < H * K1; e += TM) {
+    for (int e = tid; e < H * K1; e += NT) {
         const int r = e / K1, k = e % K1;
         s.W1[koff(r, k, K1)] = __float2half_rn(k < IN ? W1[r * IN + k] : 0.f);
     }
-    for (int e = tid; e < H * H; e += TM) s.W2[koff(e / H, e % H, H)] = __float2half_rn(W2[e]);
-    for (int e = tid; e < N3 * H; e += TM) {
+    for (int e = tid; e < H * H; e += NT) s.W2[koff(e / H, e % H, H)] = __float2half_rn(W2[e]);
+    for (int e = tid; e < N3 * H; e += NT) {
         const int r = e / H, k = e % H;
         s.W3[koff(r, k, H)] = __float2half_rn(r < OUT ? W3[r * H + k] : 0.f);
     }
-    for (int e = tid; e < H; e += TM) {
+    for (int e = tid; e < H; e += NT) {
         s.b1[e] = b1[e];
         s.b2[e] = b2[e];
     }
-    for (int e = tid; e < N3; e += TM) s.b3[e] = e < OUT ? b3[e] : 0.f;
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&s.mbar)) : "memory");
+    for (int e = tid; e < N3; e += NT) s.b3[e] = e < OUT ? b3[e] : 0.f;
+    if (tid < GROUPS) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&s.mbar[tid])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s.tmem_base)),
-                     "r"(TMEM_COLS)
+                     "r"(TMEM_COLS * GROUPS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -184,8 +204,11 @@ __global__ void __launch_bounds__(TM, 1) k_guess_tc(StepArgs a, const double* __
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tbase = s.tmem_base;
-    const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tbase = s.tmem_base + (uint32_t)(g * TMEM_COLS);            // the group's columns
+    const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16);        // this warp's 32 lanes
+    __half* A = s.A[g];
+    unsigned long long* bar = &s.mbar[g];
+    const int bid = 1 + g;
 
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
     const float cx = (float)(dt / a.dx[0]), cy = (float)(dt / a.dx[1]), cz = (float)(dt / a.dx[2]);
@@ -193,14 +216,20 @@ __global__ void __launch_bounds__(TM, 1) k_guess_tc(StepArgs a, const double* __
     const long long ntiles = (N + TM - 1) / TM;
     uint32_t parity = 0;
     bool timed_out = false;
-    auto sync_mma = [&]() -> bool {          // all threads wait for the committed layer
-        const bool ok = mbar_wait(&s.mbar, parity);
+    auto sync_mma = [&]() -> bool {          // the group waits for its committed layer
+        const bool ok = mbar_wait(bar, parity);
         parity ^= 1u;
         fence_after();
-        return __syncthreads_or(ok ? 0 : 1) == 0;
+        return !group_sync_or(bid, !ok);
     };
-    for (long long t = blockIdx.x; t < ntiles && !timed_out; t += gridDim.x) {
-        const long long z = t * TM + tid;
+    auto handoff = [&]() {                   // A written by the group -> visible to its MMAs
+        fence_async_smem();
+        fence_before();
+        group_sync(bid);
+        fence_after();
+    };
+    for (long long t = (long long)blockIdx.x * GROUPS + g; t < ntiles; t += (long long)gridDim.x * GROUPS) {
+        const long long z = t * TM + row;
         float sv[NV] = {};
         bool act = false;
         {
@@ -222,39 +251,30 @@ __global__ void __launch_bounds__(TM, 1) k_guess_tc(StepArgs a, const double* __
                 __align__(16) __half h[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) h[j] = __float2half_rn(x[kc + j]);
-                *reinterpret_cast<uint4*>(&s.A[koff(tid, kc, K1)]) = *reinterpret_cast<const uint4*>(h);
+                *reinterpret_cast<uint4*>(&A[koff(row, kc, K1)]) = *reinterpret_cast<const uint4*>(h);
             }
         }
         // layer 1
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (tid == 0) {
-            issue_layer(tbase, s.A, s.W1, K1, H);
-            mma_commit(&s.mbar);
+        handoff();
+        if (row == 0) {
+            issue_layer(tbase, A, s.W1, K1, H);
+            mma_commit(bar);
         }
         if (!sync_mma()) { timed_out = true; break; }
-        hidden_epilogue<NV>(s, s.b1, tlane, tid);
+        hidden_epilogue(A, s.b1, tlane, row);
         // layer 2
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (tid == 0) {
-            issue_layer(tbase, s.A, s.W2, H, H);
-            mma_commit(&s.mbar);
+        handoff();
+        if (row == 0) {
+            issue_layer(tbase, A, s.W2, H, H);
+            mma_commit(bar);
         }
         if (!sync_mma()) { timed_out = true; break; }
-        hidden_epilogue<NV>(s, s.b2, tlane, tid);
+        hidden_epilogue(A, s.b2, tlane, row);
         // layer 3
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (tid == 0) {
-            issue_layer(tbase, s.A, s.W3, H, N3);
-            mma_commit(&s.mbar);
+        handoff();
+        if (row == 0) {
+            issue_layer(tbase, A, s.W3, H, N3);
+            mma_commit(bar);
         }
         if (!sync_mma()) { timed_out = true; break; }
 #pragma unroll
@@ -270,18 +290,20 @@ __global__ void __launch_bounds__(TM, 1) k_guess_tc(StepArgs a, const double* __
             }
         }
         fence_before();
-        __syncthreads();         // the next tile's layer 1 overwrites A and the accumulator
+        group_sync(bid);         // the next tile's layer 1 overwrites A and the accumulator
         fence_after();
     }
     if (timed_out) {
-        if (tid == 0) raise_flag(a.flag, FLAG_TIMEOUT);
-        mbar_wait(&s.mbar, parity ^ 1u);     // bounded: let the MMAs in flight finish before TMEM is freed
+        if (row == 0) raise_flag(a.flag, FLAG_TIMEOUT);
+        mbar_wait(bar, parity ^ 1u);         // bounded: let the group's MMAs in flight finish before TMEM is freed
     }
     fence_before();
     __syncthreads();
     fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem_base),
+                     "r"(TMEM_COLS * GROUPS)
+                     : "memory");
 }
 
 template <int NV, class R>
@@ -300,16 +322,18 @@ int launch_nv(const StepArgs& a, const double* U, cudaStream_t st) {
         if (cudaFuncSetAttribute(k_guess_tc<NV, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
             cudaSuccess)
             return -1;
-        int dev = 0, sms = 0, occ = 0;
+        int dev = 0, sms = 0, smem_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_guess_tc<NV, R>, TM, smem) != cudaSuccess || occ < 1)
-            return -1;
-        max_blocks = sms * occ;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        // one CTA per SM: its GROUPS pipelines hold all 512 TMEM columns
+        (void)smem_sm;
+        max_blocks = sms;
     }
     const long long tiles = (a.grid.n + TM - 1) / TM;
-    const unsigned blocks = (unsigned)(tiles < max_blocks ? tiles : max_blocks);
-    k_guess_tc<NV, R><<<blocks, TM, smem, st>>>(a, U);
+    const long long want = (tiles + GROUPS - 1) / GROUPS;
+    const unsigned blocks = (unsigned)(want < max_blocks ? want : max_blocks);
+    k_guess_tc<NV, R><<<blocks, TM * GROUPS, smem, st>>>(a, U);
     return 1;
 }
 
