@@ -335,8 +335,8 @@ int ader_batch_create(int n, const ader_grid* grids, const int* orders, const do
         off[p] = bytes;
         const int m = b->mhd[p];
         const size_t per = (size_t)(s1_per_zone(orders[p], m) + std::max(1, s2_per_zone(orders[p], m)) +
-                                    s3_per_zone(m, solvers[p] == ADER_LINEARIZED)) + (m ? 6 : 0);
-        bytes += align(per * (size_t)N * sizeof(float) + 5 * 256);
+                                    s3_per_zone(m, solvers[p] == ADER_LINEARIZED)) + (m ? 6 : 0) + 5;
+        bytes += align(per * (size_t)N * sizeof(float) + 8 * 256);      // six arrays, each 256-B aligned
     }
     bool ok = cudaMalloc(&b->arena, bytes) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&b->flags, n * sizeof(unsigned)) == cudaSuccess;
@@ -370,6 +370,7 @@ int ader_batch_create(int n, const ader_grid* grids, const int* orders, const do
         a.dx[0] = grids[p].dx;
         a.dx[1] = grids[p].dy;
         a.dx[2] = grids[p].dz;
+        finish_args(a);
         a.mhd = m;
         a.flag = b->flags + p;
         char* base = (char*)b->arena + off[p];
@@ -383,6 +384,7 @@ int ader_batch_create(int n, const ader_grid* grids, const int* orders, const do
         a.S3 = take((size_t)s3_per_zone(m, solvers[p] == ADER_LINEARIZED) * N);
         a.ZB = m ? take((size_t)3 * N) : nullptr;
         a.E = m ? take((size_t)3 * N) : nullptr;
+        a.Uf = (const float*)take((size_t)5 * N);
         b->items.push_back(it);
     }
     // variant groups

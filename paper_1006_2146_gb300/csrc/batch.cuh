@@ -61,10 +61,20 @@ __global__ void __launch_bounds__(256) kb_face_b(BatchGroupDev g) {
     });
 }
 
+// the FP32 copy of each problem's state (five values per zone)
+static __global__ void __launch_bounds__(256) kb_to_f32(BatchGroupDev g) {
+    batch_for(g, [](const BatchItem& it, long long z) {
+        float* Uf = const_cast<float*>(it.a.Uf);
+        const long long N = it.a.grid.n;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Uf[v * N + z] = (float)it.U[v * N + z];
+    });
+}
+
 template <int ORDER, int NV, class R>
 __global__ void __launch_bounds__(256) kb_weno1d(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) {
-        zone_weno1d<ORDER, NV, R>(it.a.grid, it.U, (const R*)it.a.ZB, (R*)it.a.S1, z);
+        zone_weno1d<ORDER, NV, R>(it.a.grid, it.a.Uf, (const R*)it.a.ZB, (R*)it.a.S1, z);
     });
 }
 
@@ -104,7 +114,8 @@ __global__ void __launch_bounds__(256) kb_ct(BatchGroupDev g) {
 }
 
 // Phases of one step, in order; a group runs those that apply to it.
-enum BatchPhase { PH_FACE_B = 0, PH_WENO1D, PH_CROSS1, PH_CROSS2, PH_PREDICT, PH_UPDATE, PH_EMF, PH_CT, PH_COUNT };
+enum BatchPhase { PH_TO_F32 = 0, PH_FACE_B, PH_WENO1D, PH_CROSS1, PH_CROSS2, PH_PREDICT, PH_UPDATE, PH_EMF, PH_CT,
+                  PH_COUNT };
 
 inline bool batch_phase_applies(int ph, int order, int mhd) {
     switch (ph) {

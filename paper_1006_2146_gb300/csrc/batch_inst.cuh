@@ -12,6 +12,7 @@ int batch_phase(int ph, const BatchGroupDev& g, int form, int solver, int thread
     using R = float;
     const void* k = nullptr;
     switch (ph) {
+        case PH_TO_F32: k = (const void*)kb_to_f32; break;
         case PH_FACE_B:
             if constexpr (NV == 8) k = (const void*)kb_face_b<ORDER, R>;
             break;

@@ -8,7 +8,9 @@
 // the flux differences in the update kernel (3 per variable per direction)
 // is added explicitly.
 //
-// Build and run:  nvcc -O1 -std=c++17 --expt-relaxed-constexpr flopcount.cu -o flopcount && ./flopcount
+// Build and run (host tool; the device side of the headers needs sm_103a):
+//   nvcc -O0 -Xcompiler -O0 -std=c++17 --expt-relaxed-constexpr -gencode arch=compute_103a,code=sm_103a \
+//        flopcount.cu -o flopcount && ./flopcount
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -66,6 +68,7 @@ int main() {
         a.n_iter = order - 1;
         a.gamma = 1.4;
         a.dx[0] = a.dx[1] = a.dx[2] = 1.0 / n;
+        finish_args(a);
         a.dt = 0.01;
         a.S1 = S1.data();
         a.S2 = S2.data();

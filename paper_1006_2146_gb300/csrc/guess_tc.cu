@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(TM * GROUPS, 1) k_guess_tc(StepArgs a, const d
     const int bid = 1 + g;
 
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
-    const float cx = (float)(dt / a.dx[0]), cy = (float)(dt / a.dx[1]), cz = (float)(dt / a.dx[2]);
+    const float cx = (float)(dt * a.idx[0]), cy = (float)(dt * a.idx[1]), cz = (float)(dt * a.idx[2]);
     const long long N = a.grid.n;
     const long long ntiles = (N + TM - 1) / TM;
     uint32_t parity = 0;

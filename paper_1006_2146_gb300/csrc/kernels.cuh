@@ -25,6 +25,9 @@ struct StepArgs {
                         // guess kernel and read by the predictor; null = start from zero
     double gamma;
     double dx[3];
+    double idx[3];      // 1 / dx, computed once on the host
+    double gm1;         // gamma - 1
+    float gamma_f, gm1_f, idx_f[3];   // FP32 copies for the FP32-bulk kernels (no FP64 work per zone)
     double dt;          // used when dt_dev is null
     const double* dt_dev;
     void* S1;           // 1-D WENO moments          (R)
@@ -35,7 +38,29 @@ struct StepArgs {
     const double* Bface; // MHD: face field B_d on faces i_d - 1/2 (3 x N), read
     void* ZB;           // MHD: zone-averaged B from the face-B WENO (3 x N, R)
     void* E;            // MHD: edge EMFs Ex, Ey, Ez (3 x N, R)
+    const float* Uf;    // FP32 bulk: the state rounded to FP32 once per step (5 x N), read by the WENO
 };
+
+// gamma, gamma - 1 and 1 / dx_d in the bulk precision R
+template <class R> ADER_DEV R arg_gamma(const StepArgs& a) {
+    if constexpr (sizeof(R) == 4) return a.gamma_f; else return R(a.gamma);
+}
+template <class R> ADER_DEV R arg_gm1(const StepArgs& a) {
+    if constexpr (sizeof(R) == 4) return a.gm1_f; else return R(a.gm1);
+}
+template <class R> ADER_DEV R arg_idx(const StepArgs& a, int d) {
+    if constexpr (sizeof(R) == 4) return a.idx_f[d]; else return R(a.idx[d]);
+}
+// fills the derived fields from gamma and dx
+inline void finish_args(StepArgs& a) {
+    a.gm1 = a.gamma - 1.0;
+    a.gamma_f = (float)a.gamma;
+    a.gm1_f = (float)a.gm1;
+    for (int d = 0; d < 3; ++d) {
+        a.idx[d] = 1.0 / a.dx[d];
+        a.idx_f[d] = (float)a.idx[d];
+    }
+}
 
 // Number of R values per zone in each scratch array.
 inline int nvar(int mhd) { return mhd ? 8 : 5; }
@@ -51,6 +76,8 @@ inline int s3_per_zone(int mhd, int linearized = 0) {
 }
 
 template <class R> int launch_recon(const StepArgs& a, const double* U, cudaStream_t st);
+// out[i] = (float)U[i], i < count (the FP32 copy of the state the FP32 WENO reads)
+int launch_to_f32(float* out, const double* U, long long count, cudaStream_t st);
 template <int ORDER, int NV, class R> int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st);
 // out = base + c * L(U) with L = -sum_d (F(i+1/2) - F(i-1/2)) / dx_d from the face data in S3;
 // c = c_host, multiplied by *a.dt_dev when use_dt_dev; base may equal out (in place) or be null (out = c L).

@@ -34,11 +34,36 @@ __global__ void __launch_bounds__(128) k_face_b(Grid g, const double* __restrict
     if (z < g.n) zone_face_b<ORDER, R>(g, Bf, ZB, S1, z);
 }
 
-template <int ORDER, int NV, class R>
-__global__ void __launch_bounds__(128) k_weno1d(Grid g, const double* __restrict__ U, const R* __restrict__ ZB,
+template <int ORDER, int NV, class R, class T>
+__global__ void __launch_bounds__(128) k_weno1d(Grid g, const T* __restrict__ U, const R* __restrict__ ZB,
                                                 R* __restrict__ S1) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z < g.n) zone_weno1d<ORDER, NV>(g, U, ZB, S1, z);
+}
+
+// FP32 copy of the state: every value is rounded once per step here instead of
+// at each of the 13 stencil points that read it (on GB300 the conversion runs
+// on the scarce FP64 units).  Pairs of values per thread; an odd last value is
+// taken by the first thread.
+__global__ void __launch_bounds__(256) k_to_f32(float* __restrict__ out, const double* __restrict__ U, long long count) {
+    const long long n2 = count / 2;
+    const double2* in = reinterpret_cast<const double2*>(U);
+    float2* o = reinterpret_cast<float2*>(out);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = in[i];
+        o[i] = make_float2((float)v.x, (float)v.y);
+    }
+    if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[count - 1] = (float)U[count - 1];
+}
+
+int launch_to_f32(float* out, const double* U, long long count, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (count / 2 + 255) / 256;
+    const unsigned blocks = (unsigned)(want < (long long)sms * 16 ? (want > 0 ? want : 1) : (long long)sms * 16);
+    k_to_f32<<<blocks, 256, 0, st>>>(out, U, count);
+    return 1;
 }
 
 template <int ORDER, int NV, class R>
@@ -69,15 +94,24 @@ static int launch_recon_nv(const StepArgs& a, const double* U, cudaStream_t st) 
         }
         n = 1;
     }
+    // the state in the bulk precision: FP32 steps read a copy rounded once per step
+    using In = R;
+    const In* Ui;
+    if constexpr (sizeof(R) == 4) {
+        n += launch_to_f32(const_cast<float*>(a.Uf), U, 5 * a.grid.n, st);
+        Ui = a.Uf;
+    } else {
+        Ui = U;
+    }
     switch (a.order) {
-        case 2: k_weno1d<2, NV, R><<<blocks, T, 0, st>>>(a.grid, U, ZB, S1); n += 1; break;
+        case 2: k_weno1d<2, NV, R, In><<<blocks, T, 0, st>>>(a.grid, Ui, ZB, S1); n += 1; break;
         case 3:
-            k_weno1d<3, NV, R><<<blocks, T, 0, st>>>(a.grid, U, ZB, S1);
+            k_weno1d<3, NV, R, In><<<blocks, T, 0, st>>>(a.grid, Ui, ZB, S1);
             k_cross1<3, NV, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
             n += 2;
             break;
         default:
-            k_weno1d<4, NV, R><<<blocks, T, 0, st>>>(a.grid, U, ZB, S1);
+            k_weno1d<4, NV, R, In><<<blocks, T, 0, st>>>(a.grid, Ui, ZB, S1);
             k_cross1<4, NV, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
             k_cross2<NV, R><<<blocks, T, 0, st>>>(a.grid, S2);
             n += 3;

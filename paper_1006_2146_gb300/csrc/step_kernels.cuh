@@ -27,7 +27,10 @@ ADER_DEV void load_modes(const StepArgs& a, const double* __restrict__ U, long l
     const R* S2 = (const R*)a.S2;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        m[1][v] = v < 5 ? R(U[v * N + z]) : ((const R*)a.ZB)[(v - 5) * N + z];
+        if constexpr (sizeof(R) == 4)       // FP32 bulk: the zone means from the FP32 copy of the state
+            m[1][v] = v < 5 ? (a.Uf ? a.Uf[v * N + z] : R(U[v * N + z])) : ((const R*)a.ZB)[(v - 5) * N + z];
+        else
+            m[1][v] = v < 5 ? R(U[v * N + z]) : ((const R*)a.ZB)[(v - 5) * N + z];
 #pragma unroll
         for (int d = 0; d < 3; ++d) m[2 + d][v] = S1[((0 * 3 + d) * NV + v) * N + z];          // w2 w3 w4
         if (ORDER >= 3) {
@@ -114,9 +117,9 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
     load_modes<ORDER>(a, U, z, m);
 #pragma unroll
     for (int k = LS + 1; k <= L; ++k) m[k] = vzero<NV, R>();
-    const double dt = a.dt_dev ? *a.dt_dev : a.dt;
-    const R gm1 = R(a.gamma - 1.0);
-    const R cx = R(dt / a.dx[0]), cy = R(dt / a.dx[1]), cz = R(dt / a.dx[2]);
+    const R dt = R(a.dt_dev ? *a.dt_dev : a.dt);
+    const R gm1 = arg_gm1<R>(a);
+    const R cx = dt * arg_idx<R>(a, 0), cy = dt * arg_idx<R>(a, 1), cz = dt * arg_idx<R>(a, 2);
     if (a.n_iter > 0) {      // n_iter = 0: spatial polynomial only (SSP-RK face rule)
         if constexpr (ORDER == 3) {
             if (a.G) {          // learned initial guess of the evolutionary modes
@@ -173,7 +176,7 @@ ADER_DEV void flux_difference(const StepArgs& a, long long z, int i, int j, int 
     const long long zm = nbr(a.grid, i, j, k, -(D == 0), -(D == 1), -(D == 2));
     const Vec<NV, R> Fp = riemann<SOLVER, D>(load_side<NV, R>(a, 2 * D, z), load_side<NV, R>(a, 2 * D + 1, zp), gamma, gm1);
     const Vec<NV, R> Fm = riemann<SOLVER, D>(load_side<NV, R>(a, 2 * D, zm), load_side<NV, R>(a, 2 * D + 1, z), gamma, gm1);
-    const double inv = rcp(a.dx[D]);
+    const double inv = a.idx[D];
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] -= ((double)Fp[v] - (double)Fm[v]) * inv;
 }
@@ -184,7 +187,7 @@ ADER_DEV void zone_flux_update(const StepArgs& a, double* out, const double* bas
     const int i = (int)(z % a.grid.nx);
     const long long t = z / a.grid.nx;
     const int j = (int)(t % a.grid.ny), k = (int)(t / a.grid.ny);
-    const R gamma = R(a.gamma), gm1 = R(a.gamma - 1.0);
+    const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
     double acc[5] = {0, 0, 0, 0, 0};
     flux_difference<SOLVER, 0, NV, R>(a, z, i, j, k, gamma, gm1, acc);
     flux_difference<SOLVER, 1, NV, R>(a, z, i, j, k, gamma, gm1, acc);
@@ -276,7 +279,7 @@ ADER_DEV void zone_emf(const StepArgs& a, long long z) {
     const int i = (int)(z % g.nx);
     const long long t = z / g.nx;
     const int j = (int)(t % g.ny), k = (int)(t / g.ny);
-    const R gamma = R(a.gamma), gm1 = R(a.gamma - 1.0);
+    const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
     const long long zx = nbr(g, i, j, k, 1, 0, 0), zy = nbr(g, i, j, k, 0, 1, 0), zz = nbr(g, i, j, k, 0, 0, 1);
     const long long zxy = nbr(g, i, j, k, 1, 1, 0), zxz = nbr(g, i, j, k, 1, 0, 1), zyz = nbr(g, i, j, k, 0, 1, 1);
     // x-faces: t1 = y (slots 0, 1), t2 = z (2, 3); y-faces: t1 = x, t2 = z; z-faces: t1 = x, t2 = y
@@ -312,7 +315,7 @@ ADER_DEV void zone_ct(const StepArgs& a, double* Bf, double c_host, int use_dt_d
     auto Ey = [&](int di, int dj, int dk) { return (double)E[N + nbr(g, i, j, k, di, dj, dk)]; };
     auto Ez = [&](int di, int dj, int dk) { return (double)E[2 * N + nbr(g, i, j, k, di, dj, dk)]; };
     const double dt = use_dt_dev ? c_host * (*a.dt_dev) : c_host;
-    const double idx = 1.0 / a.dx[0], idy = 1.0 / a.dx[1], idz = 1.0 / a.dx[2];
+    const double idx = a.idx[0], idy = a.idx[1], idz = a.idx[2];
     // the edges of face i-1/2 are stored one zone lower in x (likewise for y, z)
     Bf[z] -= dt * ((Ez(-1, 0, 0) - Ez(-1, -1, 0)) * idy - (Ey(-1, 0, 0) - Ey(-1, 0, -1)) * idz);
     Bf[N + z] -= dt * ((Ex(0, -1, 0) - Ex(0, -1, -1)) * idz - (Ez(0, -1, 0) - Ez(-1, -1, 0)) * idx);

@@ -130,14 +130,15 @@ ADER_DEV R slope_of(const Grid& g, const R* __restrict__ F, int i, int j, int k,
 // from U; for MHD (NV = 8) variable 5 + e is the zone field B_e read from ZB,
 // whose moments along e come from the face-B WENO (zone_face_b), so only the
 // two transverse directions are reconstructed here.
-template <int ORDER, int NV, class R>
-ADER_DEV void zone_weno1d(const Grid& g, const double* __restrict__ U, const R* __restrict__ ZB,
+// T: the type U is read in (double, or the FP32 copy of FP32-bulk steps).
+template <int ORDER, int NV, class R, class T>
+ADER_DEV void zone_weno1d(const Grid& g, const T* __restrict__ U, const R* __restrict__ ZB,
                           R* __restrict__ S1, long long z) {
     int i, j, k;
     zone_ijk(g, z, i, j, k);
     constexpr int RAD = ORDER == 4 ? 3 : 2;
     for (int v = 0; v < NV; ++v) {
-        const double* Uv = v < 5 ? U + (long long)v * g.n : nullptr;
+        const T* Uv = v < 5 ? U + (long long)v * g.n : nullptr;
         const R* Bv = v >= 5 ? ZB + (long long)(v - 5) * g.n : nullptr;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
