@@ -104,8 +104,10 @@ int ader_max_dt(ader_ctx* ctx, const double* U, const double* Bface, double cfl,
 
 /* One SSP-RK step of the context's order (Eq. 18 for order 2, Eq. 19 for
  * order 3, Eq. 20 for order 4) with the same reconstruction and Riemann
- * solver and the App. D facial quadrature with every time mode zero.
- * Euler contexts only. */
+ * solver and the App. D facial quadrature with every time mode zero.  MHD:
+ * Bface advances with the same stage combinations, its operator being
+ * -curl E from the stage's edge fields (the rate whose Euler step is Eq. 8),
+ * so every stage keeps the discrete div B.  U and Bface as for ader_step. */
 int ader_rk_step(ader_ctx* ctx, double* U, double* Bface, double dt, void* stream);
 
 /* End-to-end step through host memory: copies U_host to the device, runs

@@ -143,17 +143,24 @@ def div_b(Bface, dx):
 
 
 # ----------------------------------------------------------------------------- SSP-RK, Sec. II.d
-def rk_operator(U, dx, order, solver="hll", gamma=1.4):
-    """L(U) = -sum_d (Fbar(i+1/2) - Fbar(i-1/2))/dx_d with the spatial-only face rule."""
-    Uz, W = zone_state(U, None, order)
+def rk_operator(U, dx, order, solver="hll", gamma=1.4, Bface=None):
+    """L(U) = -sum_d (Fbar(i+1/2) - Fbar(i-1/2))/dx_d with the spatial-only face rule.
+
+    MHD (Bface given): also L(B) = -curl E of the face field, the rate whose Euler step is Eq. 8, with the
+    edge fields of Eq. 7 from the same spatial-only face and edge data; returns (L(U), L(B)).
+    """
+    mhd = Bface is not None
+    Uz, W = zone_state(U, Bface, order)
     LSn, Ln = basis.LS[order], basis.L[order]
     Uhat = np.zeros((Ln,) + W.shape[1:])
     Uhat[:LSn] = W
-    F, _ = _face_fluxes(Uhat, order, gamma, solver, Uz, False)
+    F, edge_data = _face_fluxes(Uhat, order, gamma, solver, Uz, mhd)
     out = np.zeros_like(U)
     for d in range(3):
         out = out - (F[d][:5] - weno.shift(F[d][:5], d, -1)) / dx[d]
-    return out
+    if not mhd:
+        return out
+    return out, ct_update(np.zeros_like(Bface), F, edge_data, Uz, order, gamma, solver, 1.0, dx)
 
 
 RK_STAGES = {
@@ -176,19 +183,24 @@ RK_STAGES = {
 }
 
 
-def rk_step(U, dx, dt, order, solver="hll", gamma=1.4):
-    """One SSP-RK step of the order's scheme (Eq. 18, 19 or 20)."""
+def rk_step(U, dx, dt, order, solver="hll", gamma=1.4, Bface=None):
+    """One SSP-RK step of the order's scheme (Eq. 18, 19 or 20); MHD advances (U, Bface) together."""
     A, B = RK_STAGES[order]
-    states = [U]
+    mhd = Bface is not None
+    states = [(U, Bface) if mhd else (U,)]
     ops = []
     for s in range(len(A)):
-        ops.append(rk_operator(states[-1], dx, order, solver, gamma))
-        nxt = np.zeros_like(U)
-        for j, a in enumerate(A[s]):
-            if a != 0.0:
-                nxt = nxt + a * states[j]
-        for j, b in enumerate(B[s]):
-            if b != 0.0:
-                nxt = nxt + b * dt * ops[j]
-        states.append(nxt)
-    return states[-1]
+        op = rk_operator(states[-1][0], dx, order, solver, gamma, states[-1][1] if mhd else None)
+        ops.append(op if mhd else (op,))
+        nxt = []
+        for c in range(len(states[0])):
+            x = np.zeros_like(states[0][c])
+            for j, a in enumerate(A[s]):
+                if a != 0.0:
+                    x = x + a * states[j][c]
+            for j, b in enumerate(B[s]):
+                if b != 0.0:
+                    x = x + b * dt * ops[j][c]
+            nxt.append(x)
+        states.append(tuple(nxt))
+    return states[-1] if mhd else states[-1][0]

@@ -32,11 +32,13 @@ struct ader_ctx {
     double* dt_dev = nullptr;                 // device dt of the host-memory path
     double* Ustage = nullptr;                 // device state of the host-memory path
     double* rk[7] = {};                       // SSP-RK stage states and operators
+    double* rkB[6] = {};                      // MHD: SSP-RK stage face fields and the stored operator
     double tol = 0.0;                         // converged predictor tolerance (0: fixed M-1 iterations)
     int max_iter = 50;
     unsigned long long* stats = nullptr;      // converged predictor statistics (3 words)
     const float* guess = nullptr;             // learned-guess MLP parameters (device), order 3
     float* G = nullptr;                       // per-zone learned guess (5 x NV x N FP32), allocated by ader_set_guess
+    float* Uf = nullptr;                      // FP32 bulk: the state rounded to FP32 (5 x N), rewritten each step
     bool setup_failed = false;                // a kernel could not be configured while enqueuing
     int launches = 0;
     std::string err;
@@ -103,6 +105,8 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.dx[0] = c->g.dx;
     a.dx[1] = c->g.dy;
     a.dx[2] = c->g.dz;
+    finish_args(a);
+    a.Uf = c->Uf;
     a.dt = dt;
     a.dt_dev = dt_dev;
     a.S1 = c->S1;
@@ -201,6 +205,7 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
         alloc(&c->ZB, N * 3 * c->rsize, "cudaMalloc zone B");
         alloc(&c->E, N * 3 * c->rsize, "cudaMalloc EMF");
     }
+    if (c->fp32) alloc((void**)&c->Uf, N * 5 * sizeof(float), "cudaMalloc FP32 state copy");
     alloc((void**)&c->flag, sizeof(unsigned), "cudaMalloc flag");
     alloc((void**)&c->stats, 3 * sizeof(unsigned long long), "cudaMalloc predictor statistics");
     alloc((void**)&c->dtscr, 2 * sizeof(unsigned long long), "cudaMalloc dt scratch");
@@ -209,6 +214,8 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
     alloc((void**)&c->dt_dev, sizeof(double), "cudaMalloc dt");
     alloc((void**)&c->Ustage, N * 5 * sizeof(double), "cudaMalloc host-path state");
     for (int s = 0; s < 7; ++s) alloc((void**)&c->rk[s], N * 5 * sizeof(double), "cudaMalloc RK stage");
+    if (c->mhd)
+        for (int s = 0; s < 6; ++s) alloc((void**)&c->rkB[s], N * 3 * sizeof(double), "cudaMalloc RK face field");
     if (rc == ADER_OK) rc = cuda_check(c, cudaMemset(c->flag, 0, sizeof(unsigned)), "cudaMemset flag");
     if (rc == ADER_OK) rc = cuda_check(c, cudaMemset(c->stats, 0, 3 * sizeof(unsigned long long)), "cudaMemset");
     if (rc == ADER_OK) rc = cuda_check(c, cudaMemset(c->dtscr, 0, 2 * sizeof(unsigned long long)), "cudaMemset");
@@ -227,8 +234,9 @@ void ader_destroy(ader_ctx* c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->spare) cudaEventDestroy(e);
-    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->flag, c->stats, c->dtscr, c->partial, c->dt_dev,
-                    c->Ustage, c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6]};
+    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Uf, c->flag, c->stats, c->dtscr, c->partial, c->dt_dev,
+                    c->Ustage, c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6],
+                    c->rkB[0], c->rkB[1], c->rkB[2], c->rkB[3], c->rkB[4], c->rkB[5]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -363,51 +371,79 @@ static const double RK4B[5][5] = {{0.39175222700392, 0, 0, 0, 0},
 int ader_rk_step(ader_ctx* c, double* U, double* Bface, double dt, void* stream) {
     if (!c) return ADER_ERR_ARG;
     if (!U) return fail(c, ADER_ERR_ARG, "U is null");
-    if (Bface || c->mhd) return fail(c, ADER_ERR_ARG, "ader_rk_step is built for Euler contexts only");
+    if (int rc = check_bface(c, Bface)) return rc;
     if (!(dt > 0.0)) return fail(c, ADER_ERR_ARG, "dt must be positive");
     cudaStream_t st = (cudaStream_t)stream;
+    const bool mhd = c->mhd;
     const int ns = c->order == 2 ? 2 : (c->order == 3 ? 3 : 5);
     const double* A = c->order == 2 ? &RK2A[0][0] : (c->order == 3 ? &RK3A[0][0] : &RK4A[0][0]);
     const double* B = c->order == 2 ? &RK2B[0][0] : (c->order == 3 ? &RK3B[0][0] : &RK4B[0][0]);
-    const StepArgs a = make_args(c, dt, nullptr, 0);
-    const long long cnt = c->grid.n * 5;
-    // states[0] = U^n (copied), states[s] = U(s); ops[s] = L(U(s)) (stored only where reused)
+    const StepArgs a0 = make_args(c, dt, nullptr, 0);
+    const long long cnt = c->grid.n * 5, cntB = c->grid.n * 3;
+    // states[0] = U^n (copied), states[s] = U(s); ops[s] = L(U(s)) (stored only where reused);
+    // for MHD the same for the face field (its operator is -curl E, the rate of Eq. 8)
     double* states[5] = {c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4]};
     double* ops[2] = {c->rk[5], c->rk[6]};
+    double* statesB[5] = {c->rkB[0], c->rkB[1], c->rkB[2], c->rkB[3], c->rkB[4]};
+    double* opsB = c->rkB[5];
     int n = 0;
     cudaError_t e = cudaMemcpyAsync(states[0], U, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && mhd)
+        e = cudaMemcpyAsync(statesB[0], Bface, cntB * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_check(c, e, "cudaMemcpyAsync");
     for (int s = 0; s < ns; ++s) {
         const double* rowA = A + s * ns;
         const double* rowB = B + s * ns;
+        StepArgs a = a0;
+        a.Bface = mhd ? statesB[s] : nullptr;          // the stage's face field (face-B WENO, EMFs)
         // state part of the stage
         const double* X[6];
+        const double* XB[6];
         double w[6];
         int m = 0;
         for (int j = 0; j <= s; ++j)
             if (rowA[j] != 0.0) {
                 X[m] = states[j];
+                XB[m] = mhd ? statesB[j] : nullptr;
                 w[m++] = rowA[j];
             }
         // operator terms other than L(U(s)) come from stored operators (only SSP(5,4)'s last stage)
         if (ns == 5 && s == 4) {
             X[m] = ops[0];          // L(U(3)) stored at stage 3
+            XB[m] = opsB;
             w[m++] = rowB[3] * dt;
         }
         double* dst = (s == ns - 1) ? U : states[s + 1];
+        double* dstB = mhd ? ((s == ns - 1) ? Bface : statesB[s + 1]) : nullptr;
         {
             Trace t(c, "rk_combine", st);
             n += launch_lincomb(dst, m, X, w, cnt, st);
+            if (mhd) n += launch_lincomb(dstB, m, XB, w, cntB, st);
         }
         if (ns == 5 && s == 3) {
-            // keep L(U(3)) for the final stage: ops[0] = L(U(3)); then dst += B[3][3] dt L(U(3))
+            // keep L(U(3)) (and L(B(3))) for the final stage, then dst += B[3][3] dt L(U(3))
             n += enqueue_operator(c, a, states[3], ops[0], nullptr, 1.0, false, st);
+            if (mhd) {
+                if (int rc = cuda_check(c, cudaMemsetAsync(opsB, 0, cntB * sizeof(double), st), "cudaMemsetAsync"))
+                    return rc;
+                Trace t(c, "emf_ct", st);
+                n += c->fp32 ? launch_emf_ct<float>(a, opsB, 1.0, false, st) : launch_emf_ct<double>(a, opsB, 1.0, false, st);
+            }
             const double* Y[2] = {dst, ops[0]};
             const double wy[2] = {1.0, rowB[3] * dt};
             Trace t(c, "rk_combine", st);
             n += launch_lincomb(dst, 2, Y, wy, cnt, st);
+            if (mhd) {
+                const double* YB[2] = {dstB, opsB};
+                n += launch_lincomb(dstB, 2, YB, wy, cntB, st);
+            }
         } else {
             n += enqueue_operator(c, a, states[s], dst, dst, rowB[s] * dt, false, st);
+            if (mhd) {
+                Trace t(c, "emf_ct", st);
+                n += c->fp32 ? launch_emf_ct<float>(a, dstB, rowB[s] * dt, false, st)
+                             : launch_emf_ct<double>(a, dstB, rowB[s] * dt, false, st);
+            }
         }
     }
     c->launches = n + 1;

@@ -129,3 +129,23 @@ def test_mhd_diagnostics_totals_and_div_b(ader):
     got2 = out2.cpu().numpy()
     assert np.all(np.abs(got2[:8] - got[:8]) <= 1e-13 * scale)
     ader.ader_destroy(h)
+
+
+@pytest.mark.parametrize("order,solver", [(2, "hll"), (3, "hll"), (3, "linearized"), (4, "hll")])
+def test_mhd_ssprk_step_parity_fp64(ader, order, solver):
+    """SSP-RK of the same order and solver for MHD (Eqs. 18-20 with the CT-rate operator) against the oracle;
+    div B unchanged to round-off."""
+    n = 10
+    U, B = _perturbed_alfven(n, seed=8)
+    dx = (1.0 / n,) * 3
+    dt = 0.3 * scheme.max_dt(U, dx, 0.4, G, Bface=B)
+    Uo, Bo = scheme.rk_step(U, dx, dt, order, solver, G, Bface=B)
+    h = _mhd_solver(ader, (n, n, n), order, "modal", solver=solver)
+    dU, dB = to_dev(U), to_dev(B)
+    ader.ader_rk_step(h, dU, dB, dt)
+    assert ader.ader_sync_status(h) == 0
+    assert rel_l1(to_host(dU), Uo) <= 1e-12
+    assert rel_l1(to_host(dB), Bo) <= 1e-12
+    d0 = scheme.div_b(B, dx)
+    assert np.abs(scheme.div_b(to_host(dB), dx) - d0).max() <= 1e-12 * np.abs(B).max() / dx[0]
+    ader.ader_destroy(h)

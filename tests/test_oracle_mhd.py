@@ -88,3 +88,39 @@ def test_emf_identification_on_uniform_state():
     np.testing.assert_allclose(Ex, E[0], atol=1e-13)
     np.testing.assert_allclose(Ey, E[1], atol=1e-13)
     np.testing.assert_allclose(Ez, E[2], atol=1e-13)
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_ssprk_mhd_keeps_div_b_and_conserves(order):
+    """SSP-RK with the spatial-only operator (Eqs. 18-20; L(B) = -curl E, the rate of Eq. 8): each stage is a
+    combination of CT updates, so div B is unchanged to round-off and the totals are conserved."""
+    rng = np.random.default_rng(10 + order)
+    n = 8
+    dx = (1.0 / n,) * 3
+    U, B = inputs.alfven_wave(n, amp=0.3)
+    U = U * (1.0 + 0.02 * rng.normal(size=U.shape))
+    U[4] += 0.5
+    d0 = scheme.div_b(B, dx)
+    dt = 0.3 * scheme.max_dt(U, dx, 0.4, G, Bface=B)
+    U1, B1 = scheme.rk_step(U, dx, dt, order, "hll", G, Bface=B)
+    scale = np.abs(B).max() / dx[0]
+    assert np.abs(scheme.div_b(B1, dx) - d0).max() <= 1e-13 * scale
+    assert np.abs(B1 - B).max() > 1e-6
+    np.testing.assert_allclose(B1.reshape(3, -1).sum(axis=1), B.reshape(3, -1).sum(axis=1), atol=1e-12 * np.abs(B).sum())
+    np.testing.assert_allclose(U1.reshape(5, -1).sum(axis=1), U.reshape(5, -1).sum(axis=1), atol=1e-12 * np.abs(U).sum())
+
+
+def test_ssprk_mhd_alfven_wave_convergence():
+    """SSP-RK3 with the third-order spatial operator on the Alfven wave: L1 order within 0.2 of 3."""
+    errs = []
+    for n in (8, 16):
+        U, B = inputs.alfven_wave(n)
+        dx = (1.0 / n,) * 3
+        t, T = 0.0, 0.05
+        while t < T - 1e-14:
+            dt = min(0.5 * scheme.max_dt(U, dx, 0.4, G, Bface=B), T - t)
+            U, B = scheme.rk_step(U, dx, dt, 3, "hll", G, Bface=B)
+            t += dt
+        Ue, Be = inputs.alfven_wave(n, t=T)
+        errs.append(np.abs(B - Be).mean() + np.abs(U[1:4] - Ue[1:4]).mean())
+    assert np.log2(errs[0] / errs[1]) >= 3 - 0.2
