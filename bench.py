@@ -183,6 +183,7 @@ def mhd_variants(ader, torch, stream, n=128, steps=3, warmup=1):
             d, b = U0.clone(), B0.clone()
             dt = torch.zeros(1, dtype=torch.float64, device="cuda")
             _lib.ader_max_dt(h, d, b, 0.4, dt, stream)
+            torch.cuda.synchronize()
             dt_rk = 0.5 * float(dt.item())            # SSP-RK3 at half the ADER step (host dt: its stages)
             with torch.cuda.stream(stream):
                 for _ in range(warmup):

@@ -124,6 +124,20 @@ def test_fp32_bulk_all_orders_one_step(ader, order):
     assert rel_l1(_gpu_step(ader, U, shape, dt, order, "modal", "linearized", fp32=True), want) <= 1e-6
 
 
+@pytest.mark.parametrize("form", FORMS)
+def test_fp32_tiled_cross_moments(ader, form):
+    """FP32, third order, on a grid whose x and y sizes take the shared-memory tiles of the cross moments
+    (x a multiple of 32, y of 8; z not a multiple of the 32-plane chunks): one step within the FP32 bar of
+    the oracle."""
+    shape = (10, 16, 64)
+    U = inputs.random_smooth(shape, seed=21, amp=0.3)
+    dx = _dx(shape)
+    dt = 0.8 * scheme.max_dt(U, dx, 0.4)
+    want = scheme.ader_step(U, dx, dt, 3, form, "hll")
+    got = _gpu_step(ader, U, shape, dt, 3, form, "hll", fp32=True)
+    assert rel_l1(got, want) <= 1e-6
+
+
 def test_max_dt_parity(ader):
     import torch
     shape = (7, 9, 12)
