@@ -72,6 +72,100 @@ __global__ void __launch_bounds__(128) k_cross1(Grid g, const R* __restrict__ S1
     if (z < g.n) zone_cross1<ORDER, NV>(g, S1, S2, z);
 }
 
+// Third-order cross moments in FP32 from shared-memory tiles (2.5-D
+// blocking).  A block of CT_X x CT_Y threads owns a tile of the x-y plane and
+// marches through CT_Z planes of z (4 more planes of the z window are read per chunk).  Each thread keeps w2 and w3 of its column
+// at z-2..z+2 in registers (for the z slopes); the plane z of w2 (with y
+// halos), w3 (x halos) and w4 (both) sits in shared memory for the x and y
+// slopes.  Every moment is read about once per zone and plane instead of once
+// per neighbour stencil that uses it; the arithmetic is zone_cross1's.
+// Requires nx % CT_X == 0 and ny % CT_Y == 0 (other grids use k_cross1).
+constexpr int CT_X = 32, CT_Y = 8, CT_Z = 8;    // 8-plane chunks: enough blocks to fill the SMs from 128^3 up
+
+template <int NV>
+__global__ void __launch_bounds__(CT_X * CT_Y) k_cross1_tiled(Grid g, const float* __restrict__ S1,
+                                                              float* __restrict__ S2) {
+    __shared__ float s2[CT_Y + 4][CT_X];          // w2 with two rows of y halo on each side
+    __shared__ float s3[CT_Y][CT_X + 4];          // w3 with two columns of x halo
+    __shared__ float s4[CT_Y + 4][CT_X + 4];      // w4 with both
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tiles_x = g.nx / CT_X;
+    const int i = (int)(blockIdx.x % tiles_x) * CT_X + tx, j = (int)(blockIdx.x / tiles_x) * CT_Y + ty;
+    const int k0 = (int)blockIdx.y * CT_Z, k1 = min(k0 + CT_Z, g.nz);
+    const long long N = g.n;
+    auto at = [&](int ii, int jj, int kk) -> long long {
+        return ((long long)wrap(kk, g.nz) * g.ny + wrap(jj, g.ny)) * g.nx + wrap(ii, g.nx);
+    };
+    for (int v = 0; v < NV; ++v) {
+        const float* w2 = S1 + ((0 * 3 + 0) * NV + v) * N;
+        const float* w3 = S1 + ((0 * 3 + 1) * NV + v) * N;
+        const float* w4 = S1 + ((0 * 3 + 2) * NV + v) * N;
+        float c2[5], c3[5];                        // the column at z - 2 .. z + 2
+#pragma unroll
+        for (int o = -2; o <= 1; ++o) {
+            c2[o + 3] = w2[at(i, j, k0 + o)];
+            c3[o + 3] = w3[at(i, j, k0 + o)];
+        }
+        for (int k = k0; k < k1; ++k) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                c2[q] = c2[q + 1];
+                c3[q] = c3[q + 1];
+            }
+            c2[4] = w2[at(i, j, k + 2)];
+            c3[4] = w3[at(i, j, k + 2)];
+            // the plane k with its halos
+            s2[ty + 2][tx] = c2[2];
+            s3[ty][tx + 2] = c3[2];
+            s4[ty + 2][tx + 2] = w4[at(i, j, k)];
+            if (ty < 2) {
+                s2[ty][tx] = w2[at(i, j - 2, k)];
+                s4[ty][tx + 2] = w4[at(i, j - 2, k)];
+            }
+            if (ty >= CT_Y - 2) {
+                s2[ty + 4][tx] = w2[at(i, j + 2, k)];
+                s4[ty + 4][tx + 2] = w4[at(i, j + 2, k)];
+            }
+            if (tx < 2) {
+                s3[ty][tx] = w3[at(i - 2, j, k)];
+                s4[ty + 2][tx] = w4[at(i - 2, j, k)];
+            }
+            if (tx >= CT_X - 2) {
+                s3[ty][tx + 4] = w3[at(i + 2, j, k)];
+                s4[ty + 2][tx + 4] = w4[at(i + 2, j, k)];
+            }
+            __syncthreads();
+            float a[5];
+#pragma unroll
+            for (int o = 0; o < 5; ++o) a[o] = s2[ty + o][tx];
+            const float sy2 = slope(a);
+#pragma unroll
+            for (int o = 0; o < 5; ++o) a[o] = s3[ty][tx + o];
+            const float sx3 = slope(a);
+#pragma unroll
+            for (int o = 0; o < 5; ++o) a[o] = s4[ty + o][tx + 2];
+            const float sy4 = slope(a);
+#pragma unroll
+            for (int o = 0; o < 5; ++o) a[o] = s4[ty + 2][tx + o];
+            const float sx4 = slope(a);
+            const float sz3 = slope(c3), sz2 = slope(c2);
+            const long long z = ((long long)k * g.ny + j) * g.nx + i;
+            S2[(0 * NV + v) * N + z] = 0.5f * (sy2 + sx3);
+            S2[(1 * NV + v) * N + z] = 0.5f * (sz3 + sy4);
+            S2[(2 * NV + v) * N + z] = 0.5f * (sz2 + sx4);
+            __syncthreads();
+        }
+    }
+}
+
+template <int NV>
+static bool launch_cross1_tiled(const Grid& g, const float* S1, float* S2, cudaStream_t st) {
+    if (g.nx % CT_X != 0 || g.ny % CT_Y != 0) return false;
+    const dim3 grid((unsigned)((g.nx / CT_X) * (g.ny / CT_Y)), (unsigned)((g.nz + CT_Z - 1) / CT_Z));
+    k_cross1_tiled<NV><<<grid, dim3(CT_X, CT_Y), 0, st>>>(g, S1, S2);
+    return true;
+}
+
 template <int NV, class R>
 __global__ void __launch_bounds__(128) k_cross2(Grid g, R* __restrict__ S2) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -107,7 +201,12 @@ static int launch_recon_nv(const StepArgs& a, const double* U, cudaStream_t st) 
         case 2: k_weno1d<2, NV, R, In><<<blocks, T, 0, st>>>(a.grid, Ui, ZB, S1); n += 1; break;
         case 3:
             k_weno1d<3, NV, R, In><<<blocks, T, 0, st>>>(a.grid, Ui, ZB, S1);
-            k_cross1<3, NV, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
+            if constexpr (sizeof(R) == 4) {      // FP32: shared-memory tiles where the grid allows them
+                if (!launch_cross1_tiled<NV>(a.grid, S1, S2, st))
+                    k_cross1<3, NV, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
+            } else {
+                k_cross1<3, NV, R><<<blocks, T, 0, st>>>(a.grid, S1, S2);
+            }
             n += 2;
             break;
         default:
