@@ -55,6 +55,28 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(secs, world, device):
+    """The slowest rank's timed seconds (every rank returns the same value); world == 1 returns secs."""
+    if world <= 1:
+        return secs
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([secs], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step, steps, world, secs):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time (weak scaling,
+    every rank runs its own problem of the same size)."""
+    return units_per_rank_step * steps * world / secs
+
+
+def cores_used(cpu_s, wall_s):
+    """Threads a host run kept busy on average: process CPU time over wall time, at least one."""
+    return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -528,12 +550,8 @@ def gpu_arm(args):
     barrier()
     wall = time.perf_counter() - t0
     ck = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([secs], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        secs = float(tt.item())
-    value = zones * args.steps * world / secs
+    secs = max_over_ranks(secs, world, "cuda")
+    value = job_throughput(zones, args.steps, world, secs)
 
     # dominant kernel roofline: FLOPs per zone x zones / mean launch time.  The plain kernels are bound by
     # the FP64 (or FP32) ALUs; the learned-guess kernel is a dense contraction on the tensor cores.
@@ -663,14 +681,14 @@ def cpu_baseline(args, budget_s=15.0):
     m = 32
     U = inputs.sod_planar(m)
     dx = (1.0 / m,) * 3
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     steps = 0
     while time.perf_counter() - t0 < budget_s or steps == 0:
         dt = scheme.max_dt(U, dx, 0.4)
         U = scheme.ader_step(U, dx, dt, args.order, args.form, args.solver)
         steps += 1
     el = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+    threads = cores_used(time.process_time() - c0, el)
     return {"value": m ** 3 * steps / el, "unit": "zone-updates/s", "cores": threads, "kind": "oracle",
             "sample": "%d steps of the same scheme on a %d^3 Sod tube (numpy FP64 oracle, %.1f s)" % (steps, m, el)}
 
@@ -693,11 +711,11 @@ def reference_arm(args):
 
     for _ in range(args.warmup):
         U = step(U)
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     for _ in range(args.steps):
         U = step(U)
     el = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+    threads = cores_used(time.process_time() - c0, el)
     value = m ** 3 * args.steps / el
     cpu = {"value": value, "unit": "zone-updates/s", "cores": threads, "kind": "oracle",
            "sample": "%d timed steps (after %d untimed) of the same scheme on a %d^3 Sod tube (numpy FP64 "
