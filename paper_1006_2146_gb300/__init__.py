@@ -15,27 +15,32 @@ from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_FP32_BULK, ADER_HLL, ADER_LINE
 
 
 class Solver:
-    """One ADER context on the current CUDA device (owns the library scratch)."""
+    """One ADER context on the current CUDA device (owns the library scratch).
 
-    def __init__(self, shape, order=3, form="modal", solver="hll", gamma=1.4, fp32=False, lengths=(1.0, 1.0, 1.0)):
+    mhd=True makes an ideal-MHD context: every call then takes the face field Bface (device, (3, nz, ny, nx)
+    FP64), which ader_step and ader_rk_step advance in place by constrained transport."""
+
+    def __init__(self, shape, order=3, form="modal", solver="hll", gamma=1.4, fp32=False, lengths=(1.0, 1.0, 1.0),
+                 mhd=False):
         nz, ny, nx = shape
         self.shape = tuple(shape)
+        self.mhd = mhd
         self.dx = (lengths[0] / nx, lengths[1] / ny, lengths[2] / nz)
-        flags = (ADER_NODAL if form == "nodal" else 0) | (ADER_FP32_BULK if fp32 else 0)
+        flags = (ADER_NODAL if form == "nodal" else 0) | (ADER_FP32_BULK if fp32 else 0) | (ADER_MHD if mhd else 0)
         sol = ADER_HLL if solver == "hll" else ADER_LINEARIZED
         self.h = ader_create(nx, ny, nz, self.dx[0], self.dx[1], self.dx[2], order, gamma, sol, flags)
 
-    def step(self, U, dt, stream=None):
-        ader_step(self.h, U, None, dt, stream)
+    def step(self, U, dt, stream=None, Bface=None):
+        ader_step(self.h, U, Bface, dt, stream)
 
-    def step_devdt(self, U, dt_dev, stream=None):
-        ader_step_devdt(self.h, U, None, dt_dev, stream)
+    def step_devdt(self, U, dt_dev, stream=None, Bface=None):
+        ader_step_devdt(self.h, U, Bface, dt_dev, stream)
 
-    def max_dt(self, U, cfl, dt_dev, stream=None):
-        ader_max_dt(self.h, U, None, cfl, dt_dev, stream)
+    def max_dt(self, U, cfl, dt_dev, stream=None, Bface=None):
+        ader_max_dt(self.h, U, Bface, cfl, dt_dev, stream)
 
-    def rk_step(self, U, dt, stream=None):
-        ader_rk_step(self.h, U, None, dt, stream)
+    def rk_step(self, U, dt, stream=None, Bface=None):
+        ader_rk_step(self.h, U, Bface, dt, stream)
 
     def set_predictor(self, tol, max_iter=50):
         ader_set_predictor(self.h, tol, max_iter)

@@ -225,6 +225,65 @@ def orszag_tang(n, gamma=5.0 / 3.0, rho0=25.0 / (36.0 * np.pi), P0=5.0 / (12.0 *
     return U, Bface
 
 
+def _zone_field(Bface):
+    """Zone-centred B: the mean of each component's two faces (for the magnetic energy of synthetic states)."""
+    return np.stack([0.5 * (Bface[d] + np.roll(Bface[d], -1, axis=2 - d)) for d in range(3)])
+
+
+def with_field(U, Bface):
+    """Euler state U plus the magnetic energy of the face field Bface: the MHD state (U, Bface)."""
+    Bz = _zone_field(Bface)
+    U = U.copy()
+    U[4] += (Bz ** 2).sum(axis=0) / (2.0 * FOUR_PI)
+    return U, Bface
+
+
+def random_magnetised(n, seed, amp=0.2, b_amp=0.3, B0=1.0, modes=6, kmax=2, gamma=5.0 / 3.0, P0=1.0):
+    """Seeded magnetised random state: rho and v as random_smooth, and B = B0 e + b from a periodic vector
+    potential.
+
+    e is a random unit vector; b = curl A with A a sum of `modes` Fourier modes a_m cos(2 pi k_m . x + phi_m)
+    (integer wave vectors, |k_m,i| <= kmax, a_m transverse to k_m), scaled so that the bound
+    sum_m 2 pi |k_m| |a_m| on |b| equals b_amp B0.  Bface comes from A by Stokes' theorem (divergence-free
+    to round-off).  Returns (U, Bface).
+    """
+    U = random_smooth(n, seed, amp=amp, gamma=gamma, P0=P0)
+    rng = np.random.default_rng(seed + 7919)
+    e = rng.normal(size=3)
+    e /= np.linalg.norm(e)
+    ks, amps, phases = [], [], []
+    for _ in range(modes):
+        k = np.zeros(3)
+        while not k.any():
+            k = rng.integers(-kmax, kmax + 1, 3).astype(np.float64)
+        a = rng.normal(size=3)
+        a -= k * (a @ k) / (k @ k)
+        ks.append(k)
+        amps.append(a)
+        phases.append(rng.uniform(0.0, 2 * np.pi))
+    bound = sum(2 * np.pi * np.linalg.norm(k) * np.linalg.norm(a) for k, a in zip(ks, amps))
+    scale = b_amp * B0 / bound
+
+    def comp(c):
+        def A(x, y, z):
+            out = 0.0 * (x + y + z)
+            for k, a, ph in zip(ks, amps, phases):
+                out = out + scale * a[c] * np.cos(2 * np.pi * (k[0] * x + k[1] * y + k[2] * z) + ph)
+            return out
+        return A
+
+    Bw = face_field_from_potential([comp(0), comp(1), comp(2)], n, npts=6)
+    Bface = np.stack([Bw[c] + B0 * e[c] for c in range(3)])
+    return with_field(U, Bface)
+
+
+def uniform_field(n, B0, direction):
+    """Face field of the uniform B = B0 direction / |direction| on an n^3 grid."""
+    e = np.asarray(direction, dtype=np.float64)
+    e = e / np.linalg.norm(e)
+    return np.stack([np.full((n, n, n), B0 * e[c]) for c in range(3)])
+
+
 def batch_problems(count=64, seed=1006, sizes=(32, 48, 64, 80, 96, 112, 128), mhd_fraction=0.5):
     """Seeded set of independent problems of uneven cubic sizes for the batched step.
 
