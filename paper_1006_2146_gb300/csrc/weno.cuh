@@ -7,8 +7,8 @@ namespace ader {
 constexpr double WENO_EPS = 1.0e-12;
 
 template <class R>
-ADER_DEV R wsq(R is) {
-    const R t = R(WENO_EPS) + is;
+ADER_DEV R wsq(R is, R eps) {
+    const R t = eps + is;
     return t * t;
 }
 
@@ -21,11 +21,11 @@ ADER_DEV R wsq(R is) {
 // form, where such products would underflow.  g may be any positive multiple
 // of the linear weights: the normalisation removes it.
 template <int S, class R>
-ADER_DEV R weno_weights(const R* g, const R* is, R* a) {
+ADER_DEV R weno_weights(const R* g, const R* is, R* a, R eps = R(WENO_EPS)) {
     if constexpr (sizeof(R) == 8) {
         R q[S], pre[S], suf[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) q[s] = wsq(is[s]);
+        for (int s = 0; s < S; ++s) q[s] = wsq(is[s], eps);
         pre[0] = R(1);
 #pragma unroll
         for (int s = 1; s < S; ++s) pre[s] = pre[s - 1] * q[s - 1];
@@ -43,27 +43,39 @@ ADER_DEV R weno_weights(const R* g, const R* is, R* a) {
         R d = R(0);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            a[s] = g[s] / wsq(is[s]);
+            a[s] = g[s] / wsq(is[s], eps);
             d += a[s];
         }
         return rcp(d);
     }
 }
 
-// order-3 1-D WENO on the five values a[-2..2] (a[2] = centre); returns b, c
+// order-3 1-D WENO on the five values a[-2..2] (a[2] = centre); returns b, c.
+// Each candidate is carried doubled, B = 2b and C = 2c, built from the four
+// neighbour differences d1..d4 (ten operations for the six moments), and the
+// smoothness indicators are 4 IS = B^2 + 13/3 C^2 with 4 EPS: every (EPS + IS)^2
+// is scaled by the same 16, so the normalised weights are unchanged.
+template <class R>
+ADER_DEV void weno3_doubled(const R* a, R* al, R& inv, R* B, R* C) {
+    const R d1 = a[1] - a[0], d2 = a[2] - a[1], d3 = a[3] - a[2], d4 = a[4] - a[3];
+    B[0] = R(3) * d2 - d1;  C[0] = d2 - d1;              // stencil {i-2, i-1, i}
+    B[1] = d2 + d3;         C[1] = d3 - d2;              // {i-1, i, i+1}
+    B[2] = R(3) * d3 - d4;  C[2] = d4 - d3;              // {i, i+1, i+2}
+    const R k13 = R(13.0 / 3.0);
+    const R g[3] = {R(1), R(10), R(1)};                  // (1, 10, 1) / 12
+    R is[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) is[s] = B[s] * B[s] + k13 * (C[s] * C[s]);
+    inv = weno_weights<3>(g, is, al, R(4.0 * WENO_EPS));
+}
+
 template <class R>
 ADER_DEV void weno3(const R* a, R& b, R& c) {
-    const R um2 = a[0], um1 = a[1], u0 = a[2], up1 = a[3], up2 = a[4];
-    const R bL = R(0.5) * (um2 - R(4) * um1 + R(3) * u0), cL = R(0.5) * (um2 - R(2) * um1 + u0);
-    const R bC = R(0.5) * (up1 - um1), cC = R(0.5) * (up1 - R(2) * u0 + um1);
-    const R bR = R(0.5) * (R(-3) * u0 + R(4) * up1 - up2), cR = R(0.5) * (u0 - R(2) * up1 + up2);
-    const R k13 = R(13.0 / 3.0);
-    const R g[3] = {R(1), R(10), R(1)};                       // (1, 10, 1) / 12
-    const R is[3] = {bL * bL + k13 * cL * cL, bC * bC + k13 * cC * cC, bR * bR + k13 * cR * cR};
-    R al[3];
-    const R inv = weno_weights<3>(g, is, al);
-    b = (al[0] * bL + al[1] * bC + al[2] * bR) * inv;
-    c = (al[0] * cL + al[1] * cC + al[2] * cR) * inv;
+    R al[3], B[3], C[3], inv;
+    weno3_doubled(a, al, inv, B, C);
+    const R h = R(0.5) * inv;
+    b = (al[0] * B[0] + al[1] * B[1] + al[2] * B[2]) * h;
+    c = (al[0] * C[0] + al[1] * C[1] + al[2] * C[2]) * h;
 }
 
 // order-4 1-D WENO on the seven values a[-3..3] (a[3] = centre); returns b, c, d
