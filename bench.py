@@ -168,7 +168,7 @@ def flops_per_zone(order, form, solver, fp32):
         f = json.load(fh)["order%d" % order]
     return {"weno_reconstruction": f["weno_reconstruction"],
             "predictor_faces": f["predictor_faces_" + form],
-            "riemann_update": f["riemann_update_" + solver]}
+            "riemann_update": f["riemann_update_" + ("fused_" if fp32 else "") + solver]}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -204,6 +204,7 @@ def mhd_variants(ader, torch, stream, n=128, steps=3, warmup=1):
                                  _lib.ADER_LINEARIZED if solver == "linearized" else _lib.ADER_HLL, flags)
             d, b = U0.clone(), B0.clone()
             dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()                    # the copies (current stream) before `stream` reads them
             _lib.ader_max_dt(h, d, b, 0.4, dt, stream)
             torch.cuda.synchronize()
             dt_rk = 0.5 * float(dt.item())            # SSP-RK3 at half the ADER step (host dt: its stages)
@@ -239,6 +240,80 @@ def mhd_variants(ader, torch, stream, n=128, steps=3, warmup=1):
     return out
 
 
+def mhd_learned_evaluation(ader, torch, stream, n=128, steps=3, train_n=64):
+    """The learned guess for ideal MHD on the unseen n^3 Orszag-Tang-type vortex (third order, modal,
+    linearized solver).  The MHD network is trained first (outside every timed region) on predictor samples
+    of the seeded magnetised training states at train_n^3.  Each run starts from the same state, takes one
+    warm-up step, then `steps` timed steps of one fixed dt; it reports the mean predictor iterations and,
+    for FP32, the error against the FP64 converged predictor (the judge of the guess's error)."""
+    from paper_1006_2146_gb300 import _lib, inputs, learned
+    out = {}
+    try:
+        t0 = time.perf_counter()
+        X, Y = learned.make_samples(learned.training_states(train_n, mhd=True), train_n, mhd=True)
+        t1 = time.perf_counter()
+        P, losses = learned.train(X, Y, mhd=True)
+        torch.cuda.synchronize()
+        out["training"] = {"samples": int(X.shape[0]), "epochs": len(losses), "first_epoch_loss": losses[0],
+                           "final_loss": losses[-1], "sample_s": t1 - t0, "train_s": time.perf_counter() - t1}
+        del X, Y
+        Uh, Bh = inputs.orszag_tang(n)
+        U0 = torch.from_numpy(Uh).to("cuda")
+        B0 = torch.from_numpy(Bh).to("cuda")
+    except Exception as exc:
+        out["error"] = str(exc)[:200]
+        return out
+    zones = n ** 3
+
+    def run(fp32, tol, guess):
+        flags = _lib.ADER_MHD | (_lib.ADER_FP32_BULK if fp32 else 0)
+        h = _lib.ader_create(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n, 3, 5.0 / 3.0, _lib.ADER_LINEARIZED, flags)
+        try:
+            dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+            _lib.ader_max_dt(h, U0, B0, 0.4, dtv, stream)
+            torch.cuda.synchronize()
+            dt = float(dtv.item())
+            _lib.ader_set_predictor(h, tol, 50)
+            if guess is not None:
+                _lib.ader_set_guess(h, guess)
+            d, b = U0.clone(), B0.clone()
+            torch.cuda.synchronize()                    # the copies (current stream) before `stream` reads them
+            _lib.ader_step(h, d, b, dt, stream)                 # warm-up step, counts discarded
+            torch.cuda.synchronize()
+            _lib.ader_predictor_stats(h, stream)
+            d, b = U0.clone(), B0.clone()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(steps):
+                    _lib.ader_step(h, d, b, dt, stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            secs = e0.elapsed_time(e1) / 1e3
+            tot, mx, capped = _lib.ader_predictor_stats(h, stream)
+            st = _lib.ader_sync_status(h, stream)
+        finally:
+            _lib.ader_destroy(h)
+        return d, b, {"zone_updates_per_s": zones * steps / secs, "ms_per_step": secs / steps * 1e3,
+                      "mean_predictor_iterations": tot / (steps * zones), "max_predictor_iterations": mx,
+                      "capped": capped, "status": st, "tol": tol}
+
+    try:
+        ref_d, ref_b, rec = run(False, 1e-13, None)
+        out["fp64_converged"] = rec
+        for name, fp32, tol, guess in (("fp64_converged_learned_guess", False, 1e-13, P),
+                                       ("fp32_converged", True, 1e-6, None),
+                                       ("fp32_converged_learned_guess", True, 1e-6, P)):
+            d, b, rec = run(fp32, tol, guess)
+            rec["rel_l1_vs_fp64_converged_%dsteps" % steps] = rel_l1_dev(d, ref_d)
+            rec["face_b_rel_l1_vs_fp64_converged"] = float((b - ref_b).abs().sum() / ref_b.abs().sum())
+            out[name] = rec
+    except Exception as exc:
+        out["error"] = str(exc)[:200]
+    return out
+
+
 def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32, 48, 64, 80, 96, 112, 128)):
     """`count` seeded independent problems of uneven cubic sizes (Euler and MHD, orders 2-4, FP32 bulk):
     one tuned batch replayed from a captured graph vs one context per problem launched in sequence.
@@ -270,6 +345,7 @@ def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32,
                                        flags_of(p)))
         d = [u.clone() for u in Us]
         db = [None if x is None else x.clone() for x in Bs]
+        torch.cuda.synchronize()                        # the copies (current stream) before `stream` reads them
 
         def seq_step():
             for k, h in enumerate(hs):
@@ -306,10 +382,11 @@ def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32,
                                    [flags_of(p) for p in probs])
         d = [u.clone() for u in Us]
         db = [None if x is None else x.clone() for x in Bs]
+        dtb = torch.zeros(len(probs), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()                        # the copies (current stream) before `stream` reads them
         t0 = time.perf_counter()
         _lib.ader_batch_tune(b, d, db, stream)
         tune_s = time.perf_counter() - t0
-        dtb = torch.zeros(len(probs), dtype=torch.float64, device="cuda")
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 _lib.ader_batch_advance(b, d, db, 0.4, dtb, stream)
@@ -355,10 +432,12 @@ def blast_evaluation(ader, torch, P, stream, n=256, steps=3):
             if guess is not None:
                 s.set_guess(guess)
             d = U0.clone()
+            torch.cuda.synchronize()                    # the copy (current stream) before `stream` reads it
             s.step(d, dt, stream)                       # warm-up step, discarded counts
             torch.cuda.synchronize()
             s.predictor_stats(stream)
             d = U0.clone()
+            torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(stream):
                 e0.record(stream)
@@ -477,6 +556,7 @@ def run_config(ader, torch, n, order, form, solver, fp32, steps, warmup, stream,
         state = torch.from_numpy(inputs.sod_planar(n)).to("cuda")
     d = state.clone()
     dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()                            # the copy (current stream) before `stream` reads it
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             s.max_dt(d, 0.4, dt, stream)
@@ -615,6 +695,7 @@ def gpu_arm(args):
                 variants[name] = {"error": str(exc)[:200]}
         variants.update(learned_variants(ader, torch, n, U0, stream))
         variants.update(mhd_variants(ader, torch, stream))
+        variants["learned_guess_mhd_ot_128"] = mhd_learned_evaluation(ader, torch, stream)
         variants["batched_64_problems_fp32"] = batched_variant(ader, torch, stream)
         variants["batched_512_small_problems_fp32"] = batched_variant(ader, torch, stream, count=512,
                                                                       sizes=(16, 24, 32))
@@ -622,6 +703,7 @@ def gpu_arm(args):
         srk = ader.Solver((n, n, n), order=3, form="nodal", solver="hll")
         drk = U0.clone()
         dtv = 1e-4
+        torch.cuda.synchronize()                        # the copy (current stream) before `stream` reads it
         with torch.cuda.stream(stream):
             srk.rk_step(drk, dtv, stream)
             torch.cuda.synchronize()

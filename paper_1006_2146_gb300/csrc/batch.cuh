@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(256) kb_predict_faces(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) { zone_predict_faces<ORDER, FORM, NV, R>(it.a, it.U, z); });
 }
 
-// U += dt L(U) in place, dt from the problem's dt_dev
+// U += dt L(U) in place, dt from the problem's dt_dev (fused fluxes: the FP64 accumulation bounds the
+// FP32-bulk update, not the Riemann solves)
 template <int SOLVER, int NV, class R>
 __global__ void __launch_bounds__(256) kb_flux_update(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) {

@@ -28,12 +28,8 @@ int batch_phase(int ph, const BatchGroupDev& g, int form, int solver, int thread
                                    : (const void*)kb_predict_faces<ORDER, FORM_MODAL, NV, R>;
             break;
         case PH_UPDATE:
-            if constexpr (NV == 8)
-                k = solver == SOLVER_LINEARIZED ? (const void*)kb_flux_update<SOLVER_LINEARIZED, 8, R>
-                                                : (const void*)kb_flux_update<SOLVER_HLL, 8, R>;
-            else
-                k = solver == SOLVER_LINEARIZED ? (const void*)kb_flux_update<SOLVER_LINEARIZED, 5, R>
-                                                : (const void*)kb_flux_update<SOLVER_HLL, 5, R>;
+            k = solver == SOLVER_LINEARIZED ? (const void*)kb_flux_update<SOLVER_LINEARIZED, NV, R>
+                                            : (const void*)kb_flux_update<SOLVER_HLL, NV, R>;
             break;
         case PH_EMF:
             if constexpr (NV == 8) k = (const void*)kb_emf<R>;

@@ -211,14 +211,45 @@ struct Grid {
     long long n;      // nx*ny*nz
 };
 
+// i modulo n in [0, n).  Every caller displaces an in-range coordinate by a
+// few zones, so two comparisons decide it; the remainder is the fallback for
+// displacements beyond one period (grids thinner than the stencil).
 ADER_DEV int wrap(int i, int n) {
+    if (i >= 0 && i < n) return i;
+    if (i < 0 && i >= -n) return i + n;
+    if (i >= n && i < 2 * n) return i - n;
     i %= n;
     return i < 0 ? i + n : i;
+}
+
+// (i, j, k) of the linear zone index z (x fastest).  Grids of up to 2^32 zones
+// take 32-bit divisions, which cost a fraction of the 64-bit ones.
+ADER_DEV void zone_ijk(const Grid& g, long long z, int& i, int& j, int& k) {
+    if (g.n <= 0xffffffffLL) {
+        const unsigned u = (unsigned)z, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+        const unsigned t = u / nx;
+        i = (int)(u - t * nx);
+        const unsigned q = t / ny;
+        j = (int)(t - q * ny);
+        k = (int)q;
+    } else {
+        i = (int)(z % g.nx);
+        const long long t = z / g.nx;
+        j = (int)(t % g.ny);
+        k = (int)(t / g.ny);
+    }
 }
 
 // linear index of the zone displaced by (di, dj, dk) from (i, j, k), periodic
 ADER_DEV long long nbr(const Grid& g, int i, int j, int k, int di, int dj, int dk) {
     return ((long long)wrap(k + dk, g.nz) * g.ny + wrap(j + dj, g.ny)) * g.nx + wrap(i + di, g.nx);
+}
+
+// linear index of the zone o zones from zone z = (i, j, k) along direction d, periodic
+ADER_DEV long long nbr_along(const Grid& g, long long z, int i, int j, int k, int d, int o) {
+    if (d == 0) return z + (wrap(i + o, g.nx) - i);
+    if (d == 1) return z + (long long)(wrap(j + o, g.ny) - j) * g.nx;
+    return z + (long long)(wrap(k + o, g.nz) - k) * ((long long)g.nx * g.ny);
 }
 
 ADER_DEV void raise_flag(unsigned* flag, unsigned bit) {

@@ -5,8 +5,8 @@
 // a small periodic grid.  Counted: add/sub, mul, div, sqrt (one FLOP each;
 // an FMA is its mul + add, i.e. two).  min/max/abs/compare are counted
 // separately and not included in the FLOP total.  The FP64 accumulation of
-// the flux differences in the update kernel (3 per variable per direction)
-// is added explicitly.
+// the stored face-flux differences in the update kernel (3 per variable per
+// direction, then base + c acc) is added explicitly.
 //
 // Build and run (host tool; the device side of the headers needs sm_103a):
 //   nvcc -O0 -Xcompiler -O0 -std=c++17 --expt-relaxed-constexpr -gencode arch=compute_103a,code=sm_103a \
@@ -111,13 +111,22 @@ int main() {
         std::vector<double> out(5 * N);
         for (int sol = 0; sol < 2; ++sol) {
             reset();
+            // FP64: each face solved once, then the update from the stored fluxes
+            for (long long z = 0; z < N; ++z) {
+                if (sol == 0) zone_face_fluxes<0, 5, Cnt>(a, z);
+                else zone_face_fluxes<1, 5, Cnt>(a, z);
+            }
+            for (long long z = 0; z < N; ++z) zone_flux_update_stored<Cnt>(a, out.data(), U.data(), 0.01, 0, z);
+            // FP64 accumulation: per direction and variable one subtract, one multiply, one subtract; then base + c*acc
+            const double acc = 3 * 5 * 3 + 5 * 2;
+            std::printf(", \"riemann_update_%s\": %.1f", sol ? "linearized" : "hll", (double)flops() / N + acc);
+            // FP32 bulk: each zone solves both faces of each direction (one fused pass)
+            reset();
             for (long long z = 0; z < N; ++z) {
                 if (sol == 0) zone_flux_update<0, 5, Cnt>(a, out.data(), U.data(), 0.01, 0, z);
                 else zone_flux_update<1, 5, Cnt>(a, out.data(), U.data(), 0.01, 0, z);
             }
-            // FP64 accumulation: per direction and variable one subtract, one multiply, one subtract; then base + c*acc
-            const double acc = 3 * 5 * 3 + 5 * 2;
-            std::printf(", \"riemann_update_%s\": %.1f", sol ? "linearized" : "hll", (double)flops() / N + acc);
+            std::printf(", \"riemann_update_fused_%s\": %.1f", sol ? "linearized" : "hll", (double)flops() / N + acc);
         }
         std::printf("}%s\n", order < 4 ? "," : "");
     }

@@ -29,9 +29,8 @@ __global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict
         const S vx = mx * ir, vy = my * ir, vz = mz * ir;
         S v;
         if (Bf) {
-            const int i = (int)(z % g.nx);
-            const long long t = z / g.nx;
-            const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+            int i, j, k;
+            zone_ijk(g, z, i, j, k);
             Vec<8, S> u;
             u[0] = rho; u[1] = mx; u[2] = my; u[3] = mz; u[4] = E;
             u[5] = S(0.5 * (Bf[z] + Bf[nbr(g, i, j, k, 1, 0, 0)]));
@@ -138,9 +137,8 @@ __global__ void __launch_bounds__(256) k_diag_mhd_partial(Grid g, const double* 
     for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < N; z += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int v = 0; v < 5; ++v) s[v] += U[v * N + z];
-        const int i = (int)(z % g.nx);
-        const long long t = z / g.nx;
-        const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+        int i, j, k;
+        zone_ijk(g, z, i, j, k);
         const double bx = Bf[z], by = Bf[N + z], bz = Bf[2 * N + z];
         s[5] += bx;
         s[6] += by;
@@ -232,15 +230,28 @@ int launch_flux_update(const StepArgs& a, double* out, const double* base, doubl
     const int T = 128;
     const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
     const int dd = use_dt_dev ? 1 : 0;
-    if (a.mhd && a.solver == SOLVER_HLL)
-        k_flux_update<SOLVER_HLL, 8, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
-    else if (a.mhd)
-        k_flux_update<SOLVER_LINEARIZED, 8, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
-    else if (a.solver == SOLVER_HLL)
-        k_flux_update<SOLVER_HLL, 5, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
-    else
-        k_flux_update<SOLVER_LINEARIZED, 5, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
-    return 1;
+    if constexpr (sizeof(R) == 4) {           // fused: the FP64 accumulation bounds it, not the solves
+        if (a.mhd && a.solver == SOLVER_HLL)
+            k_flux_update<SOLVER_HLL, 8, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+        else if (a.mhd)
+            k_flux_update<SOLVER_LINEARIZED, 8, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+        else if (a.solver == SOLVER_HLL)
+            k_flux_update<SOLVER_HLL, 5, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+        else
+            k_flux_update<SOLVER_LINEARIZED, 5, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+        return 1;
+    } else {                                   // each face solved once, then the update
+        if (a.mhd && a.solver == SOLVER_HLL)
+            k_face_fluxes<SOLVER_HLL, 8, R><<<blocks, T, 0, st>>>(a);
+        else if (a.mhd)
+            k_face_fluxes<SOLVER_LINEARIZED, 8, R><<<blocks, T, 0, st>>>(a);
+        else if (a.solver == SOLVER_HLL)
+            k_face_fluxes<SOLVER_HLL, 5, R><<<blocks, T, 0, st>>>(a);
+        else
+            k_face_fluxes<SOLVER_LINEARIZED, 5, R><<<blocks, T, 0, st>>>(a);
+        k_flux_update_stored<R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+        return 2;
+    }
 }
 
 template <class R>

@@ -166,32 +166,38 @@ ADER_DEV FaceSide<NV, R> load_side(const StepArgs& a, int side, long long z) {
     return s;
 }
 
-// F(i+1/2) - F(i-1/2) in direction D, accumulated in FP64 for the five
-// conserved hydrodynamic variables.  The same function with the same operands
-// computes a face's flux for both of its zones, so the two values are
-// identical and Eq. 6 telescopes exactly.
+// Eq. 6 for zone z: out = base + c sum_D (F(i_D - 1/2) - F(i_D + 1/2)) / dx_D,
+// accumulated in FP64 for the five hydrodynamic variables.  Two ways to the
+// same fluxes:
+//  * fused (zone_flux_update): each zone solves the two faces of each
+//    direction itself -- every face twice over the grid, in one pass.  The
+//    same function with the same operands gives both zones of a face the same
+//    value, so Eq. 6 telescopes exactly.  Used by the FP32-bulk kernels, whose
+//    cost there is the FP64 accumulation, not the Riemann solves.
+//  * stored (zone_face_fluxes, then zone_flux_update_stored): every face is
+//    solved once, by the zone below it, into the WENO scratch S1 (dead once
+//    the face data exist; at least 15 values per zone at every order), and
+//    the update takes differences of stored values.  Used by FP64, where the
+//    solves are FP64 work on the critical path.
+template <int SOLVER, int D, int NV, class R>
+ADER_DEV Vec<NV, R> upper_face_flux(const StepArgs& a, long long z, int i, int j, int k, R gamma, R gm1) {
+    const long long zp = nbr_along(a.grid, z, i, j, k, D, 1);
+    return riemann<SOLVER, D>(load_side<NV, R>(a, 2 * D, z), load_side<NV, R>(a, 2 * D + 1, zp), gamma, gm1);
+}
+
 template <int SOLVER, int D, int NV, class R>
 ADER_DEV void flux_difference(const StepArgs& a, long long z, int i, int j, int k, R gamma, R gm1, double* acc) {
-    const long long zp = nbr(a.grid, i, j, k, D == 0, D == 1, D == 2);
-    const long long zm = nbr(a.grid, i, j, k, -(D == 0), -(D == 1), -(D == 2));
-    const Vec<NV, R> Fp = riemann<SOLVER, D>(load_side<NV, R>(a, 2 * D, z), load_side<NV, R>(a, 2 * D + 1, zp), gamma, gm1);
-    const Vec<NV, R> Fm = riemann<SOLVER, D>(load_side<NV, R>(a, 2 * D, zm), load_side<NV, R>(a, 2 * D + 1, z), gamma, gm1);
+    const long long zm = nbr_along(a.grid, z, i, j, k, D, -1);
+    const Vec<NV, R> Fp = upper_face_flux<SOLVER, D, NV, R>(a, z, i, j, k, gamma, gm1);
+    const Vec<NV, R> Fm = riemann<SOLVER, D>(load_side<NV, R>(a, 2 * D, zm), load_side<NV, R>(a, 2 * D + 1, z),
+                                             gamma, gm1);
     const double inv = a.idx[D];
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] -= ((double)Fp[v] - (double)Fm[v]) * inv;
 }
 
-template <int SOLVER, int NV, class R>
-ADER_DEV void zone_flux_update(const StepArgs& a, double* out, const double* base, double c_host, int use_dt_dev,
-                               long long z) {
-    const int i = (int)(z % a.grid.nx);
-    const long long t = z / a.grid.nx;
-    const int j = (int)(t % a.grid.ny), k = (int)(t / a.grid.ny);
-    const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
-    double acc[5] = {0, 0, 0, 0, 0};
-    flux_difference<SOLVER, 0, NV, R>(a, z, i, j, k, gamma, gm1, acc);
-    flux_difference<SOLVER, 1, NV, R>(a, z, i, j, k, gamma, gm1, acc);
-    flux_difference<SOLVER, 2, NV, R>(a, z, i, j, k, gamma, gm1, acc);
+ADER_DEV void store_update(const StepArgs& a, double* out, const double* base, double c_host, int use_dt_dev,
+                           const double* acc, long long z) {
     const double c = use_dt_dev ? c_host * (*a.dt_dev) : c_host;
     const long long N = a.grid.n;
     bool bad = false;
@@ -205,10 +211,73 @@ ADER_DEV void zone_flux_update(const StepArgs& a, double* out, const double* bas
 }
 
 template <int SOLVER, int NV, class R>
+ADER_DEV void zone_flux_update(const StepArgs& a, double* out, const double* base, double c_host, int use_dt_dev,
+                               long long z) {
+    int i, j, k;
+    zone_ijk(a.grid, z, i, j, k);
+    const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
+    double acc[5] = {0, 0, 0, 0, 0};
+    flux_difference<SOLVER, 0, NV, R>(a, z, i, j, k, gamma, gm1, acc);
+    flux_difference<SOLVER, 1, NV, R>(a, z, i, j, k, gamma, gm1, acc);
+    flux_difference<SOLVER, 2, NV, R>(a, z, i, j, k, gamma, gm1, acc);
+    store_update(a, out, base, c_host, use_dt_dev, acc, z);
+}
+
+template <int SOLVER, int NV, class R>
 __global__ void __launch_bounds__(128) k_flux_update(StepArgs a, double* out, const double* base, double c_host,
                                                      int use_dt_dev) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z < a.grid.n) zone_flux_update<SOLVER, NV, R>(a, out, base, c_host, use_dt_dev, z);
+}
+
+template <int SOLVER, int NV, class R>
+ADER_DEV void zone_face_fluxes(const StepArgs& a, long long z) {
+    int i, j, k;
+    zone_ijk(a.grid, z, i, j, k);
+    const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
+    R* F = (R*)a.S1;
+    const long long N = a.grid.n;
+    const Vec<NV, R> f0 = upper_face_flux<SOLVER, 0, NV, R>(a, z, i, j, k, gamma, gm1);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[(0 * 5 + v) * N + z] = f0[v];
+    const Vec<NV, R> f1 = upper_face_flux<SOLVER, 1, NV, R>(a, z, i, j, k, gamma, gm1);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[(1 * 5 + v) * N + z] = f1[v];
+    const Vec<NV, R> f2 = upper_face_flux<SOLVER, 2, NV, R>(a, z, i, j, k, gamma, gm1);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[(2 * 5 + v) * N + z] = f2[v];
+}
+
+template <int SOLVER, int NV, class R>
+__global__ void __launch_bounds__(128) k_face_fluxes(StepArgs a) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < a.grid.n) zone_face_fluxes<SOLVER, NV, R>(a, z);
+}
+
+template <class R>
+ADER_DEV void zone_flux_update_stored(const StepArgs& a, double* out, const double* base, double c_host,
+                                      int use_dt_dev, long long z) {
+    int i, j, k;
+    zone_ijk(a.grid, z, i, j, k);
+    const R* F = (const R*)a.S1;
+    const long long N = a.grid.n;
+    double acc[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int D = 0; D < 3; ++D) {
+        const long long zm = nbr_along(a.grid, z, i, j, k, D, -1);
+        const double inv = a.idx[D];
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+            acc[v] -= ((double)F[(D * 5 + v) * N + z] - (double)F[(D * 5 + v) * N + zm]) * inv;
+    }
+    store_update(a, out, base, c_host, use_dt_dev, acc, z);
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) k_flux_update_stored(StepArgs a, double* out, const double* base,
+                                                            double c_host, int use_dt_dev) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < a.grid.n) zone_flux_update_stored<R>(a, out, base, c_host, use_dt_dev, z);
 }
 
 // ------------------------------------------------------------------ MHD: edge EMFs (Sec. II.3, Eq. 7)
@@ -276,9 +345,8 @@ ADER_DEV R edge_flux(const StepArgs& a, long long zl, long long zr, int e, R gam
 template <class R>
 ADER_DEV void zone_emf(const StepArgs& a, long long z) {
     const Grid& g = a.grid;
-    const int i = (int)(z % g.nx);
-    const long long t = z / g.nx;
-    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+    int i, j, k;
+    zone_ijk(g, z, i, j, k);
     const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
     const long long zx = nbr(g, i, j, k, 1, 0, 0), zy = nbr(g, i, j, k, 0, 1, 0), zz = nbr(g, i, j, k, 0, 0, 1);
     const long long zxy = nbr(g, i, j, k, 1, 1, 0), zxz = nbr(g, i, j, k, 1, 0, 1), zyz = nbr(g, i, j, k, 0, 1, 1);
@@ -306,9 +374,8 @@ __global__ void __launch_bounds__(128) k_emf(StepArgs a) {
 template <class R>
 ADER_DEV void zone_ct(const StepArgs& a, double* Bf, double c_host, int use_dt_dev, long long z) {
     const Grid& g = a.grid;
-    const int i = (int)(z % g.nx);
-    const long long t = z / g.nx;
-    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+    int i, j, k;
+    zone_ijk(g, z, i, j, k);
     const R* E = (const R*)a.E;
     const long long N = g.n;
     auto Ex = [&](int di, int dj, int dk) { return (double)E[nbr(g, i, j, k, di, dj, dk)]; };

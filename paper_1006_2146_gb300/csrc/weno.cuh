@@ -120,19 +120,13 @@ ADER_DEV R slope(const R* a) {
 }
 
 
-ADER_DEV void zone_ijk(const Grid& g, long long z, int& i, int& j, int& k) {
-    i = (int)(z % g.nx);
-    long long t = z / g.nx;
-    j = (int)(t % g.ny);
-    k = (int)(t / g.ny);
-}
 
 // slope along direction d of the field F at zone (i, j, k)
 template <class R>
 ADER_DEV R slope_of(const Grid& g, const R* __restrict__ F, int i, int j, int k, int d) {
     R a[5];
 #pragma unroll
-    for (int o = -2; o <= 2; ++o) a[o + 2] = F[nbr(g, i, j, k, d == 0 ? o : 0, d == 1 ? o : 0, d == 2 ? o : 0)];
+    for (int o = -2; o <= 2; ++o) a[o + 2] = F[nbr_along(g, (long long)(k * g.ny + j) * g.nx + i, i, j, k, d, o)];
     return slope(a);
 }
 
@@ -159,7 +153,7 @@ ADER_DEV void zone_weno1d(const Grid& g, const T* __restrict__ U, const R* __res
 #pragma unroll
             for (int o = -RAD; o <= RAD; ++o)
             {
-                const long long zz = nbr(g, i, j, k, d == 0 ? o : 0, d == 1 ? o : 0, d == 2 ? o : 0);
+                const long long zz = nbr_along(g, z, i, j, k, d, o);
                 a[o + RAD] = v < 5 ? R(Uv[zz]) : Bv[zz];
             }
             if (ORDER == 4) {
@@ -233,7 +227,7 @@ ADER_DEV void zone_face_b(const Grid& g, const double* __restrict__ Bf, R* __res
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         const double* B = Bf + (long long)e * g.n;
-        auto at = [&](int o) { return R(B[nbr(g, i, j, k, e == 0 ? o : 0, e == 1 ? o : 0, e == 2 ? o : 0)]); };
+        auto at = [&](int o) { return R(B[nbr_along(g, z, i, j, k, e, o)]); };
         const R Bm = at(0), Bp = at(1);                   // faces i - 1/2 and i + 1/2
         R m[4];
         if (ORDER == 2) {
