@@ -126,7 +126,10 @@ template <class R>
 ADER_DEV R slope_of(const Grid& g, const R* __restrict__ F, int i, int j, int k, int d) {
     R a[5];
 #pragma unroll
-    for (int o = -2; o <= 2; ++o) a[o + 2] = F[nbr_along(g, (long long)(k * g.ny + j) * g.nx + i, i, j, k, d, o)];
+    for (int o = -2; o <= 2; ++o) {
+        const long long z = ((long long)k * g.ny + j) * g.nx + i;
+        a[o + 2] = F[o == 0 ? z : nbr_along(g, z, i, j, k, d, o)];
+    }
     return slope(a);
 }
 
@@ -143,18 +146,26 @@ ADER_DEV void zone_weno1d(const Grid& g, const T* __restrict__ U, const R* __res
     int i, j, k;
     zone_ijk(g, z, i, j, k);
     constexpr int RAD = ORDER == 4 ? 3 : 2;
+    // the stencil's neighbour offsets, once for all variables (offset 0 is the zone itself)
+    long long off[3][2 * RAD + 1];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int o = -RAD; o <= RAD; ++o) off[d][o + RAD] = o == 0 ? 0 : nbr_along(g, z, i, j, k, d, o) - z;
     for (int v = 0; v < NV; ++v) {
-        const T* Uv = v < 5 ? U + (long long)v * g.n : nullptr;
-        const R* Bv = v >= 5 ? ZB + (long long)(v - 5) * g.n : nullptr;
+        const T* Uv = v < 5 ? U + (long long)v * g.n + z : nullptr;
+        const R* Bv = v >= 5 ? ZB + (long long)(v - 5) * g.n + z : nullptr;
+        const R centre = v < 5 ? R(Uv[0]) : Bv[0];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             if (v >= 5 && d == v - 5) continue;
             R a[2 * RAD + 1];
 #pragma unroll
-            for (int o = -RAD; o <= RAD; ++o)
-            {
-                const long long zz = nbr_along(g, z, i, j, k, d, o);
-                a[o + RAD] = v < 5 ? R(Uv[zz]) : Bv[zz];
+            for (int o = -RAD; o <= RAD; ++o) {
+                if (o == 0)
+                    a[RAD] = centre;
+                else
+                    a[o + RAD] = v < 5 ? R(Uv[off[d][o + RAD]]) : Bv[off[d][o + RAD]];
             }
             if (ORDER == 4) {
                 R b, c, e;
