@@ -93,9 +93,12 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_cross1_tiled(Grid g, const floa
     const int i = (int)(blockIdx.x % tiles_x) * CT_X + tx, j = (int)(blockIdx.x / tiles_x) * CT_Y + ty;
     const int k0 = (int)blockIdx.y * CT_Z, k1 = min(k0 + CT_Z, g.nz);
     const long long N = g.n;
-    auto at = [&](int ii, int jj, int kk) -> long long {
-        return ((long long)wrap(kk, g.nz) * g.ny + wrap(jj, g.ny)) * g.nx + wrap(ii, g.nx);
-    };
+    // periodic offsets, once per thread: the column (i, j), its y and x halos, and the z planes
+    const long long nxy = (long long)g.nx * g.ny;
+    const long long xy = (long long)j * g.nx + i;
+    const long long xy_jm = (long long)wrap(j - 2, g.ny) * g.nx + i, xy_jp = (long long)wrap(j + 2, g.ny) * g.nx + i;
+    const long long xy_im = (long long)j * g.nx + wrap(i - 2, g.nx), xy_ip = (long long)j * g.nx + wrap(i + 2, g.nx);
+    auto plane = [&](int kk) -> long long { return (long long)wrap(kk, g.nz) * nxy; };
     for (int v = 0; v < NV; ++v) {
         const float* w2 = S1 + ((0 * 3 + 0) * NV + v) * N;
         const float* w3 = S1 + ((0 * 3 + 1) * NV + v) * N;
@@ -103,8 +106,9 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_cross1_tiled(Grid g, const floa
         float c2[5], c3[5];                        // the column at z - 2 .. z + 2
 #pragma unroll
         for (int o = -2; o <= 1; ++o) {
-            c2[o + 3] = w2[at(i, j, k0 + o)];
-            c3[o + 3] = w3[at(i, j, k0 + o)];
+            const long long p = plane(k0 + o) + xy;
+            c2[o + 3] = w2[p];
+            c3[o + 3] = w3[p];
         }
         for (int k = k0; k < k1; ++k) {
 #pragma unroll
@@ -112,27 +116,29 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_cross1_tiled(Grid g, const floa
                 c2[q] = c2[q + 1];
                 c3[q] = c3[q + 1];
             }
-            c2[4] = w2[at(i, j, k + 2)];
-            c3[4] = w3[at(i, j, k + 2)];
-            // the plane k with its halos
+            const long long p2 = plane(k + 2) + xy;
+            c2[4] = w2[p2];
+            c3[4] = w3[p2];
+            // the plane k (k < nz) with its halos
+            const long long pk = (long long)k * nxy;
             s2[ty + 2][tx] = c2[2];
             s3[ty][tx + 2] = c3[2];
-            s4[ty + 2][tx + 2] = w4[at(i, j, k)];
+            s4[ty + 2][tx + 2] = w4[pk + xy];
             if (ty < 2) {
-                s2[ty][tx] = w2[at(i, j - 2, k)];
-                s4[ty][tx + 2] = w4[at(i, j - 2, k)];
+                s2[ty][tx] = w2[pk + xy_jm];
+                s4[ty][tx + 2] = w4[pk + xy_jm];
             }
             if (ty >= CT_Y - 2) {
-                s2[ty + 4][tx] = w2[at(i, j + 2, k)];
-                s4[ty + 4][tx + 2] = w4[at(i, j + 2, k)];
+                s2[ty + 4][tx] = w2[pk + xy_jp];
+                s4[ty + 4][tx + 2] = w4[pk + xy_jp];
             }
             if (tx < 2) {
-                s3[ty][tx] = w3[at(i - 2, j, k)];
-                s4[ty + 2][tx] = w4[at(i - 2, j, k)];
+                s3[ty][tx] = w3[pk + xy_im];
+                s4[ty + 2][tx] = w4[pk + xy_im];
             }
             if (tx >= CT_X - 2) {
-                s3[ty][tx + 4] = w3[at(i + 2, j, k)];
-                s4[ty + 2][tx + 4] = w4[at(i + 2, j, k)];
+                s3[ty][tx + 4] = w3[pk + xy_ip];
+                s4[ty + 2][tx + 4] = w4[pk + xy_ip];
             }
             __syncthreads();
             float a[5];
@@ -149,7 +155,7 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_cross1_tiled(Grid g, const floa
             for (int o = 0; o < 5; ++o) a[o] = s4[ty + 2][tx + o];
             const float sx4 = slope(a);
             const float sz3 = slope(c3), sz2 = slope(c2);
-            const long long z = ((long long)k * g.ny + j) * g.nx + i;
+            const long long z = pk + xy;
             S2[(0 * NV + v) * N + z] = 0.5f * (sy2 + sx3);
             S2[(1 * NV + v) * N + z] = 0.5f * (sz3 + sy4);
             S2[(2 * NV + v) * N + z] = 0.5f * (sz2 + sx4);

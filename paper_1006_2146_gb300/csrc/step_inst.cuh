@@ -25,6 +25,11 @@ namespace ader {
                                       R* ef) {                                                                       \
             o##O::face_mhd<D>(p, gm1, ub, avg, Fa, eu, ef);                                                           \
         }                                                                                                            \
+        static constexpr bool HAS_FACE_PAIR = o##O::HAS_FACE_PAIR;                                                   \
+        template <int D, int NV, class R>                                                                            \
+        static ADER_DEV void face_pair(const Vec<NV, R>* p, R gm1, Vec<NV, R>* ub, Vec<NV, R>* avg, Vec<NV, R>* Fa) {  \
+            o##O::face_pair<D>(p, gm1, ub, avg, Fa);                                                                  \
+        }                                                                                                            \
         template <int D, class R>                                                                                    \
         static ADER_DEV void edge_states(const Vec<8, R>* p, const Vec<8, R>& ub, const Vec<8, R>& avg, Vec<8, R>* e) { \
             o##O::edge_states<D>(p, ub, avg, e);                                                                      \

@@ -48,6 +48,25 @@ ADER_DEV void load_modes(const StepArgs& a, const double* __restrict__ U, long l
     }
 }
 
+// the Euler part of one face side: the barycentre state (replaced by the zone
+// average for the wave speeds when it is not physical), <u> and <F>
+template <int D, int S, int NV, class R>
+ADER_DEV void write_side(const StepArgs& a, long long z, const Vec<NV, R>& mean, Vec<NV, R> ub, const Vec<NV, R>& avg,
+                         const Vec<NV, R>& Fa, R gm1) {
+    constexpr int NQ = side_values(NV);
+    const Prim<NV, R> q = primitives(ub, gm1);
+    if (!(ub[0] > R(0)) || !(q.p > R(0))) ub = mean;
+    constexpr int side = 2 * D + (S < 0 ? 1 : 0);
+    R* S3 = (R*)a.S3;
+    const long long N = a.grid.n;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        S3[(side * NQ + v) * N + z] = ub[v];
+        S3[(side * NQ + NV + v) * N + z] = avg[v];
+        S3[(side * NQ + 2 * NV + v) * N + z] = Fa[v];
+    }
+}
+
 template <int ORDER, int D, int S, int NV, class R>
 ADER_DEV void store_face(const StepArgs& a, long long z, const Vec<NV, R>* m, R gm1) {
     constexpr int L = ModeCount<ORDER>::L;
@@ -60,19 +79,11 @@ ADER_DEV void store_face(const StepArgs& a, long long z, const Vec<NV, R>* m, R 
         ZoneOps<ORDER>::template face_mhd<D>(p, gm1, ub, avg, Fa, eu, ef);
     else
         ZoneOps<ORDER>::template face<D>(p, gm1, ub, avg, Fa);
-    // a non-physical barycentre state is replaced by the zone average for the wave speeds
-    const Prim<NV, R> q = primitives(ub, gm1);
-    if (!(ub[0] > R(0)) || !(q.p > R(0))) ub = m[1];
-    constexpr int side = 2 * D + (S < 0 ? 1 : 0);
-    R* S3 = (R*)a.S3;
-    const long long N = a.grid.n;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        S3[(side * NQ + v) * N + z] = ub[v];
-        S3[(side * NQ + NV + v) * N + z] = avg[v];
-        S3[(side * NQ + 2 * NV + v) * N + z] = Fa[v];
-    }
+    write_side<D, S>(a, z, m[1], ub, avg, Fa, gm1);
     if constexpr (NV == 8) {
+        constexpr int side = 2 * D + (S < 0 ? 1 : 0);
+        R* S3 = (R*)a.S3;
+        const long long N = a.grid.n;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             S3[(side * NQ + 3 * NV + 2 * e) * N + z] = eu[e];
@@ -87,6 +98,23 @@ ADER_DEV void store_face(const StepArgs& a, long long z, const Vec<NV, R>* m, R 
 #pragma unroll
                 for (int v = 0; v < 8; ++v) X[(side * EDGE_STATE_VALUES + e * 8 + v) * N + z] = es[e][v];
         }
+    }
+}
+
+// both faces of direction D: the paired form where the order has one (Euler), else one face at a time
+template <int ORDER, int D, int NV, class R>
+ADER_DEV void store_faces(const StepArgs& a, long long z, const Vec<NV, R>* m, R gm1) {
+    if constexpr (NV == 5 && ZoneOps<ORDER>::HAS_FACE_PAIR) {
+        constexpr int L = ModeCount<ORDER>::L;
+        Vec<NV, R> p[L + 1];
+        to_face_frame<ORDER, D, +1>(m, p);
+        Vec<NV, R> ub[2], avg[2], Fa[2];
+        ZoneOps<ORDER>::template face_pair<D>(p, gm1, ub, avg, Fa);
+        write_side<D, +1>(a, z, m[1], ub[0], avg[0], Fa[0], gm1);
+        write_side<D, -1>(a, z, m[1], ub[1], avg[1], Fa[1], gm1);
+    } else {
+        store_face<ORDER, D, +1>(a, z, m, gm1);
+        store_face<ORDER, D, -1>(a, z, m, gm1);
     }
 }
 
@@ -137,12 +165,9 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
         if (a.tol > 0.0 && a.stats) record_iterations(a.stats, ctl);
         if (ctl.capped) raise_flag(a.flag, FLAG_NOT_CONVERGED);
     }
-    store_face<ORDER, 0, +1>(a, z, m, gm1);
-    store_face<ORDER, 0, -1>(a, z, m, gm1);
-    store_face<ORDER, 1, +1>(a, z, m, gm1);
-    store_face<ORDER, 1, -1>(a, z, m, gm1);
-    store_face<ORDER, 2, +1>(a, z, m, gm1);
-    store_face<ORDER, 2, -1>(a, z, m, gm1);
+    store_faces<ORDER, 0>(a, z, m, gm1);
+    store_faces<ORDER, 1>(a, z, m, gm1);
+    store_faces<ORDER, 2>(a, z, m, gm1);
 }
 
 // FP32 bulk asks for three 128-thread blocks per SM (at most 168 registers, a few hundred bytes of

@@ -213,6 +213,62 @@ ADER_DEV void face(const Vec<NV, R>* p, R gm1, Vec<NV, R>& ub, Vec<NV, R>& avg, 
           flux<D>(t10, gm1)) / 6.0;
 }
 
+// Both x-faces of one direction at once (Euler).  p is the zone's modes in
+// the frame of the upper face; the lower face's frame differs only in the
+// sign of the modes odd in the normal coordinate (2, 8, 10, 13), so each of
+// face()'s node states is E + O on the upper face and E - O on the lower one,
+// with E its part from the even modes and O from the odd ones.  E and O are
+// face()'s own linear combinations split by parity, each computed once; the
+// nodes are taken in an order that keeps few of them alive at a time.
+// Index 0 of ub, avg, Fa is the upper face (S = +1), index 1 the lower.
+constexpr bool HAS_FACE_PAIR = true;
+
+template <int D, int NV, class R>
+ADER_DEV void face_pair(const Vec<NV, R>* p, R gm1, Vec<NV, R>* ub, Vec<NV, R>* avg, Vec<NV, R>* Fa) {
+    const Vec<NV, R> t1e = p[1] + (2.0 * p[5] - p[6] - p[7]) / 12.0, t1o = 0.5 * p[2];
+    const Vec<NV, R> q1e = 0.5 * p[11] + 0.25 * p[12], q1o = 0.25 * p[13];
+    {
+        const Vec<NV, R> ube = t1e + q1e, ubo = t1o + q1o;
+        const Vec<NV, R> avge = ube + (p[6] + p[7] + p[12]) / 12.0;
+        ub[0] = ube + ubo;
+        ub[1] = ube - ubo;
+        avg[0] = avge + ubo;
+        avg[1] = avge - ubo;
+    }
+    Vec<NV, R> up = flux<D>(t1e + t1o, gm1), lo = flux<D>(t1e - t1o, gm1);       // node 1
+    {
+        const Vec<NV, R> e = t1e + p[11] + p[12], o = t1o + 0.5 * p[13];          // node 10
+        up += flux<D>(e + o, gm1);
+        lo += flux<D>(e - o, gm1);
+    }
+    const Vec<NV, R> t2e = t1e + 0.5 * (p[3] + p[4]) + 0.25 * (p[6] + p[7] + p[9]), t2o = t1o + 0.25 * (p[8] + p[10]);
+    const Vec<NV, R> t3e = t2e - p[3] - 0.5 * p[9], t3o = t2o - 0.5 * p[8];
+    const Vec<NV, R> t4e = t2e - p[4] - 0.5 * p[9], t4o = t2o - 0.5 * p[10];
+    {
+        const Vec<NV, R> e = 0.5 * (t2e + t4e) + q1e + 0.25 * (p[14] - p[7]), o = 0.5 * (t2o + t4o) + q1o;   // 6
+        up += flux<D>(e + o, gm1);
+        lo += flux<D>(e - o, gm1);
+    }
+    {
+        const Vec<NV, R> e = 0.5 * (t2e + t3e) + q1e + 0.25 * (p[15] - p[6]), o = 0.5 * (t2o + t3o) + q1o;   // 8
+        up += flux<D>(e + o, gm1);
+        lo += flux<D>(e - o, gm1);
+    }
+    const Vec<NV, R> t5e = t4e - p[3] + 0.5 * p[9], t5o = t4o - 0.5 * p[8];
+    {
+        const Vec<NV, R> e = 0.5 * (t4e + t5e) + q1e - 0.25 * (p[6] + p[15]), o = 0.5 * (t4o + t5o) + q1o;   // 9
+        up += flux<D>(e + o, gm1);
+        lo += flux<D>(e - o, gm1);
+    }
+    {
+        const Vec<NV, R> e = 0.5 * (t3e + t5e) + q1e - 0.25 * (p[7] + p[14]), o = 0.5 * (t3o + t5o) + q1o;   // 7
+        up += flux<D>(e + o, gm1);
+        lo += flux<D>(e - o, gm1);
+    }
+    Fa[0] = up / 6.0;
+    Fa[1] = lo / 6.0;
+}
+
 // MHD face: all ten facial nodes of Eq. D.6; edge averages by Eq. 63 (<u>)
 // and Eqs. D.9-D.10 (<F>) for the field component of each edge's EMF
 // (slots t1+, t1-, t2+, t2-; component 5 + t1 / 5 + t2).

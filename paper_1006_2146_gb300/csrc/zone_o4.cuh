@@ -482,5 +482,10 @@ ADER_DEV void edge_states(const Vec<8, R>* p, const Vec<8, R>& ub, const Vec<8, 
     e[3] = u2 - q2;
 }
 
+// No paired-face form at this order: the faces are evaluated one at a time.
+constexpr bool HAS_FACE_PAIR = false;
+template <int D, int NV, class R>
+ADER_DEV void face_pair(const Vec<NV, R>*, R, Vec<NV, R>*, Vec<NV, R>*, Vec<NV, R>*) {}
+
 }  // namespace o4
 }  // namespace ader
