@@ -1,7 +1,7 @@
 """ADER-CG local space-time predictor, modal (Sec. IV) and nodal (Apps. A-C).
 
-Both forms compute a Picard iteration on the reference element (Eq. 5, no
-source term):  du/dtau = -(df/dxi + dg/deta + dh/dzeta),  u(tau = 0) = w,
+Both forms compute a Picard iteration on the reference element (Eq. 5):
+du/dtau = -(df/dxi + dg/deta + dh/dzeta) + s,  u(tau = 0) = w,
 where f, g, h are the scaled fluxes f = dt F/dx etc. evaluated at the nodes
 of the current iterate and turned back into polynomials:
 
@@ -12,7 +12,9 @@ of the current iterate and turned back into polynomials:
   polynomial is their Lagrange interpolant (one node per mode).
 
 The new evolutionary modes follow by matching du/dtau with -div(flux) mode
-by mode (this is what Eqs. 30, 36, 45 and A.4, B.3, C.3 state for S = 0).
+by mode (this is what Eqs. 30, 36, 45 and A.4, B.3, C.3 state for S = 0);
+with a source s = dt S (``oracle.source``) they solve the Galerkin system
+whose test functions are the evolutionary basis functions.
 The iteration starts from zero evolutionary modes (the paper is silent) and
 runs M-1 times (Secs. IV.1-IV.3), or - in converged mode - per zone until the
 largest change of an evolutionary mode is below `tol` times (|w_1| + 1e-300),
@@ -78,13 +80,45 @@ def update_from_fluxes(Uhat, Fm, order):
     return new
 
 
-def predict(W, order, form, gamma, dt, dx, n_iter=None, tol=None, max_iter=50, guess=None):
+def source_modes(Uhat, order, form, dt, model):
+    """All L modes of the scaled source polynomial s (dt S at the nodes of the current iterate; modal
+    extraction rules or nodal interpolation, see ``oracle.source``)."""
+    from . import source
+    T = tables(order, form)
+    unodes = _apply(T.V, Uhat)                              # (n_nodes, nvar, ...)
+    s = dt * np.stack([source.evaluate(unodes[n], model) for n in range(unodes.shape[0])])
+    return source.modal_modes(order, s) if form == "modal" else _apply(T.Vinv, s)
+
+
+def update_with_source(Uhat, Fm, Sm, order, form):
+    """Evolutionary modes of du/dtau = -div(flux) + s in the Galerkin sense (Eqs. 30, 36, 45 and
+    A.4, B.3, C.3 with S): test functions are the evolutionary basis functions of the form."""
+    from . import source
+    D = tables(order, "modal").D
+    rhs = -(_apply(D[0], Fm[0]) + _apply(D[1], Fm[1]) + _apply(D[2], Fm[2])) + Sm
+    E = [k for k, m in enumerate(basis.MODES[order]) if m[3] >= 1]
+    new = Uhat.copy()
+    new[E] = source.evolve(order, form, rhs)
+    return new
+
+
+def _step(Uhat, order, form, gamma, scale, dt, model):
+    Fm = flux_modes(Uhat, order, form, gamma, scale)
+    if model is None:
+        return update_from_fluxes(Uhat, Fm, order)
+    return update_with_source(Uhat, Fm, source_modes(Uhat, order, form, dt, model), order, form)
+
+
+def predict(W, order, form, gamma, dt, dx, n_iter=None, tol=None, max_iter=50, guess=None, source=None):
     """Space-time modes u_hat (L, nvar, ...) from spatial modes W (LS, nvar, ...).
 
     dt/dx gives the reference-element scaling of Eq. 5.  Returns (Uhat, iterations)
     where iterations is an int (fixed count) or a per-zone integer array
     (converged mode).  `guess` optionally supplies initial evolutionary modes
-    (L - LS, nvar, ...).
+    (L - LS, nvar, ...).  `source` is a source model of ``oracle.source``; with
+    one, the result is (Uhat, iterations, Sdt) with Sdt (nvar, ...) the
+    space-time average of the source polynomial of the final iterate (dt times
+    the S-bar of Eq. 6).
     """
     LS, L = basis.LS[order], basis.L[order]
     Uhat = np.zeros((L,) + W.shape[1:])
@@ -95,19 +129,24 @@ def predict(W, order, form, gamma, dt, dx, n_iter=None, tol=None, max_iter=50, g
     if tol is None:
         n = order - 1 if n_iter is None else n_iter
         for _ in range(n):
-            Uhat = update_from_fluxes(Uhat, flux_modes(Uhat, order, form, gamma, scale), order)
-        return Uhat, n
-    grid = W.shape[2:]
-    done = np.zeros(grid, dtype=bool)
-    iters = np.zeros(grid, dtype=np.int64)
-    ref = np.abs(W[0]).max(axis=0) + 1e-300
-    for _ in range(max_iter):
-        new = update_from_fluxes(Uhat, flux_modes(Uhat, order, form, gamma, scale), order)
-        change = np.abs(new[LS:] - Uhat[LS:]).max(axis=(0, 1)) / ref
-        act = ~done
-        Uhat[:, :, act] = new[:, :, act]
-        iters[act] += 1
-        done |= change < tol
-        if done.all():
-            break
-    return Uhat, iters
+            Uhat = _step(Uhat, order, form, gamma, scale, dt, source)
+        iters = n
+    else:
+        grid = W.shape[2:]
+        done = np.zeros(grid, dtype=bool)
+        iters = np.zeros(grid, dtype=np.int64)
+        ref = np.abs(W[0]).max(axis=0) + 1e-300
+        for _ in range(max_iter):
+            new = _step(Uhat, order, form, gamma, scale, dt, source)
+            change = np.abs(new[LS:] - Uhat[LS:]).max(axis=(0, 1)) / ref
+            act = ~done
+            Uhat[:, :, act] = new[:, :, act]
+            iters[act] += 1
+            done |= change < tol
+            if done.all():
+                break
+    if source is None:
+        return Uhat, iters
+    from . import source as src
+    Sdt = _apply(src.average_weights(order)[None, :], source_modes(Uhat, order, form, dt, source))[0]
+    return Uhat, iters, Sdt

@@ -50,15 +50,21 @@ def zone_state(U, Bface, order):
 
 
 def ader_step(U, dx, dt, order, form="nodal", solver="hll", gamma=1.4, Bface=None,
-              n_iter=None, tol=None, guess=None, return_iters=False):
-    """Ubar^{n+1} by Eq. 6 (and B_face^{n+1} by Eq. 8 for MHD) after one ADER step of size dt."""
+              n_iter=None, tol=None, guess=None, return_iters=False, source=None):
+    """Ubar^{n+1} by Eq. 6 (and B_face^{n+1} by Eq. 8 for MHD) after one ADER step of size dt.
+
+    `source`: a non-stiff source model of ``oracle.source`` (None: S = 0); it enters the predictor and
+    the update through S-bar, the space-time average of the final iterate's source polynomial."""
     mhd = Bface is not None
     Uz, W = zone_state(U, Bface, order)
-    Uhat, iters = predictor.predict(W, order, form, gamma, dt, dx, n_iter=n_iter, tol=tol, guess=guess)
+    res = predictor.predict(W, order, form, gamma, dt, dx, n_iter=n_iter, tol=tol, guess=guess, source=source)
+    Uhat, iters = res[0], res[1]
     F, edge_data = _face_fluxes(Uhat, order, gamma, solver, Uz, mhd)
     Un = U.copy()
     for d in range(3):
         Un = Un - (dt / dx[d]) * (F[d][:5] - weno.shift(F[d][:5], d, -1))
+    if source is not None:
+        Un = Un + res[2][:5]
     out = Un
     if mhd:
         Bn = ct_update(Bface, F, edge_data, Uz, order, gamma, solver, dt, dx)
