@@ -541,13 +541,16 @@ def learned_variants(ader, torch, n, U0, stream, steps=3):
 
 
 def run_config(ader, torch, n, order, form, solver, fp32, steps, warmup, stream, profile=False, state=None,
-               tol=None, guess=None):
+               tol=None, guess=None, source=None):
     """Times `steps` steps of max_dt + step_devdt; returns (seconds, profile dict, solver, device state).
 
-    tol: converged predictor (iterate to tol, at most 50 times); guess: learned-guess parameters (device).
+    tol: converged predictor (iterate to tol, at most 50 times); guess: learned-guess parameters (device);
+    source: (kind, params) of Solver.set_source.
     """
     from paper_1006_2146_gb300 import inputs
     s = ader.Solver((n, n, n), order=order, form=form, solver=solver, fp32=fp32)
+    if source is not None:
+        s.set_source(*source)
     if tol is not None:
         s.set_predictor(tol, 50)
     if guess is not None:
@@ -684,10 +687,15 @@ def gpu_arm(args):
             vs.append(("fp32_modal_hll_o%d" % order, order, "modal", "hll", True))
         vs += [("fp64_nodal_linearized_o3", 3, "nodal", "linearized", False),
                ("fp32_nodal_hll_o3", 3, "nodal", "hll", True)]
-        for name, order, form, solver, fp32 in vs:
+        vs = [v + (None,) for v in vs]
+        # the same step with a non-stiff source (uniform gravity): its cost in the predictor
+        grav = ("gravity", (0.0, 0.0, -1.0))
+        vs += [("fp64_nodal_hll_o3_gravity", 3, "nodal", "hll", False, grav),
+               ("fp32_nodal_hll_o3_gravity", 3, "nodal", "hll", True, grav)]
+        for name, order, form, solver, fp32, src in vs:
             try:
                 vsecs, vprof, vs_, _, _ = run_config(ader, torch, n, order, form, solver, fp32, 3, 1, stream,
-                                                     profile=True, state=U0)
+                                                     profile=True, state=U0, source=src)
                 vs_.close()
                 variants[name] = {"zone_updates_per_s": zones * 3 / vsecs, "ms_per_step": vsecs / 3 * 1e3,
                                   "kernel_ms": {k: round(v[1] / v[0], 3) for k, v in vprof.items()}}

@@ -153,6 +153,26 @@ int ader_profile_read(ader_ctx* ctx, const char** names, int* launches, double* 
 int ader_set_predictor(ader_ctx* ctx, double tol, int max_iter);
 int ader_predictor_stats(ader_ctx* ctx, unsigned long long* out3_host, void* stream);
 
+/* Non-stiff source term S(U) of Eq. 4 (Sec. II; orders 2 and 3, modal and
+ * nodal).  The paper carries a general S through the predictor (Eqs. 30, 34,
+ * 36, 43; A.4, B.2-B.3) and the update (Eq. 6 with S-bar of Eqs. 35, 44;
+ * A.7, B.6) without naming one; two models are built:
+ *   ADER_SOURCE_LINEAR:  S = -k U on the five hydrodynamic variables,
+ *                        params[0] = k;
+ *   ADER_SOURCE_GRAVITY: S = (0, rho g, rho v . g), params[0..2] = g.
+ * The face field of MHD gets no source (Eq. 8 is unchanged).  The predictor
+ * evaluates the source at its nodes each iteration; S-bar comes from the
+ * source polynomial of the final iterate.  params is a host array (1 or 3
+ * doubles, copied); ADER_SOURCE_NONE (params may be NULL) removes the source.
+ * The first source allocates a per-zone buffer (5 x zones, bulk precision).
+ * Returns ADER_ERR_ARG for an unknown kind, non-finite parameters or an
+ * order-4 context.  ader_rk_step refuses a context with a source, and the
+ * learned-guess samples (ader_guess_samples) are taken without it. */
+#define ADER_SOURCE_NONE 0
+#define ADER_SOURCE_LINEAR 1
+#define ADER_SOURCE_GRAVITY 2
+int ader_set_source(ader_ctx* ctx, int kind, const double* params);
+
 /* Learned initial guess (third order; the paper has no learned component and
  * starts its Picard iteration of Sec. IV from zero).  params (device, FP32,
  * layout and size from ader_mlp_shape) is an MLP mapping a zone's normalised

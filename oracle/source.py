@@ -6,13 +6,17 @@ The paper carries a general source S through every formulation (Sec. II, Eq. 4;
 Sec. IV: Eqs. 30/34-35, 36/43-44, 45/52-53; Apps. A-C: A.4/A.7, B.2-B.3/B.6,
 C.2-C.3/C.6) but never names one.  Two source models are built here:
 
-* ``("linear", k)``: S = -k U (every component decays at the rate k), whose
-  uniform solution U(t) = U(0) exp(-k t) is a closed form;
+* ``("linear", k)``: S = -k U on the five hydrodynamic components (each
+  decays at the rate k), whose uniform solution U(t) = U(0) exp(-k t) is a
+  closed form;
 * ``("gravity", (gx, gy, gz))``: a uniform gravitational acceleration,
   S = (0, rho g, rho v . g) (and zero for B), whose solution with a uniform
   velocity and pressure is the initial density profile carried along
   x - v0 t - g t^2 / 2 while v = v0 + g t (exact for Euler and MHD with a
   uniform field).
+
+For MHD the field components get no source: the face field evolves by the
+constrained transport of Eq. 8 alone.
 
 How the source enters (the reading of the printed formulas, pinned against
 them in tests/test_oracle_source.py):
@@ -45,7 +49,9 @@ def evaluate(U, model):
     """S(U) at states U (nvar, ...) for a source model ("linear", k) or ("gravity", (gx, gy, gz))."""
     kind, par = model
     if kind == "linear":
-        return -float(par) * U
+        out = np.zeros_like(U)
+        out[:5] = -float(par) * U[:5]
+        return out
     if kind == "gravity":
         g = [float(v) for v in par]
         out = np.zeros_like(U)

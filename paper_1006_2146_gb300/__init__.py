@@ -8,9 +8,10 @@ plus the seeded input generators (``inputs``).
 """
 from . import inputs  # noqa: F401
 from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_FP32_BULK, ADER_HLL, ADER_LINEARIZED, ADER_MHD, ADER_NODAL,  # noqa: F401
+                   ADER_SOURCE_GRAVITY, ADER_SOURCE_LINEAR, ADER_SOURCE_NONE,
                    AderError, ader_create, ader_destroy, ader_diagnostics, ader_last_error, ader_launches_per_step,
                    ader_guess_eval, ader_guess_samples, ader_max_dt, ader_mlp_grad, ader_mlp_shape, ader_mlp_train, ader_predictor_stats,
-                   ader_profile, ader_profile_read, ader_profile_reset, ader_rk_step, ader_set_guess,
+                   ader_profile, ader_profile_read, ader_profile_reset, ader_rk_step, ader_set_guess, ader_set_source,
                    ader_set_predictor, ader_step, ader_step_devdt, ader_step_host, ader_sync_status, load)
 
 
@@ -47,6 +48,11 @@ class Solver:
 
     def predictor_stats(self, stream=None):
         return ader_predictor_stats(self.h, stream)
+
+    def set_source(self, kind, params=None):
+        """Non-stiff source: "linear" with params (k,), "gravity" with (gx, gy, gz), or None to remove it."""
+        code = {None: ADER_SOURCE_NONE, "linear": ADER_SOURCE_LINEAR, "gravity": ADER_SOURCE_GRAVITY}[kind]
+        ader_set_source(self.h, code, params)
 
     def set_guess(self, params):
         ader_set_guess(self.h, params)

@@ -15,11 +15,12 @@ ADER_HLL, ADER_LINEARIZED = 0, 1
 ADER_MHD, ADER_NODAL, ADER_FP32_BULK, ADER_CONVERGED_PREDICTOR = 1, 2, 4, 16
 ADER_OK, ADER_ERR_ARG, ADER_ERR_CUDA, ADER_ERR_UNPHYSICAL, ADER_ERR_NONFINITE, ADER_ERR_NOT_CONVERGED = 0, -1, -2, -3, -4, -5
 ADER_ERR_TIMEOUT = -6
+ADER_SOURCE_NONE, ADER_SOURCE_LINEAR, ADER_SOURCE_GRAVITY = 0, 1, 2
 
 EXPORTS = ("ader_create", "ader_step", "ader_step_devdt", "ader_max_dt", "ader_rk_step", "ader_step_host",
            "ader_diagnostics", "ader_sync_status", "ader_launches_per_step", "ader_profile", "ader_profile_reset",
-           "ader_profile_read", "ader_set_predictor", "ader_predictor_stats", "ader_set_guess", "ader_mlp_shape",
-           "ader_guess_samples", "ader_guess_eval", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy",
+           "ader_profile_read", "ader_set_predictor", "ader_predictor_stats", "ader_set_source", "ader_set_guess",
+           "ader_mlp_shape", "ader_guess_samples", "ader_guess_eval", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy",
            "ader_max_dt_static", "ader_batch_create", "ader_batch_tune", "ader_batch_step", "ader_batch_advance",
            "ader_batch_status", "ader_batch_tuning", "ader_batch_groups", "ader_batch_last_error",
            "ader_batch_destroy")
@@ -65,6 +66,7 @@ def load(path=None):
     lib.ader_set_predictor.argtypes = [vp, dbl, i32]
     lib.ader_predictor_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), vp]
     lib.ader_set_guess.argtypes = [vp, vp]
+    lib.ader_set_source.argtypes = [vp, ctypes.c_int, vp]
     lib.ader_mlp_shape.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(ctypes.c_longlong)]
     lib.ader_guess_samples.argtypes = [vp, vp, vp, dbl, vp, vp, vp, vp]
@@ -199,6 +201,16 @@ def ader_predictor_stats(h, stream=None):
     out = (ctypes.c_ulonglong * 3)()
     _check(h, load().ader_predictor_stats(h, out, _stream(stream)))
     return tuple(int(v) for v in out)
+
+
+def ader_set_source(h, kind, params=None):
+    """Non-stiff source of Eq. 4: ADER_SOURCE_LINEAR (params (k,)), ADER_SOURCE_GRAVITY ((gx, gy, gz)) or
+    ADER_SOURCE_NONE; params are copied by the library."""
+    arr = None
+    if params is not None:
+        vals = [float(v) for v in params]
+        arr = (ctypes.c_double * len(vals))(*vals)
+    return _check(h, load().ader_set_source(h, int(kind), arr))
 
 
 def ader_set_guess(h, params):

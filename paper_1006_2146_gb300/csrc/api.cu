@@ -1,6 +1,7 @@
 // C ABI of the library (include/ader.h): context, scratch ownership, step
 // sequencing and error reporting.  Every numerical step runs in the kernels
 // of recon.cu, step_o*.cu and reduce.cu.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -39,6 +40,9 @@ struct ader_ctx {
     const float* guess = nullptr;             // learned-guess MLP parameters (device), order 3
     float* G = nullptr;                       // per-zone learned guess (5 x NV x N FP32), allocated by ader_set_guess
     float* Uf = nullptr;                      // FP32 bulk: the state rounded to FP32 (5 x N), rewritten each step
+    int src_kind = SOURCE_NONE;               // non-stiff source (ader_set_source)
+    double src_par[3] = {0.0, 0.0, 0.0};
+    void* Sb = nullptr;                       // dt S-bar per zone (5 x N, bulk precision), allocated with the source
     bool setup_failed = false;                // a kernel could not be configured while enqueuing
     int launches = 0;
     std::string err;
@@ -122,6 +126,9 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.stats = c->stats;
     a.guess = n_iter > 0 ? c->guess : nullptr;
     a.G = a.guess ? c->G : nullptr;
+    a.src_kind = n_iter > 0 ? c->src_kind : SOURCE_NONE;
+    for (int i = 0; i < 3; ++i) a.src_par[i] = c->src_par[i];
+    a.Sb = a.src_kind != SOURCE_NONE ? c->Sb : nullptr;
     return a;
 }
 
@@ -234,7 +241,7 @@ void ader_destroy(ader_ctx* c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->spare) cudaEventDestroy(e);
-    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Uf, c->flag, c->stats, c->dtscr, c->partial, c->dt_dev,
+    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Uf, c->Sb, c->flag, c->stats, c->dtscr, c->partial, c->dt_dev,
                     c->Ustage, c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6],
                     c->rkB[0], c->rkB[1], c->rkB[2], c->rkB[3], c->rkB[4], c->rkB[5]};
     for (void* p : ptrs)
@@ -373,6 +380,7 @@ int ader_rk_step(ader_ctx* c, double* U, double* Bface, double dt, void* stream)
     if (!U) return fail(c, ADER_ERR_ARG, "U is null");
     if (int rc = check_bface(c, Bface)) return rc;
     if (!(dt > 0.0)) return fail(c, ADER_ERR_ARG, "dt must be positive");
+    if (c->src_kind != SOURCE_NONE) return fail(c, ADER_ERR_ARG, "SSP-RK with a source term is not built");
     cudaStream_t st = (cudaStream_t)stream;
     const bool mhd = c->mhd;
     const int ns = c->order == 2 ? 2 : (c->order == 3 ? 3 : 5);
@@ -466,6 +474,30 @@ int ader_predictor_stats(ader_ctx* c, unsigned long long* out3_host, void* strea
     if (rc == ADER_OK) rc = cuda_check(c, cudaMemsetAsync(c->stats, 0, 3 * sizeof(unsigned long long), st), "memset");
     if (rc == ADER_OK) rc = cuda_check(c, cudaStreamSynchronize(st), "cudaStreamSynchronize");
     return rc;
+}
+
+int ader_set_source(ader_ctx* c, int kind, const double* params) {
+    if (!c) return ADER_ERR_ARG;
+    if (kind == ADER_SOURCE_NONE) {
+        c->src_kind = SOURCE_NONE;
+        return ADER_OK;
+    }
+    if (kind != ADER_SOURCE_LINEAR && kind != ADER_SOURCE_GRAVITY) return fail(c, ADER_ERR_ARG, "unknown source kind");
+    if (c->order == 4) return fail(c, ADER_ERR_ARG, "source terms are built for orders 2 and 3");
+    if (!params) return fail(c, ADER_ERR_ARG, "null source parameters");
+    const int np = kind == ADER_SOURCE_LINEAR ? 1 : 3;
+    double par[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < np; ++i) {
+        if (!std::isfinite(params[i])) return fail(c, ADER_ERR_ARG, "non-finite source parameter");
+        par[i] = params[i];
+    }
+    if (!c->Sb) {
+        if (int rc = cuda_check(c, cudaMalloc(&c->Sb, (size_t)5 * (size_t)c->grid.n * c->rsize), "cudaMalloc source"))
+            return rc;
+    }
+    c->src_kind = kind == ADER_SOURCE_LINEAR ? SOURCE_LINEAR : SOURCE_GRAVITY;
+    for (int i = 0; i < 3; ++i) c->src_par[i] = par[i];
+    return ADER_OK;
 }
 
 int ader_set_guess(ader_ctx* c, const float* params) {

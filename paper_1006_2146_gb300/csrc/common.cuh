@@ -176,6 +176,37 @@ ADER_DEV R fast_speed(const Vec<NV, R>& u, const Prim<NV, R>& q, R gamma) {
     }
 }
 
+// ------------------------------------------------------------------ non-stiff source S(U) of Eq. 4
+// The paper carries a general source through every predictor and through
+// Eq. 6 without naming one; two models are built.  SOURCE_LINEAR: S = -k U on
+// the five hydrodynamic components.  SOURCE_GRAVITY: a uniform acceleration g,
+// S = (0, rho g, rho v . g).  The field components of MHD get no source (the
+// face field evolves by constrained transport alone).  Src holds the model
+// with dt folded in: the predictor works with s = dt S, as with the scaled
+// fluxes of Eq. 5.
+enum { SOURCE_NONE = 0, SOURCE_LINEAR = 1, SOURCE_GRAVITY = 2 };
+
+template <class R>
+struct Src {
+    int kind;
+    R a[3];           // dt k (linear) or dt g (gravity)
+};
+
+template <int NV, class R>
+ADER_DEV Vec<NV, R> source_at(const Vec<NV, R>& u, const Src<R>& s) {
+    Vec<NV, R> r = vzero<NV, R>();
+    if (s.kind == SOURCE_LINEAR) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) r[v] = -s.a[0] * u[v];
+    } else {
+        r[1] = s.a[0] * u[0];
+        r[2] = s.a[1] * u[0];
+        r[3] = s.a[2] * u[0];
+        r[4] = s.a[0] * u[1] + s.a[1] * u[2] + s.a[2] * u[3];
+    }
+    return r;
+}
+
 // ------------------------------------------------------------------ predictor control
 // Fixed mode (tol <= 0): exactly n_iter Picard steps (M - 1 in the paper).
 // Converged mode (tol > 0): iterate until the largest change of an

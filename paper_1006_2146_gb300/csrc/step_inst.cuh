@@ -25,6 +25,17 @@ namespace ader {
                                       R* ef) {                                                                       \
             o##O::face_mhd<D>(p, gm1, ub, avg, Fa, eu, ef);                                                           \
         }                                                                                                            \
+        static constexpr bool HAS_SOURCE = o##O::HAS_SOURCE;                                                         \
+        template <int NV, class R>                                                                                   \
+        static ADER_DEV void predict_modal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& n, const Src<R>& s,  \
+                                               Vec<NV, R>& sdt) {                                                    \
+            o##O::predict_modal_src(m, gm1, cx, cy, cz, n, s, sdt);                                                  \
+        }                                                                                                            \
+        template <int NV, class R>                                                                                   \
+        static ADER_DEV void predict_nodal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& n, const Src<R>& s,  \
+                                               Vec<NV, R>& sdt) {                                                    \
+            o##O::predict_nodal_src(m, gm1, cx, cy, cz, n, s, sdt);                                                  \
+        }                                                                                                            \
         static constexpr bool HAS_FACE_PAIR = o##O::HAS_FACE_PAIR;                                                   \
         template <int D, int NV, class R>                                                                            \
         static ADER_DEV void face_pair(const Vec<NV, R>* p, R gm1, Vec<NV, R>* ub, Vec<NV, R>* avg, Vec<NV, R>* Fa) {  \

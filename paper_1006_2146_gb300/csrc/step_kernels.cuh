@@ -138,7 +138,9 @@ ADER_DEV void record_iterations(unsigned long long* stats, const PredCtl& ctl) {
 #endif
 }
 
-template <int ORDER, int FORM, int NV, class R>
+// SRC: the context carries a non-stiff source (orders with ZoneOps::HAS_SOURCE); the predictor then also
+// writes dt S-bar of Eq. 6 for the update (a.Sb).
+template <int ORDER, int FORM, int NV, class R, bool SRC = false>
 ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U, long long z) {
     constexpr int LS = ModeCount<ORDER>::LS, L = ModeCount<ORDER>::L;
     Vec<NV, R> m[L + 1];
@@ -158,10 +160,24 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
             }
         }
         PredCtl ctl{a.n_iter, a.tol, a.max_iter, 0, false};
-        if (FORM == FORM_MODAL)
+        if constexpr (SRC) {
+            Src<R> src;
+            src.kind = a.src_kind;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) src.a[i] = dt * R(a.src_par[i]);
+            Vec<NV, R> sdt;
+            if (FORM == FORM_MODAL)
+                ZoneOps<ORDER>::predict_modal_src(m, gm1, cx, cy, cz, ctl, src, sdt);
+            else
+                ZoneOps<ORDER>::predict_nodal_src(m, gm1, cx, cy, cz, ctl, src, sdt);
+            R* Sb = (R*)a.Sb;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) Sb[v * a.grid.n + z] = sdt[v];
+        } else if (FORM == FORM_MODAL) {
             ZoneOps<ORDER>::predict_modal(m, gm1, cx, cy, cz, ctl);
-        else
+        } else {
             ZoneOps<ORDER>::predict_nodal(m, gm1, cx, cy, cz, ctl);
+        }
         if (a.tol > 0.0 && a.stats) record_iterations(a.stats, ctl);
         if (ctl.capped) raise_flag(a.flag, FLAG_NOT_CONVERGED);
     }
@@ -172,11 +188,11 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
 
 // FP32 bulk asks for three 128-thread blocks per SM (at most 168 registers, a few hundred bytes of
 // spills to L1): the extra warps hide more latency than the spills cost (about 12% per 256^3 step).
-template <int ORDER, int FORM, int NV, class R>
+template <int ORDER, int FORM, int NV, class R, bool SRC = false>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1)
     k_predict_faces(StepArgs a, const double* __restrict__ U) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (z < a.grid.n) zone_predict_faces<ORDER, FORM, NV, R>(a, U, z);
+    if (z < a.grid.n) zone_predict_faces<ORDER, FORM, NV, R, SRC>(a, U, z);
 }
 
 template <int NV, class R>
@@ -224,14 +240,18 @@ ADER_DEV void flux_difference(const StepArgs& a, long long z, int i, int j, int 
     for (int v = 0; v < 5; ++v) acc[v] -= ((double)Fp[v] - (double)Fm[v]) * inv;
 }
 
+// out = base + c acc (+ dt S-bar of Eq. 6 where the predictor wrote one, a.Sb in the bulk precision R)
+template <class R>
 ADER_DEV void store_update(const StepArgs& a, double* out, const double* base, double c_host, int use_dt_dev,
                            const double* acc, long long z) {
     const double c = use_dt_dev ? c_host * (*a.dt_dev) : c_host;
     const long long N = a.grid.n;
+    const R* Sb = (const R*)a.Sb;
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-        const double val = (base ? base[v * N + z] : 0.0) + c * acc[v];
+        double val = (base ? base[v * N + z] : 0.0) + c * acc[v];
+        if (Sb) val += (double)Sb[v * N + z];
         bad |= !isfinite(val);
         out[v * N + z] = val;
     }
@@ -248,7 +268,7 @@ ADER_DEV void zone_flux_update(const StepArgs& a, double* out, const double* bas
     flux_difference<SOLVER, 0, NV, R>(a, z, i, j, k, gamma, gm1, acc);
     flux_difference<SOLVER, 1, NV, R>(a, z, i, j, k, gamma, gm1, acc);
     flux_difference<SOLVER, 2, NV, R>(a, z, i, j, k, gamma, gm1, acc);
-    store_update(a, out, base, c_host, use_dt_dev, acc, z);
+    store_update<R>(a, out, base, c_host, use_dt_dev, acc, z);
 }
 
 template <int SOLVER, int NV, class R>
@@ -298,7 +318,7 @@ ADER_DEV void zone_flux_update_stored(const StepArgs& a, double* out, const doub
         for (int v = 0; v < 5; ++v)
             acc[v] -= ((double)F[(D * 5 + v) * N + z] - (double)F[(D * 5 + v) * N + zm]) * inv;
     }
-    store_update(a, out, base, c_host, use_dt_dev, acc, z);
+    store_update<R>(a, out, base, c_host, use_dt_dev, acc, z);
 }
 
 template <class R>
@@ -427,6 +447,15 @@ template <int ORDER, int NV, class R>
 int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st) {
     const int T = 128;
     const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
+    if constexpr (ZoneOps<ORDER>::HAS_SOURCE) {
+        if (a.src_kind != SOURCE_NONE && a.Sb && a.n_iter > 0) {
+            if (a.form == FORM_MODAL)
+                k_predict_faces<ORDER, FORM_MODAL, NV, R, true><<<blocks, T, 0, st>>>(a, U);
+            else
+                k_predict_faces<ORDER, FORM_NODAL, NV, R, true><<<blocks, T, 0, st>>>(a, U);
+            return 1;
+        }
+    }
     if (a.form == FORM_MODAL)
         k_predict_faces<ORDER, FORM_MODAL, NV, R><<<blocks, T, 0, st>>>(a, U);
     else

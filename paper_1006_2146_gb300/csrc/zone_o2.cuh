@@ -53,6 +53,70 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
     finish_o2(m, u5 - u1, ctl);
 }
 
+// ---- with a non-stiff source (s = dt S at the nodes of the current iterate)
+// The update of u5 now depends on u5 through the source at the tau = 1 node,
+// so each iteration recomputes it; sdt receives dt S-bar from the final
+// iterate.  `next(m5)` gives the new u5 for the current one.
+template <int NV, class R, class Next>
+ADER_DEV void iterate_o2(Vec<NV, R>* m, PredCtl& ctl, Next next) {
+    const bool conv = ctl.tol > 0.0;
+    const int cap = conv ? ctl.max_iter : ctl.n_iter;
+    const R ref = max_abs(m[1]) + R(1e-300);
+    ctl.iters = 0;
+    ctl.capped = conv;
+    for (int it = 0; it < cap; ++it) {
+        const Vec<NV, R> n5 = next(m[5]);
+        const R change = max_abs_diff(n5, m[5]);
+        m[5] = n5;
+        ++ctl.iters;
+        if (conv && change < R(ctl.tol) * ref) {
+            ctl.capped = false;
+            break;
+        }
+    }
+}
+
+// Eqs. 31-34, 30 and 35: s at the seven nodes of Eq. 31 (node 7 = u1 + u5 at tau = 1)
+constexpr bool HAS_SOURCE = true;
+
+template <int NV, class R>
+ADER_DEV void predict_modal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>& src,
+                                Vec<NV, R>& sdt) {
+    const Vec<NV, R> u1 = m[1] + 0.5 * m[2], u2 = m[1] - 0.5 * m[2];
+    const Vec<NV, R> u3 = m[1] + 0.5 * m[3], u4 = m[1] - 0.5 * m[3];
+    const Vec<NV, R> u5 = m[1] + 0.5 * m[4], u6 = m[1] - 0.5 * m[4];
+    const Vec<NV, R> F2 = scale(cx, flux<0>(u1, gm1) - flux<0>(u2, gm1));
+    const Vec<NV, R> G3 = scale(cy, flux<1>(u3, gm1) - flux<1>(u4, gm1));
+    const Vec<NV, R> H4 = scale(cz, flux<2>(u5, gm1) - flux<2>(u6, gm1));
+    const Vec<NV, R> s1 = (source_at(u1, src) + source_at(u2, src) + source_at(u3, src) + source_at(u4, src) +
+                           source_at(u5, src) + source_at(u6, src)) / 6.0;          // Eq. 34
+    const Vec<NV, R> base = s1 - (F2 + G3 + H4);
+    iterate_o2(m, ctl, [&](const Vec<NV, R>& m5) {
+        const Vec<NV, R> s5 = source_at(m[1] + m5, src) - s1;                      // Eq. 34
+        return base + (2.0 / 3.0) * s5;                                             // Eq. 30
+    });
+    sdt = s1 + 0.5 * (source_at(m[1] + m[5], src) - s1);                            // Eq. 35 (times dt)
+}
+
+// Eqs. A.5, A.4 and A.6-A.7: s at node 1 (tau = 0) and node 5 (tau = 1)
+template <int NV, class R>
+ADER_DEV void predict_nodal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>& src,
+                                Vec<NV, R>& sdt) {
+    const Vec<NV, R> u1 = m[1];
+    const Vec<NV, R> u2 = m[1] + 0.5 * m[2], u3 = m[1] + 0.5 * m[3], u4 = m[1] + 0.5 * m[4];
+    const Prim<NV, R> p1 = primitives(u1, gm1);
+    const Vec<NV, R> s1 = source_at(u1, src);
+    const Vec<NV, R> base = u1 - 2.0 * (scale(cx, flux<0>(u2, gm1) - flux_from<0>(u1, p1)) +
+                                        scale(cy, flux<1>(u3, gm1) - flux_from<1>(u1, p1)) +
+                                        scale(cz, flux<2>(u4, gm1) - flux_from<2>(u1, p1))) +
+                            s1 / 3.0;
+    iterate_o2(m, ctl, [&](const Vec<NV, R>& m5) {
+        const Vec<NV, R> u5 = base + (2.0 / 3.0) * source_at(u1 + m5, src);         // Eq. A.4
+        return u5 - u1;                                                              // Eq. A.6
+    });
+    sdt = 0.5 * (s1 + source_at(u1 + m[5], src));                                   // Eq. A.7 (times dt)
+}
+
 // Eqs. 58-59 and D.3-D.5: composing D.4 with D.5, <F> is the mean of the flux
 // at the four tau = 1/2 facial nodes (node 5 enters only through the time mode).
 template <int D, int NV, class R>

@@ -14,8 +14,12 @@ namespace o3 {
 
 
 // ------------------------------------------------------------------ modal, Sec. IV.2
-template <int NV, class R>
-ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl) {
+// SRC: with a non-stiff source (s = dt S at every node of the current iterate,
+// Eqs. 40-43 with f, g, h -> s, Eq. 36 with its source terms); sdt receives
+// dt S-bar of Eq. 44 from the source at the final iterate.
+template <int NV, class R, bool SRC = false>
+ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>* src = nullptr,
+                            Vec<NV, R>* sdt = nullptr) {
     // Eq. 38: the thirteen tau = 0 nodes of Eq. 37
     Vec<NV, R> u[14];
     u[1] = m[1] - (m[5] + m[6] + m[7]) / 12.0;
@@ -56,6 +60,27 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
     const Vec<NV, R> H7 = scale(cz, 0.5 * (q7 + q8 - q9) - 2.0 * h[1]);
     const Vec<NV, R> H9 = scale(cz, h[10] - h[11] - h[12] + h[13]);
     const Vec<NV, R> H10 = scale(cz, h[4] - h[5] - h[8] + h[9]);
+    // source modes from the tau = 0 nodes (Eqs. 40-43 with f, g, h -> s), built once
+    Vec<NV, R> S1, S2, S3, S4, s1;
+    if constexpr (SRC) {
+        Vec<NV, R> sn[14];
+#pragma unroll
+        for (int n = 1; n <= 13; ++n) sn[n] = source_at(u[n], *src);
+        const Vec<NV, R> a1 = sn[2] + sn[3] + sn[4] + sn[5], a2 = sn[6] + sn[7] + sn[8] + sn[9];
+        const Vec<NV, R> a3 = sn[10] + sn[11] + sn[12] + sn[13];
+        const Vec<NV, R> b4 = sn[2] + sn[6] + sn[10] + sn[12], b5 = sn[3] + sn[7] + sn[11] + sn[13];
+        const Vec<NV, R> b6 = sn[4] + sn[5] + sn[8] + sn[9];
+        const Vec<NV, R> c7 = sn[4] + sn[8] + sn[10] + sn[11], c8 = sn[5] + sn[9] + sn[12] + sn[13];
+        const Vec<NV, R> c9 = sn[2] + sn[3] + sn[6] + sn[7];
+        S2 = 0.25 * (a1 - a2);
+        S3 = 0.25 * (b4 - b5);
+        S4 = 0.25 * (c7 - c8);
+        const Vec<NV, R> S5 = 0.5 * (a1 + a2 - a3) - 2.0 * sn[1];
+        const Vec<NV, R> S6 = 0.5 * (b4 + b5 - b6) - 2.0 * sn[1];
+        const Vec<NV, R> S7 = 0.5 * (c7 + c8 - c9) - 2.0 * sn[1];
+        s1 = sn[1];
+        S1 = s1 + (S5 + S6 + S7) / 12.0;
+    }
     const bool conv = ctl.tol > 0.0;
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
     const R ref = max_abs(m[1]) + R(1e-300);
@@ -73,12 +98,26 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
         const Vec<NV, R> F13 = 2.0 * (scale(cx, flux<0>(u14, gm1) - flux<0>(u15, gm1)) - F2);
         const Vec<NV, R> G14 = 2.0 * (scale(cy, flux<1>(u16, gm1) - flux<1>(u17, gm1)) - G3);
         const Vec<NV, R> H15 = 2.0 * (scale(cz, flux<2>(u18, gm1) - flux<2>(u19, gm1)) - H4);
-        // Eq. 36 without sources
-        const Vec<NV, R> n11 = -(F2 + G3 + H4);
-        const Vec<NV, R> n12 = -0.5 * (F13 + G14 + H15);
-        const Vec<NV, R> n13 = -(2.0 * F5 + G8 + H10);
-        const Vec<NV, R> n14 = -(F8 + 2.0 * G6 + H9);
-        const Vec<NV, R> n15 = -(F10 + G9 + 2.0 * H7);
+        // Eq. 36
+        Vec<NV, R> n11 = -(F2 + G3 + H4);
+        Vec<NV, R> n12 = -0.5 * (F13 + G14 + H15);
+        Vec<NV, R> n13 = -(2.0 * F5 + G8 + H10);
+        Vec<NV, R> n14 = -(F8 + 2.0 * G6 + H9);
+        Vec<NV, R> n15 = -(F10 + G9 + 2.0 * H7);
+        if constexpr (SRC) {
+            const Vec<NV, R> s14 = source_at(u14, *src), s15 = source_at(u15, *src);
+            const Vec<NV, R> s16 = source_at(u16, *src), s17 = source_at(u17, *src);
+            const Vec<NV, R> s18 = source_at(u18, *src), s19 = source_at(u19, *src);
+            const Vec<NV, R> s20 = source_at(u[1] + m[11] + m[12], *src);
+            const Vec<NV, R> S13 = 2.0 * (s14 - s15 - S2), S14 = 2.0 * (s16 - s17 - S3), S15 = 2.0 * (s18 - s19 - S4);
+            const Vec<NV, R> S11 = 2.0 * (s14 + s15 + s16 + s17 + s18 + s19 - 6.0 * S1) / 3.0 - s20 + s1;
+            const Vec<NV, R> S12 = s20 - s1 - S11;
+            n11 += S1 - 0.3 * S12;
+            n12 += 0.5 * S11 + 0.6 * S12;
+            n13 += S2 + (2.0 / 3.0) * S13;
+            n14 += S3 + (2.0 / 3.0) * S14;
+            n15 += S4 + (2.0 / 3.0) * S15;
+        }
         R change = R(0);
         if (conv)
             change = fmax(fmax(fmax(max_abs_diff(n11, m[11]), max_abs_diff(n12, m[12])),
@@ -95,11 +134,33 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
             break;
         }
     }
+    if constexpr (SRC) {        // Eq. 44 from the source at the final iterate's tau > 0 nodes (Eq. 39)
+        const Vec<NV, R> u14 = 0.25 * (u[2] + u[3] + u[4] + u[5] + m[12] + m[13]) + 0.5 * m[11] - 0.125 * (m[6] + m[7]);
+        const Vec<NV, R> u16 = 0.25 * (u[2] + u[6] + u[10] + u[12] + m[12] + m[14]) + 0.5 * m[11] - 0.125 * (m[5] + m[7]);
+        const Vec<NV, R> u18 = 0.25 * (u[4] + u[8] + u[10] + u[11] + m[12] + m[15]) + 0.5 * m[11] - 0.125 * (m[5] + m[6]);
+        const Vec<NV, R> ssum = source_at(u14, *src) + source_at(u14 - m[2] - 0.5 * m[13], *src) +
+                                source_at(u16, *src) + source_at(u16 - m[3] - 0.5 * m[14], *src) +
+                                source_at(u18, *src) + source_at(u18 - m[4] - 0.5 * m[15], *src);
+        const Vec<NV, R> s20 = source_at(u[1] + m[11] + m[12], *src);
+        const Vec<NV, R> S11 = 2.0 * (ssum - 6.0 * S1) / 3.0 - s20 + s1;
+        const Vec<NV, R> S12 = s20 - s1 - S11;
+        *sdt = S1 + 0.5 * S11 + S12 / 3.0;
+    }
+}
+
+template <int NV, class R>
+ADER_DEV void predict_modal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>& src,
+                                Vec<NV, R>& sdt) {
+    predict_modal<NV, R, true>(m, gm1, cx, cy, cz, ctl, &src, &sdt);
 }
 
 // ------------------------------------------------------------------ nodal, App. B
-template <int NV, class R>
-ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl) {
+// SRC: with a non-stiff source (s = dt S at nodes 1-7 once and at the tau > 0
+// nodes of the current iterate; the source terms of Eqs. B.2-B.3); sdt
+// receives dt S-bar of Eq. B.6 from the source at the final iterate.
+template <int NV, class R, bool SRC = false>
+ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>* src = nullptr,
+                            Vec<NV, R>* sdt = nullptr) {
     // Eq. B.4: the ten tau = 0 nodes of Eq. B.1
     Vec<NV, R> u[16];
     u[1] = m[1] - (m[5] + m[6] + m[7]) / 12.0;
@@ -122,18 +183,31 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
         h[n] = scale(cz, flux_from<2>(u[n], q));
     }
     // Eq. B.2 without sources
-    const Vec<NV, R> q11 = u[1] + 0.5 * (f[3] - f[1]) + 0.5 * (g[5] - g[1]) + 0.5 * (h[7] - h[1]);
-    const Vec<NV, R> q12 = u[2] + (36.0 * f[1] - 24.0 * f[2] - 12.0 * f[3] - 36.0 * g[1] + 24.0 * g[2] + 24.0 * g[4] +
+    Vec<NV, R> q11 = u[1] + 0.5 * (f[3] - f[1]) + 0.5 * (g[5] - g[1]) + 0.5 * (h[7] - h[1]);
+    Vec<NV, R> q12 = u[2] + (36.0 * f[1] - 24.0 * f[2] - 12.0 * f[3] - 36.0 * g[1] + 24.0 * g[2] + 24.0 * g[4] +
                              12.0 * g[5] - 24.0 * g[10] - 36.0 * h[1] + 24.0 * h[2] + 24.0 * h[6] + 12.0 * h[7] -
                              24.0 * h[9]) / 24.0;
-    const Vec<NV, R> q13 = u[4] + (-36.0 * f[1] + 24.0 * f[2] + 12.0 * f[3] + 24.0 * f[4] - 24.0 * f[10] + 36.0 * g[1] -
+    Vec<NV, R> q13 = u[4] + (-36.0 * f[1] + 24.0 * f[2] + 12.0 * f[3] + 24.0 * f[4] - 24.0 * f[10] + 36.0 * g[1] -
                              24.0 * g[4] - 12.0 * g[5] - 36.0 * h[1] + 24.0 * h[4] + 24.0 * h[6] + 12.0 * h[7] -
                              24.0 * h[8]) / 24.0;
-    const Vec<NV, R> q14 = u[6] + (-36.0 * f[1] + 24.0 * f[2] + 12.0 * f[3] + 24.0 * f[6] - 24.0 * f[9] - 36.0 * g[1] +
+    Vec<NV, R> q14 = u[6] + (-36.0 * f[1] + 24.0 * f[2] + 12.0 * f[3] + 24.0 * f[6] - 24.0 * f[9] - 36.0 * g[1] +
                              24.0 * g[4] + 12.0 * g[5] + 24.0 * g[6] - 24.0 * g[8] + 36.0 * h[1] - 24.0 * h[6] -
                              12.0 * h[7]) / 24.0;
-    const Vec<NV, R> q15 = u[1] + (-60.0 * f[1] + 30.0 * f[2] + 30.0 * f[3] - 60.0 * g[1] + 30.0 * g[4] + 30.0 * g[5] -
+    Vec<NV, R> q15 = u[1] + (-60.0 * f[1] + 30.0 * f[2] + 30.0 * f[3] - 60.0 * g[1] + 30.0 * g[4] + 30.0 * g[5] -
                              60.0 * h[1] + 30.0 * h[6] + 30.0 * h[7]) / 30.0;
+    Vec<NV, R> s0sum, s1;         // with a source: s2 + ... + s7 and s1 (nodes 1-7, built once)
+    if constexpr (SRC) {          // Eq. B.2, source terms
+        Vec<NV, R> sn[8];
+#pragma unroll
+        for (int n = 1; n <= 7; ++n) sn[n] = source_at(u[n], *src);
+        s1 = sn[1];
+        s0sum = sn[2] + sn[3] + sn[4] + sn[5] + sn[6] + sn[7];
+        q11 += (-9.0 * sn[1] + 2.0 * s0sum) / 24.0;
+        q12 += (7.0 * sn[1] - 10.0 * sn[2] - 6.0 * sn[3] + 2.0 * s0sum) / 24.0;
+        q13 += (7.0 * sn[1] - 10.0 * sn[4] - 6.0 * sn[5] + 2.0 * s0sum) / 24.0;
+        q14 += (7.0 * sn[1] - 10.0 * sn[6] - 6.0 * sn[7] + 2.0 * s0sum) / 24.0;
+        q15 += (-27.0 * sn[1] + 5.0 * s0sum) / 30.0;
+    }
     // initial guess: the evolutionary modes in m[11..15] (zero: no time evolution) at the
     // tau > 0 nodes of Eq. B.1
     const Vec<NV, R> g0 = 0.5 * m[11] + 0.25 * m[12];
@@ -150,11 +224,22 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
         const Vec<NV, R> q1 = 0.5 * (scale(cx, flux_from<0>(u11, p11) - flux<0>(u12, gm1)) +
                                scale(cy, flux_from<1>(u11, p11) - flux<1>(u13, gm1)) +
                                scale(cz, flux_from<2>(u11, p11) - flux<2>(u14, gm1)));
-        u11 = q11 + q1;
-        u12 = q12 + q1;
-        u13 = q13 + q1;
-        u14 = q14 + q1;
-        u15 = q15 + 4.0 * q1;
+        if constexpr (SRC) {      // Eq. B.3 with its source terms, at the current iterate
+            const Vec<NV, R> s11 = source_at(u11, *src), s12 = source_at(u12, *src);
+            const Vec<NV, R> s13 = source_at(u13, *src), s14 = source_at(u14, *src), s15 = source_at(u15, *src);
+            const Vec<NV, R> q2 = q1 + (-4.0 * s11 - 3.0 * s15) / 24.0;
+            u11 = q11 + q1 + 0.125 * (4.0 * s11 - s15);
+            u12 = q12 + q2 + (2.0 / 3.0) * s12;
+            u13 = q13 + q2 + (2.0 / 3.0) * s13;
+            u14 = q14 + q2 + (2.0 / 3.0) * s14;
+            u15 = q15 + 4.0 * q1 + 0.1 * (8.0 * s11 + s15);
+        } else {
+            u11 = q11 + q1;
+            u12 = q12 + q1;
+            u13 = q13 + q1;
+            u14 = q14 + q1;
+            u15 = q15 + 4.0 * q1;
+        }
         ++ctl.iters;
         if (conv) {
             // Eq. B.5 each iteration, to measure the change in mode space
@@ -185,7 +270,17 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
         m[14] = 4.0 * (u13 - u11 - u[4] + u[1]);
         m[15] = 4.0 * (u14 - u11 - u[6] + u[1]);
     }
+    if constexpr (SRC)            // Eq. B.6 from the source at the final iterate (times dt)
+        *sdt = (-5.0 * s1 + s0sum + 4.0 * source_at(u11, *src) + source_at(u15, *src)) / 6.0;
 }
+
+template <int NV, class R>
+ADER_DEV void predict_nodal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>& src,
+                                Vec<NV, R>& sdt) {
+    predict_nodal<NV, R, true>(m, gm1, cx, cy, cz, ctl, &src, &sdt);
+}
+
+constexpr bool HAS_SOURCE = true;
 
 // ------------------------------------------------------------------ x+ face, Sec. V.2 and App. D
 // p = the zone's modes in the face's x-frame (modes.cuh).  Outputs the

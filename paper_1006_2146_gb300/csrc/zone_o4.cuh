@@ -482,6 +482,13 @@ ADER_DEV void edge_states(const Vec<8, R>* p, const Vec<8, R>& ub, const Vec<8, 
     e[3] = u2 - q2;
 }
 
+// No source terms at this order yet: contexts of order 4 refuse a source.
+constexpr bool HAS_SOURCE = false;
+template <int NV, class R>
+ADER_DEV void predict_modal_src(Vec<NV, R>*, R, R, R, R, PredCtl&, const Src<R>&, Vec<NV, R>&) {}
+template <int NV, class R>
+ADER_DEV void predict_nodal_src(Vec<NV, R>*, R, R, R, R, PredCtl&, const Src<R>&, Vec<NV, R>&) {}
+
 // No paired-face form at this order: the faces are evaluated one at a time.
 constexpr bool HAS_FACE_PAIR = false;
 template <int D, int NV, class R>

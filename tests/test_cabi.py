@@ -43,6 +43,8 @@ def test_invalid_arguments_are_rejected_without_touching_the_gpu(lib):
         with pytest.raises(_lib.AderError) as e:
             _lib.ader_create(*args)
         assert e.value.code == _lib.ADER_ERR_ARG
+    # a null context is refused by every call that takes one
+    assert lib.ader_set_source(None, _lib.ADER_SOURCE_GRAVITY, None) == _lib.ADER_ERR_ARG
 
 
 def test_generated_nodal_o4_coefficients_match_the_paper():
