@@ -2,8 +2,8 @@
 the mathematics fixes.
 
 * The Galerkin construction reproduces the printed source coefficients of the modal evolutionary
-  equations (Eqs. 30, 36, 45), of the nodal ones (Eqs. A.4, B.2-B.3) and the S-bar rules (Eqs. 35, 44,
-  53, A.7, B.6); the coefficients below are typed from those equations.
+  equations (Eqs. 30, 36, 45), of the nodal ones (Eqs. A.4, B.2-B.3 and three rows of C.2) and the S-bar
+  rules (Eqs. 35, 44, 53, A.7, B.6); the coefficients below are typed from those equations.
 * The modal source rules return the exact modes of any polynomial in the span.
 * The uniform decay u' = -k u: one second-order step is the Taylor polynomial 1 - x + x^2/2 (x = k dt),
   and every order's one-step error falls at order M + 1.
@@ -80,6 +80,26 @@ def test_nodal_third_order_matches_eqs_B2_B3_B6():
     sbar = source.average_weights(3) @ np.linalg.solve(V, s)
     assert sbar == pytest.approx((-5 * S(1) + S(2) + S(3) + S(4) + S(5) + S(6) + S(7) + 4 * S(11) + S(15)) / 6.0,
                                  abs=1e-14)                                                      # Eq. B.6
+
+
+def test_nodal_fourth_order_matches_printed_rows_of_eq_C2():
+    """The tau = 0 source terms of three printed rows of Eq. C.2 (q21, q34, q35), from the Galerkin
+    solution with the tau > 0 sources set to zero (they enter only Eq. C.3)."""
+    pts = nodes.as_array(nodes.NODAL[4])
+    V = basis.eval_basis(4, pts)
+    E, C = _coefs(4, "nodal")
+    uh_of_s = np.zeros((35, 35))
+    uh_of_s[E] = C @ np.linalg.inv(V)
+    rows = V @ uh_of_s                                  # node values from node sources, w = 0
+    printed = {
+        21: ([-89091, 0] + [17955] * 6 + [0] * 12, 215460),
+        34: ([413535, -114912, -138516, -11200, -163086, -32494, -343581, -156604, 171248, -11466, 159782,
+              -1638, 122234, 13104, 35840, 35840, 29288, 29288, -119392, 110432], 323190),
+        35: ([-29241, 0] + [5985] * 6 + [0] * 12, 71820),
+    }
+    for node, (num, den) in printed.items():
+        np.testing.assert_allclose(rows[node - 1, :20], np.array(num, dtype=float) / den, atol=1e-13,
+                                   err_msg="q%d" % node)
 
 
 def test_modal_sbar_weights_match_eqs_35_44_53():
