@@ -462,6 +462,7 @@ int ader_batch_tune(ader_batch* b, double* const* U, double* const* Bface, void*
             if (!batch_phase_applies(ph, g.order, g.mhd)) continue;
             Tuned best;
             for (int T : Ts) {
+                if (ph == PH_PREDICT && T > BATCH_PREDICT_MAX_THREADS) continue;
                 const void* fn = nullptr;
                 run_phase(g, ph, T, 1, st, false, &fn);
                 int occ = 0;

@@ -90,8 +90,12 @@ __global__ void __launch_bounds__(256) kb_cross2(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) { zone_cross2<NV, R>(it.a.grid, (R*)it.a.S2, z); });
 }
 
+// at most 128 zones per block, three blocks per SM (as the single-problem FP32 predictor): the tuner
+// tries no larger block for this phase
+constexpr int BATCH_PREDICT_MAX_THREADS = 128;
+
 template <int ORDER, int FORM, int NV, class R>
-__global__ void __launch_bounds__(256) kb_predict_faces(BatchGroupDev g) {
+__global__ void __launch_bounds__(BATCH_PREDICT_MAX_THREADS, 3) kb_predict_faces(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) { zone_predict_faces<ORDER, FORM, NV, R>(it.a, it.U, z); });
 }
 

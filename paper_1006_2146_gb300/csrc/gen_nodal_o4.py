@@ -1,4 +1,4 @@
-"""Generate nodal_o4_coeffs.cuh: the source-free fourth-order nodal ADER-CG update of App. C.
+"""Generate nodal_o4_coeffs.cuh: the fourth-order nodal ADER-CG update of App. C.
 
 The nodal scheme evolves the values at the 35 nodes of Eq. C.1.  Without
 source terms its update is linear in the scaled nodal fluxes: the flux
@@ -11,7 +11,9 @@ where base(k) is the tau = 0 node at the same spatial point.  The paper
 prints these coefficients as integers over 53865 .. 646380; this script
 derives them exactly (rational arithmetic) and writes them as sparse CUDA
 statements.  `coefficients()` is also used by a CPU test that compares the
-derived numbers with rows printed in Eqs. C.2-C.3.
+derived numbers with rows printed in Eqs. C.2-C.3.  `source_coefficients()`
+adds the non-stiff source terms of Eqs. C.2-C.3 (a Galerkin projection of the
+source interpolant, see there) and the weights of S-bar (Eq. C.6).
 
 Run:  python gen_nodal_o4.py   (rewrites nodal_o4_coeffs.cuh next to this file)
 """
@@ -105,6 +107,59 @@ def coefficients():
     return C
 
 
+def _int1d(a, b):
+    """Exact integral over [-1/2, 1/2] of P_a P_b."""
+    prod = [Fr(0)] * (len(PPOLY[a]) + len(PPOLY[b]) - 1)
+    for i, ca in enumerate(PPOLY[a]):
+        for j, cb in enumerate(PPOLY[b]):
+            prod[i + j] += ca * cb
+    return sum(c * (Fr(1, 2) ** (p + 1) - Fr(-1, 2) ** (p + 1)) / (p + 1) for p, c in enumerate(prod))
+
+
+def source_coefficients():
+    """(CS, W) exact.  CS[k][j]: response of node k (21..35) to the scaled source s = dt S at node j
+    (1..35); W[j]: weight of node j in the space-time average of the source polynomial (dt S-bar).
+
+    With a source, du/dtau = -div f + s holds in the Galerkin sense with the Lagrange polynomials of the
+    nodes with tau > 0 as test functions (the source polynomial is the interpolant through the nodes);
+    the flux part stays the derivative matching of coefficients(), its exact solution."""
+    n = len(NODES)
+    V = [[_phi(m, p) for m in MODES] for p in NODES]
+    Vi = _inverse(V)
+    idx = {m: i for i, m in enumerate(MODES)}
+    E = [k for k, m in enumerate(MODES) if m[3] >= 1]
+    M = [[Fr(0)] * n for _ in range(n)]
+    for i, mi in enumerate(MODES):
+        for j, mj in enumerate(MODES):
+            sp = _int1d(mi[0], mj[0]) * _int1d(mi[1], mj[1]) * _int1d(mi[2], mj[2])
+            if sp != 0:
+                M[i][j] = sp * Fr(1, mi[3] + mj[3] + 1)
+    T = [[Fr(0)] * n for _ in range(n)]                     # T[j][k]: mode j in d(phi_k)/d(tau)
+    for k, (a, b, c, d) in enumerate(MODES):
+        if d >= 1:
+            T[idx[(a, b, c, d - 1)]][k] = Fr(d)
+    evo_nodes = [q for q in range(n) if NODES[q][3] > 0]
+    Psi = [[Vi[i][q] for q in evo_nodes] for i in range(n)]  # Lagrange polynomials of the tau > 0 nodes
+    PM = [[sum(Psi[i][r] * M[i][j] for i in range(n) if Psi[i][r] != 0) for j in range(n)]
+          for r in range(len(evo_nodes))]
+    A = [[sum(PM[r][j] * T[j][E[c]] for j in range(n) if T[j][E[c]] != 0) for c in range(len(E))]
+         for r in range(len(evo_nodes))]
+    Ai = _inverse(A)
+    # evolutionary modes of a unit source value at node q: Ai PM Vi[:, q]
+    CS = [[Fr(0)] * (n + 1) for _ in range(n + 1)]
+    for q in range(n):
+        sm = [Vi[k][q] for k in range(n)]
+        b = [sum(PM[r][j] * sm[j] for j in range(n) if sm[j] != 0) for r in range(len(evo_nodes))]
+        evo = [sum(Ai[c][r] * b[r] for r in range(len(evo_nodes))) for c in range(len(E))]
+        for node in range(20, n):
+            CS[node + 1][q + 1] = sum(V[node][E[c]] * evo[c] for c in range(len(E)))
+    avg = []
+    for (a, b, c, d) in MODES:
+        avg.append(_int1d(a, 0) * _int1d(b, 0) * _int1d(c, 0) * Fr(1, d + 1))
+    W = [Fr(0)] + [sum(avg[k] * Vi[k][q] for k in range(n)) for q in range(n)]
+    return CS, W
+
+
 def base_node(k):
     """The tau = 0 node at the spatial point of node k."""
     x = NODES[k - 1][:3]
@@ -164,6 +219,31 @@ def emit():
         t = _terms(C, k, 21, 35, None, 21)
         assert all("[14]" not in s for s in t), "node 35 flux must not enter the update"
         lines.append("    e[%d] = qt[%d]%s;" % (k - 21, k - 21, "".join("\n        + " + s for s in t)))
+    CS, W = source_coefficients()
+    lines += ["}", "",
+              "// the source terms of Eq. C.2: qt[k-21] += tau = 0 node sources s[1..20] (s = dt S)",
+              "template <int NV, class R>",
+              "ADER_DEV void nodal_o4_qterms_src(const Vec<NV, R>* s, Vec<NV, R>* qt) {"]
+    for k in range(21, 36):
+        t = ["%.17g * s[%d]" % (float(CS[k][j]), j) for j in range(1, 21) if CS[k][j] != 0]
+        if t:
+            lines.append("    qt[%d] += %s;" % (k - 21, "\n        + ".join(t)))
+    lines += ["}", "",
+              "// the source terms of Eq. C.3: e[k-21] += tau > 0 node sources s[node - 21] of the current iterate",
+              "template <int NV, class R>",
+              "ADER_DEV void nodal_o4_update_src(const Vec<NV, R>* s, Vec<NV, R>* e) {"]
+    for k in range(21, 36):
+        t = ["%.17g * s[%d]" % (float(CS[k][j]), j - 21) for j in range(21, 36) if CS[k][j] != 0]
+        if t:
+            lines.append("    e[%d] += %s;" % (k - 21, "\n        + ".join(t)))
+    lines += ["}", "",
+              "// dt S-bar (Eq. C.6): the space-time average of the source interpolant; s0 indexed by node",
+              "// 1..20, s1 by node - 21",
+              "template <int NV, class R>",
+              "ADER_DEV Vec<NV, R> nodal_o4_sbar(const Vec<NV, R>* s0, const Vec<NV, R>* s1) {"]
+    t = ["%.17g * s0[%d]" % (float(W[j]), j) for j in range(1, 21) if W[j] != 0]
+    t += ["%.17g * s1[%d]" % (float(W[j]), j - 21) for j in range(21, 36) if W[j] != 0]
+    lines.append("    return %s;" % "\n        + ".join(t))
     lines += ["}", "", "}  // namespace o4", "}  // namespace ader", ""]
     return "\n".join(lines)
 

@@ -26,6 +26,7 @@ namespace ader {
             o##O::face_mhd<D>(p, gm1, ub, avg, Fa, eu, ef);                                                           \
         }                                                                                                            \
         static constexpr bool HAS_SOURCE = o##O::HAS_SOURCE;                                                         \
+        static constexpr bool HAS_SOURCE_MODAL = o##O::HAS_SOURCE_MODAL;                                             \
         template <int NV, class R>                                                                                   \
         static ADER_DEV void predict_modal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& n, const Src<R>& s,  \
                                                Vec<NV, R>& sdt) {                                                    \

@@ -449,11 +449,14 @@ int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st)
     const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
     if constexpr (ZoneOps<ORDER>::HAS_SOURCE) {
         if (a.src_kind != SOURCE_NONE && a.Sb && a.n_iter > 0) {
-            if (a.form == FORM_MODAL)
-                k_predict_faces<ORDER, FORM_MODAL, NV, R, true><<<blocks, T, 0, st>>>(a, U);
-            else
+            if (a.form == FORM_NODAL) {
                 k_predict_faces<ORDER, FORM_NODAL, NV, R, true><<<blocks, T, 0, st>>>(a, U);
-            return 1;
+                return 1;
+            }
+            if constexpr (ZoneOps<ORDER>::HAS_SOURCE_MODAL) {
+                k_predict_faces<ORDER, FORM_MODAL, NV, R, true><<<blocks, T, 0, st>>>(a, U);
+                return 1;
+            }
         }
     }
     if (a.form == FORM_MODAL)

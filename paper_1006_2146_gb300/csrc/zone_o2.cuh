@@ -78,6 +78,7 @@ ADER_DEV void iterate_o2(Vec<NV, R>* m, PredCtl& ctl, Next next) {
 
 // Eqs. 31-34, 30 and 35: s at the seven nodes of Eq. 31 (node 7 = u1 + u5 at tau = 1)
 constexpr bool HAS_SOURCE = true;
+constexpr bool HAS_SOURCE_MODAL = true;
 
 template <int NV, class R>
 ADER_DEV void predict_modal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>& src,

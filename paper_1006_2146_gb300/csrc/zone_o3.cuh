@@ -281,6 +281,7 @@ ADER_DEV void predict_nodal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl&
 }
 
 constexpr bool HAS_SOURCE = true;
+constexpr bool HAS_SOURCE_MODAL = true;
 
 // ------------------------------------------------------------------ x+ face, Sec. V.2 and App. D
 // p = the zone's modes in the face's x-frame (modes.cuh).  Outputs the

@@ -259,8 +259,11 @@ ADER_DEV void nodal_o4_to_modes(const Vec<NV, R>* u, const Vec<NV, R>* e, Vec<NV
 #undef UB
 }
 
-template <int NV, class R>
-ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl) {
+// SRC: with a non-stiff source (s = dt S at nodes 1..20 once and at the tau > 0 nodes of the current
+// iterate; the source terms of Eqs. C.2-C.3); sdt receives dt S-bar of Eq. C.6 from the final iterate.
+template <int NV, class R, bool SRC = false>
+ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>* src = nullptr,
+                            Vec<NV, R>* sdt = nullptr) {
     // Eq. C.4: the twenty tau = 0 nodes of Eq. C.1
     Vec<NV, R> u[21];
     const Vec<NV, R> q1 = 0.25 * m[2] - 0.125 * (m[8] + m[10]) + (-21.0 * m[11] + 40.0 * m[16] + 40.0 * m[18] + 60.0 * m[20]) / 960.0;
@@ -299,6 +302,12 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
         }
         nodal_o4_qterms(u, f, g, h, qt);
     }
+    Vec<NV, R> s0[21];              // with a source: s at the tau = 0 nodes, built once
+    if constexpr (SRC) {
+#pragma unroll
+        for (int n = 1; n <= 20; ++n) s0[n] = source_at(u[n], *src);
+        nodal_o4_qterms_src(s0, qt);
+    }
     // initial guess: the evolutionary modes in m[21..35] (zero: no time evolution) at the
     // tau > 0 nodes of Eq. C.1
     Vec<NV, R> e[16];
@@ -317,7 +326,13 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
             g[k] = scale(cy, flux_from<1>(e[k], q));
             h[k] = scale(cz, flux_from<2>(e[k], q));
         }
-        nodal_o4_update(qt, f, g, h, e);   // Eq. C.3 without sources
+        Vec<NV, R> se[15];
+        if constexpr (SRC) {
+#pragma unroll
+            for (int k = 0; k < 15; ++k) se[k] = source_at(e[k], *src);
+        }
+        nodal_o4_update(qt, f, g, h, e);   // Eq. C.3
+        if constexpr (SRC) nodal_o4_update_src(se, e);
         ++ctl.iters;
         if (conv) {
             Vec<NV, R> old[15];
@@ -334,6 +349,18 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
         }
     }
     if (!conv) nodal_o4_to_modes(u, e, m);
+    if constexpr (SRC) {            // Eq. C.6 from the source at the final iterate (times dt)
+        Vec<NV, R> se[15];
+#pragma unroll
+        for (int k = 0; k < 15; ++k) se[k] = source_at(e[k], *src);
+        *sdt = nodal_o4_sbar(s0, se);
+    }
+}
+
+template <int NV, class R>
+ADER_DEV void predict_nodal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>& src,
+                                Vec<NV, R>& sdt) {
+    predict_nodal<NV, R, true>(m, gm1, cx, cy, cz, ctl, &src, &sdt);
 }
 
 
@@ -482,12 +509,12 @@ ADER_DEV void edge_states(const Vec<8, R>* p, const Vec<8, R>& ub, const Vec<8, 
     e[3] = u2 - q2;
 }
 
-// No source terms at this order yet: contexts of order 4 refuse a source.
-constexpr bool HAS_SOURCE = false;
+// Source terms at this order: nodal only (the modal form's source modes of Eqs. 49-52 are not built;
+// an order-4 modal context refuses a source).
+constexpr bool HAS_SOURCE = true;
+constexpr bool HAS_SOURCE_MODAL = false;
 template <int NV, class R>
 ADER_DEV void predict_modal_src(Vec<NV, R>*, R, R, R, R, PredCtl&, const Src<R>&, Vec<NV, R>&) {}
-template <int NV, class R>
-ADER_DEV void predict_nodal_src(Vec<NV, R>*, R, R, R, R, PredCtl&, const Src<R>&, Vec<NV, R>&) {}
 
 // No paired-face form at this order: the faces are evaluated one at a time.
 constexpr bool HAS_FACE_PAIR = false;

@@ -71,6 +71,28 @@ def test_generated_nodal_o4_coefficients_match_the_paper():
     assert n > 300
 
 
+def test_generated_nodal_o4_source_terms_match_the_paper():
+    """The generator's fourth-order nodal source terms equal printed rows of Eq. C.2 (q21, q34, q35) and
+    the S-bar weights of Eq. C.6."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "gen_nodal_o4", os.path.join(ROOT, "paper_1006_2146_gb300", "csrc", "gen_nodal_o4.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    CS, W = gen.source_coefficients()
+    printed = {21: ([-89091, 0] + [17955] * 6 + [0] * 12, 215460),
+               34: ([413535, -114912, -138516, -11200, -163086, -32494, -343581, -156604, 171248, -11466,
+                     159782, -1638, 122234, 13104, 35840, 35840, 29288, 29288, -119392, 110432], 323190),
+               35: ([-29241, 0] + [5985] * 6 + [0] * 12, 71820)}
+    for node, (num, den) in printed.items():
+        for j in range(1, 21):
+            assert CS[node][j] == Fr(num[j - 1], den), (node, j)
+    c6 = {1: 15, 3: -2, 4: -2, 5: -2, 6: -2, 7: -2, 8: -2, 21: -27, 22: 6, 23: 6, 24: 6, 25: 6, 26: 6, 27: 6,
+          31: 9, 35: 3}
+    for j in range(1, 36):
+        assert W[j] == Fr(c6.get(j, 0), 24), j
+
+
 def test_generated_header_is_current():
     """nodal_o4_coeffs.cuh is exactly what gen_nodal_o4.py emits."""
     import importlib.util
