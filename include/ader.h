@@ -153,11 +153,10 @@ int ader_profile_read(ader_ctx* ctx, const char** names, int* launches, double* 
 int ader_set_predictor(ader_ctx* ctx, double tol, int max_iter);
 int ader_predictor_stats(ader_ctx* ctx, unsigned long long* out3_host, void* stream);
 
-/* Non-stiff source term S(U) of Eq. 4 (Sec. II; orders 2 and 3, modal and
- * nodal; order 4, nodal).  The paper carries a general S through the
- * predictor (Eqs. 30, 34, 36, 43; A.4, B.2-B.3, C.2-C.3) and the update
- * (Eq. 6 with S-bar of Eqs. 35, 44; A.7, B.6, C.6) without naming one; two
- * models are built:
+/* Non-stiff source term S(U) of Eq. 4 (Sec. II; orders 2-4, modal and
+ * nodal).  The paper carries a general S through the predictor (Eqs. 30, 34,
+ * 36, 43, 45, 52; A.4, B.2-B.3, C.2-C.3) and the update (Eq. 6 with S-bar of
+ * Eqs. 35, 44, 53; A.7, B.6, C.6) without naming one; two models are built:
  *   ADER_SOURCE_LINEAR:  S = -k U on the five hydrodynamic variables,
  *                        params[0] = k;
  *   ADER_SOURCE_GRAVITY: S = (0, rho g, rho v . g), params[0..2] = g.
@@ -166,8 +165,7 @@ int ader_predictor_stats(ader_ctx* ctx, unsigned long long* out3_host, void* str
  * source polynomial of the final iterate.  params is a host array (1 or 3
  * doubles, copied); ADER_SOURCE_NONE (params may be NULL) removes the source.
  * The first source allocates a per-zone buffer (5 x zones, bulk precision).
- * Returns ADER_ERR_ARG for an unknown kind, non-finite parameters or an
- * order-4 modal context.  ader_rk_step refuses a context with a source, and the
+ * Returns ADER_ERR_ARG for an unknown kind or non-finite parameters.  ader_rk_step refuses a context with a source, and the
  * learned-guess samples (ader_guess_samples) are taken without it. */
 #define ADER_SOURCE_NONE 0
 #define ADER_SOURCE_LINEAR 1

@@ -483,8 +483,6 @@ int ader_set_source(ader_ctx* c, int kind, const double* params) {
         return ADER_OK;
     }
     if (kind != ADER_SOURCE_LINEAR && kind != ADER_SOURCE_GRAVITY) return fail(c, ADER_ERR_ARG, "unknown source kind");
-    if (c->order == 4 && !(c->flags & ADER_NODAL))
-        return fail(c, ADER_ERR_ARG, "source terms at fourth order are built for the nodal form");
     if (!params) return fail(c, ADER_ERR_ARG, "null source parameters");
     const int np = kind == ADER_SOURCE_LINEAR ? 1 : 3;
     double par[3] = {0.0, 0.0, 0.0};

@@ -39,7 +39,7 @@ struct StepArgs {
     void* ZB;           // MHD: zone-averaged B from the face-B WENO (3 x N, R)
     void* E;            // MHD: edge EMFs Ex, Ey, Ez (3 x N, R)
     const float* Uf;    // FP32 bulk: the state rounded to FP32 once per step (5 x N), read by the WENO
-    int src_kind;       // SOURCE_NONE / SOURCE_LINEAR / SOURCE_GRAVITY (orders 2 and 3)
+    int src_kind;       // SOURCE_NONE / SOURCE_LINEAR / SOURCE_GRAVITY
     double src_par[3];  // k (linear) or g (gravity)
     void* Sb;           // with a source: dt S-bar of Eq. 6 per zone (5 x N, R), written by the predictor
 };

@@ -10,8 +10,12 @@ namespace o4 {
 
 
 // ------------------------------------------------------------------ modal, Sec. IV.3
-template <int NV, class R>
-ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl) {
+// SRC: with a non-stiff source (s = dt S at every node of Eq. 46 of the current iterate; the source
+// modes by Eqs. 49-51 with f, g, h -> s and Eq. 52; Eq. 45 with its source terms); sdt receives dt S-bar
+// of Eq. 53 from the final iterate.
+template <int NV, class R, bool SRC = false>
+ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>* src = nullptr,
+                            Vec<NV, R>* sdt = nullptr) {
     // Eq. 47: the 21 tau = 0 nodes of Eq. 46
     Vec<NV, R> u[22];
     u[1] = m[1] - (m[5] + m[6] + m[7]) / 12.0;
@@ -91,20 +95,70 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
         PH16 = 0.5 * (hq1 - hq2) - 2.0 * (h[2] - h[5]);
         QH56 = hq5 - hq6;
     }
-    // Eq. 45 without sources: the modes fed by tau = 0 fluxes only
-    const Vec<NV, R> e21 = -(scale(cx, F2 + 0.1 * F11) + scale(cy, G3 + 0.1 * G12) + scale(cz, H4 + 0.1 * H13));
-    const Vec<NV, R> e24 = -(scale(cx, 2.0 * F5) + scale(cy, G8) + scale(cz, H10));
-    const Vec<NV, R> e25 = -(scale(cx, F8) + scale(cy, 2.0 * G6) + scale(cz, H9));
-    const Vec<NV, R> e26 = -(scale(cx, F10) + scale(cy, G9) + scale(cz, 2.0 * H7));
-
-    const bool conv = ctl.tol > 0.0;
-    const int cap = conv ? ctl.max_iter : ctl.n_iter;
-    const R ref = max_abs(m[1]) + R(1e-300);
-    ctl.iters = 0;
-    ctl.capped = conv;
-    for (int it = 0; it < cap; ++it) {
-        // Eq. 48: nodes 23..41 of Eq. 46 (22 and 42 serve only source terms)
-        Vec<NV, R> w[42];
+    // source modes from the tau = 0 nodes (Eqs. 49-52 with f, g, h -> s), built once
+    Vec<NV, R> s1, S1, S2, S3, S4, S5, S6, S7, S8, S9, S10, PS14, PS15, PS16, QS12, QS34, QS56;
+    if constexpr (SRC) {
+        Vec<NV, R> sn[22];
+#pragma unroll
+        for (int k = 1; k <= 21; ++k) sn[k] = source_at(u[k], *src);
+        const Vec<NV, R> a1 = sn[14] + sn[15] + sn[16] + sn[17], a2 = sn[18] + sn[19] + sn[20] + sn[21];
+        const Vec<NV, R> a3 = sn[14] + sn[16] + sn[18] + sn[20], a4 = sn[15] + sn[17] + sn[19] + sn[21];
+        const Vec<NV, R> a5 = sn[14] + sn[15] + sn[18] + sn[19], a6 = sn[16] + sn[17] + sn[20] + sn[21];
+        s1 = sn[1];
+        S5 = 2.0 * (sn[2] - 2.0 * sn[1] + sn[5]);
+        S6 = 2.0 * (sn[6] - 2.0 * sn[1] + sn[9]);
+        S7 = 2.0 * (sn[10] - 2.0 * sn[1] + sn[13]);
+        S8 = 0.5 * (sn[14] - sn[15] + sn[16] - sn[17] - sn[18] + sn[19] - sn[20] + sn[21]);
+        S9 = 0.5 * (sn[14] - sn[15] - sn[16] + sn[17] + sn[18] - sn[19] - sn[20] + sn[21]);
+        S10 = 0.5 * (sn[14] + sn[15] - sn[16] - sn[17] - sn[18] - sn[19] + sn[20] + sn[21]);
+        const Vec<NV, R> S11 = (16.0 / 3.0) * (sn[2] - 2.0 * sn[3] + 2.0 * sn[4] - sn[5]);
+        const Vec<NV, R> S12 = (16.0 / 3.0) * (sn[6] - 2.0 * sn[7] + 2.0 * sn[8] - sn[9]);
+        const Vec<NV, R> S13 = (16.0 / 3.0) * (sn[10] - 2.0 * sn[11] + 2.0 * sn[12] - sn[13]);
+        S2 = (2.0 / 3.0) * (sn[2] - sn[5]) - 0.1 * S11 + (a1 - a2) / 12.0;
+        S3 = (2.0 / 3.0) * (sn[6] - sn[9]) - 0.1 * S12 + (a3 - a4) / 12.0;
+        S4 = (2.0 / 3.0) * (sn[10] - sn[13]) - 0.1 * S13 + (a5 - a6) / 12.0;
+        PS14 = 0.5 * (a3 - a4) - 2.0 * (sn[6] - sn[9]);
+        PS15 = 0.5 * (a5 - a6) - 2.0 * (sn[10] - sn[13]);
+        PS16 = 0.5 * (a1 - a2) - 2.0 * (sn[2] - sn[5]);
+        QS12 = a1 - a2;
+        QS34 = a3 - a4;
+        QS56 = a5 - a6;
+        S1 = 0.125 * (a1 + a2) - (S5 + S6 + S7) / 6.0;
+    }
+    // the time modes of the source (Eqs. 49-52 with f, g, h -> s) from the nodes 22..42 of an iterate
+    auto time_source_modes = [&](const Vec<NV, R>* w, Vec<NV, R>* T) {
+        Vec<NV, R> sw[43];
+#pragma unroll
+        for (int k = 22; k <= 42; ++k) sw[k] = source_at(w[k], *src);
+        const Vec<NV, R> q7 = sw[23] + sw[24] - sw[25] - sw[26] - sw[27] - sw[28] + sw[29] + sw[30];
+        const Vec<NV, R> q8 = sw[23] + sw[27] - sw[24] - sw[28] - sw[31] - sw[33] + sw[32] + sw[34];
+        const Vec<NV, R> q9 = sw[25] + sw[29] - sw[26] - sw[30] - sw[31] - sw[32] + sw[33] + sw[34];
+        const Vec<NV, R> q10 = sw[23] + sw[24] + sw[25] + sw[26] - sw[27] - sw[28] - sw[29] - sw[30];
+        const Vec<NV, R> q11 = sw[23] - sw[24] + sw[27] - sw[28] + sw[31] - sw[32] + sw[33] - sw[34];
+        const Vec<NV, R> q12 = sw[25] - sw[26] + sw[29] - sw[30] + sw[31] + sw[32] - sw[33] - sw[34];
+        const Vec<NV, R> S16 = q7 + PS16, S18 = -2.0 * q7 + S16;
+        const Vec<NV, R> S14 = q8 + PS14, S19 = -2.0 * q8 + S14;
+        const Vec<NV, R> S15 = q9 + PS15, S17 = -2.0 * q9 + S15;
+        // T[k - 21] = s mode k for k = 21..35
+        T[6] = 1.125 * QS12 + 4.5 * (sw[36] - sw[37]) - 2.25 * q10;                               // 27
+        T[3] = 3.0 * (sw[36] - sw[37]) - 0.75 * q10 + 0.375 * (S16 + S18) - T[6];                // 24
+        T[7] = 1.125 * QS34 + 4.5 * (sw[38] - sw[39]) - 2.25 * q11;                               // 28
+        T[4] = 3.0 * (sw[38] - sw[39]) - 0.75 * q11 + 0.375 * (S14 + S19) - T[7];                // 25
+        T[8] = 1.125 * QS56 + 4.5 * (sw[40] - sw[41]) - 2.25 * q12;                               // 29
+        T[5] = 3.0 * (sw[40] - sw[41]) - 0.75 * q12 + 0.375 * (S15 + S17) - T[8];                // 26
+        T[9] = 3.0 * (sw[36] - 2.0 * sw[35] + sw[37]) - 1.5 * S5;                                // 30
+        T[10] = 3.0 * (sw[38] - 2.0 * sw[35] + sw[39]) - 1.5 * S6;                               // 31
+        T[11] = 3.0 * (sw[40] - 2.0 * sw[35] + sw[41]) - 1.5 * S7;                               // 32
+        T[12] = 3.0 * (sw[23] - sw[27] - sw[24] + sw[28]) - 3.0 * S8;                            // 33
+        T[13] = 3.0 * (sw[31] - sw[32] - sw[33] + sw[34]) - 3.0 * S9;                            // 34
+        T[14] = 3.0 * (sw[25] - sw[29] - sw[26] + sw[30]) - 3.0 * S10;                           // 35
+        T[2] = 4.5 * (sw[42] - s1) - 13.5 * (sw[35] - sw[22]);                                   // 23 (Eq. 52)
+        T[1] = 2.25 * (s1 - sw[22] - sw[35] + sw[42]) - 1.5 * T[2];                              // 22
+        T[0] = sw[42] - s1 - T[1] - T[2] + (T[9] + T[10] + T[11]) / 12.0;                        // 21
+    };
+    // Eq. 48: the tau > 0 nodes 22..41 of Eq. 46 of the current iterate (22 and 42 serve only source
+    // terms; 42 = (0, 0, 0, 1) only with a source)
+    auto build_w = [&](Vec<NV, R>* w) {
         w[22] = u[1] + (36.0 * m[21] + 12.0 * m[22] + 4.0 * m[23] - 3.0 * m[30] - 3.0 * m[31] - 3.0 * m[32]) / 108.0;
         w[23] = w[22] + u[2] + u[6] - 2.0 * u[1] +
                 (18.0 * m[8] + 9.0 * m[14] + 9.0 * m[16] + 12.0 * m[24] + 12.0 * m[25] + 4.0 * m[27] + 4.0 * m[28] +
@@ -137,6 +191,22 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
         w[39] = u[9] + r1 - r4 + r5;
         w[40] = u[10] + r1 + r6 + r7;
         w[41] = u[13] + r1 - r6 + r7;
+        if constexpr (SRC) w[42] = u[1] + m[21] + m[22] + m[23] - (m[30] + m[31] + m[32]) / 12.0;   // (0, 0, 0, 1)
+    };
+    // Eq. 45 without sources: the modes fed by tau = 0 fluxes only
+    const Vec<NV, R> e21 = -(scale(cx, F2 + 0.1 * F11) + scale(cy, G3 + 0.1 * G12) + scale(cz, H4 + 0.1 * H13));
+    const Vec<NV, R> e24 = -(scale(cx, 2.0 * F5) + scale(cy, G8) + scale(cz, H10));
+    const Vec<NV, R> e25 = -(scale(cx, F8) + scale(cy, 2.0 * G6) + scale(cz, H9));
+    const Vec<NV, R> e26 = -(scale(cx, F10) + scale(cy, G9) + scale(cz, 2.0 * H7));
+
+    const bool conv = ctl.tol > 0.0;
+    const int cap = conv ? ctl.max_iter : ctl.n_iter;
+    const R ref = max_abs(m[1]) + R(1e-300);
+    ctl.iters = 0;
+    ctl.capped = conv;
+    for (int it = 0; it < cap; ++it) {
+        Vec<NV, R> w[43];
+        build_w(w);
         // fluxes at nodes 23..35 (all three directions) and the axis nodes 36..41
         Vec<NV, R> f[36], g[36], h[36];
 #pragma unroll
@@ -220,6 +290,25 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
         n[12] = -(scale(cx, 2.0 * F14) + scale(cy, 2.0 * G16) + scale(cz, H20));
         n[13] = -(scale(cx, F20) + scale(cy, 2.0 * G17) + scale(cz, 2.0 * H19));
         n[14] = -(scale(cx, 2.0 * F15) + scale(cy, G20) + scale(cz, 2.0 * H18));
+        if constexpr (SRC) {        // Eq. 45, source terms
+            Vec<NV, R> T[15];
+            time_source_modes(w, T);
+            n[0] += S1 + (8.0 / 70.0) * T[2];
+            n[1] += 0.5 * T[0] - (3.0 / 7.0) * T[2];
+            n[2] += T[1] / 3.0 + (4.0 / 7.0) * T[2];
+            n[3] += S2 - 0.3 * T[6];
+            n[4] += S3 - 0.3 * T[7];
+            n[5] += S4 - 0.3 * T[8];
+            n[6] += 0.5 * T[3] + 0.6 * T[6];
+            n[7] += 0.5 * T[4] + 0.6 * T[7];
+            n[8] += 0.5 * T[5] + 0.6 * T[8];
+            n[9] += S5 + (2.0 / 3.0) * T[9];
+            n[10] += S6 + (2.0 / 3.0) * T[10];
+            n[11] += S7 + (2.0 / 3.0) * T[11];
+            n[12] += S8 + (2.0 / 3.0) * T[12];
+            n[13] += S9 + (2.0 / 3.0) * T[13];
+            n[14] += S10 + (2.0 / 3.0) * T[14];
+        }
         R change = R(0);
 #pragma unroll
         for (int k = 0; k < 15; ++k) {
@@ -232,6 +321,18 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
             break;
         }
     }
+    if constexpr (SRC) {            // Eq. 53 from the source at the final iterate (times dt)
+        Vec<NV, R> w[43], T[15];
+        build_w(w);
+        time_source_modes(w, T);
+        *sdt = S1 + 0.5 * T[0] + T[1] / 3.0 + 0.25 * T[2];
+    }
+}
+
+template <int NV, class R>
+ADER_DEV void predict_modal_src(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl, const Src<R>& src,
+                                Vec<NV, R>& sdt) {
+    predict_modal<NV, R, true>(m, gm1, cx, cy, cz, ctl, &src, &sdt);
 }
 
 // ------------------------------------------------------------------ nodal, App. C
@@ -509,12 +610,8 @@ ADER_DEV void edge_states(const Vec<8, R>* p, const Vec<8, R>& ub, const Vec<8, 
     e[3] = u2 - q2;
 }
 
-// Source terms at this order: nodal only (the modal form's source modes of Eqs. 49-52 are not built;
-// an order-4 modal context refuses a source).
 constexpr bool HAS_SOURCE = true;
-constexpr bool HAS_SOURCE_MODAL = false;
-template <int NV, class R>
-ADER_DEV void predict_modal_src(Vec<NV, R>*, R, R, R, R, PredCtl&, const Src<R>&, Vec<NV, R>&) {}
+constexpr bool HAS_SOURCE_MODAL = true;
 
 // No paired-face form at this order: the faces are evaluated one at a time.
 constexpr bool HAS_FACE_PAIR = false;
