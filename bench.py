@@ -642,7 +642,10 @@ def gpu_arm(args):
     fpz["learned_guess"] = 2.0 * (52 * 128 + 128 * 128 + 128 * 25)       # the MLP's multiply-adds per zone
     kname, (kl, kms) = max(((k, v) for k, v in prof.items()), key=lambda kv: kv[1][1])
     k_avg = kms / kl / 1e3
-    achieved = fpz[kname] * zones / k_avg / 1e12 if kname in fpz else None
+    units = zones
+    if kname == "learned_guess":      # the network runs only on the zones with slopes
+        units = ader.ader_guess_count(s.h, stream)
+    achieved = fpz[kname] * units / k_avg / 1e12 if kname in fpz else None
     sm_mhz = ck.get("sm_mhz") or 2070.0
     if kname == "learned_guess":
         bound, peak = "tensor", peaks().get("bf16_tflops", 1940.9)
@@ -656,11 +659,12 @@ def gpu_arm(args):
                 "frac": achieved / peak if achieved else None,
                 "traffic": traffic_per_launch(kname, args.order, args.form, args.fp32, zones),
                 "peak_basis": basis,
-                "flops_per_zone": fpz.get(kname), "mean_launch_ms": k_avg * 1e3,
+                "flops_per_zone": fpz.get(kname), "zones_per_launch": units, "mean_launch_ms": k_avg * 1e3,
                 "kernel_share": {k: round(v[1] / total_ms, 4) for k, v in prof.items()},
                 "hbm": {"algorithmic_bytes_per_zone_update": 80,
                         "achieved_gbs": 80.0 * zones * args.steps / secs / 1e9,
                         "peak_gbs": peaks().get("hbm_gbs"), "frac": 80.0 * zones * args.steps / secs / 1e9 / peaks().get("hbm_gbs", 6658.3)}}
+    guess_zones = ader.ader_guess_count(s.h, stream) if guess is not None else None
     s.close()
     del d
 
@@ -740,6 +744,7 @@ def gpu_arm(args):
                            "precision": "fp32 bulk + fp64 update" if args.fp32 else "fp64",
                            "predictor": ("converged, tol %g" % tol if tol else "fixed M-1 iterations") +
                                         (", learned initial guess" if guess is not None else ""),
+                           "learned_guess_zones_per_step": guess_zones,
                            "l2": "state 671 MB > L2 129 MB (no flush needed)",
                            "parallelism": "independent problem per GPU" if world > 1 else "single GPU"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps,

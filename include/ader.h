@@ -176,10 +176,13 @@ int ader_set_source(ader_ctx* ctx, int kind, const double* params);
  * starts its Picard iteration of Sec. IV from zero).  params (device, FP32,
  * layout and size from ader_mlp_shape) is an MLP mapping a zone's normalised
  * spatial modes and Courant numbers to its evolutionary modes; each step then
- * runs one more kernel that writes every zone's guess, and the predictor
- * starts from it instead of zero.  The first non-NULL call allocates that
- * per-zone buffer (5 x nvar x zones FP32, held by the context); NULL disables
- * the guess.  The pointer is kept, not copied: keep the buffer alive while the
+ * runs two more kernels: one lists the zones that carry slopes (the guess of
+ * a zone whose slope magnitude is below 1e-12 is exactly zero), the other
+ * runs the network on those zones only, and the predictor starts from the
+ * guess instead of zero.  The first non-NULL call allocates the per-zone
+ * buffers (the guess, 5 x nvar x zones FP32; the list and flags, 5 bytes per
+ * zone; held by the context); NULL disables the guess.  Grids of 2^31 zones
+ * or more return ADER_ERR_ARG.  The pointer is kept, not copied: keep the buffer alive while the
  * context uses it.  With the fixed iteration count the guess changes the
  * result; with ader_set_predictor's tolerance it only changes the work. */
 int ader_set_guess(ader_ctx* ctx, const float* params);
@@ -189,6 +192,10 @@ int ader_set_guess(ader_ctx* ctx, const float* params);
  * layers on the tensor cores (tcgen05, FP16 operands, FP32 accumulation).
  * Needs ader_set_guess first.  Asynchronous on the stream. */
 int ader_guess_eval(ader_ctx* ctx, const double* U, const double* Bface, double dt, float* G, void* stream);
+/* The number of zones the network ran on in the context's last guess launch
+ * (the zones with slopes), to *out_host; synchronises the stream.  0 before
+ * the first launch or without a guess. */
+int ader_guess_count(ader_ctx* ctx, unsigned long long* out_host, void* stream);
 int ader_mlp_shape(int mhd, int* n_in, int* n_hidden, int* n_out, long long* n_params);
 
 /* Training data: for every zone of (U, Bface), the MLP features X (n x n_in)

@@ -20,7 +20,7 @@ ADER_SOURCE_NONE, ADER_SOURCE_LINEAR, ADER_SOURCE_GRAVITY = 0, 1, 2
 EXPORTS = ("ader_create", "ader_step", "ader_step_devdt", "ader_max_dt", "ader_rk_step", "ader_step_host",
            "ader_diagnostics", "ader_sync_status", "ader_launches_per_step", "ader_profile", "ader_profile_reset",
            "ader_profile_read", "ader_set_predictor", "ader_predictor_stats", "ader_set_source", "ader_set_guess",
-           "ader_mlp_shape", "ader_guess_samples", "ader_guess_eval", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy",
+           "ader_mlp_shape", "ader_guess_samples", "ader_guess_count", "ader_guess_eval", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy",
            "ader_max_dt_static", "ader_batch_create", "ader_batch_tune", "ader_batch_step", "ader_batch_advance",
            "ader_batch_status", "ader_batch_tuning", "ader_batch_groups", "ader_batch_last_error",
            "ader_batch_destroy")
@@ -67,6 +67,7 @@ def load(path=None):
     lib.ader_predictor_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), vp]
     lib.ader_set_guess.argtypes = [vp, vp]
     lib.ader_set_source.argtypes = [vp, ctypes.c_int, vp]
+    lib.ader_guess_count.argtypes = [vp, vp, vp]
     lib.ader_mlp_shape.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(ctypes.c_longlong)]
     lib.ader_guess_samples.argtypes = [vp, vp, vp, dbl, vp, vp, vp, vp]
@@ -211,6 +212,13 @@ def ader_set_source(h, kind, params=None):
         vals = [float(v) for v in params]
         arr = (ctypes.c_double * len(vals))(*vals)
     return _check(h, load().ader_set_source(h, int(kind), arr))
+
+
+def ader_guess_count(h, stream=None):
+    """Zones the network ran on in the last guess launch (synchronises the stream)."""
+    out = ctypes.c_ulonglong()
+    _check(h, load().ader_guess_count(h, ctypes.byref(out), _stream(stream)))
+    return int(out.value)
 
 
 def ader_set_guess(h, params):

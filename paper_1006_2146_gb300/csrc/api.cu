@@ -39,6 +39,9 @@ struct ader_ctx {
     unsigned long long* stats = nullptr;      // converged predictor statistics (3 words)
     const float* guess = nullptr;             // learned-guess MLP parameters (device), order 3
     float* G = nullptr;                       // per-zone learned guess (5 x NV x N FP32), allocated by ader_set_guess
+    int* Glist = nullptr;                     // the zones with slopes (N), their count and per-zone flags,
+    unsigned* Gcount = nullptr;               // allocated with G
+    unsigned char* Gact = nullptr;
     float* Uf = nullptr;                      // FP32 bulk: the state rounded to FP32 (5 x N), rewritten each step
     int src_kind = SOURCE_NONE;               // non-stiff source (ader_set_source)
     double src_par[3] = {0.0, 0.0, 0.0};
@@ -126,6 +129,9 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.stats = c->stats;
     a.guess = n_iter > 0 ? c->guess : nullptr;
     a.G = a.guess ? c->G : nullptr;
+    a.Glist = c->Glist;
+    a.Gcount = c->Gcount;
+    a.Gact = a.G ? c->Gact : nullptr;
     a.src_kind = n_iter > 0 ? c->src_kind : SOURCE_NONE;
     for (int i = 0; i < 3; ++i) a.src_par[i] = c->src_par[i];
     a.Sb = a.src_kind != SOURCE_NONE ? c->Sb : nullptr;
@@ -141,7 +147,7 @@ static int enqueue_faces(ader_ctx* c, const StepArgs& a, const double* U, cudaSt
     }
     if (a.G) {
         Trace t(c, "learned_guess", st);
-        const int k = launch_guess<R>(a, U, st);
+        const int k = launch_guess<R>(a, U, st, nullptr);
         if (k < 0)
             c->setup_failed = true;       // reported by the caller
         else
@@ -241,7 +247,8 @@ void ader_destroy(ader_ctx* c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->spare) cudaEventDestroy(e);
-    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Uf, c->Sb, c->flag, c->stats, c->dtscr, c->partial, c->dt_dev,
+    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Glist, c->Gact, c->Gcount, c->Uf, c->Sb, c->flag,
+                    c->stats, c->dtscr, c->partial, c->dt_dev,
                     c->Ustage, c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6],
                     c->rkB[0], c->rkB[1], c->rkB[2], c->rkB[3], c->rkB[4], c->rkB[5]};
     for (void* p : ptrs)
@@ -502,9 +509,16 @@ int ader_set_source(ader_ctx* c, int kind, const double* params) {
 int ader_set_guess(ader_ctx* c, const float* params) {
     if (!c) return ADER_ERR_ARG;
     if (params && c->order != 3) return fail(c, ADER_ERR_ARG, "the learned guess is built for third order");
+    if (params && c->grid.n >= (1ll << 31)) return fail(c, ADER_ERR_ARG, "the learned guess takes up to 2^31 - 1 zones");
     if (params && !c->G) {
-        const size_t bytes = (size_t)5 * (c->mhd ? 8 : 5) * (size_t)c->grid.n * sizeof(float);
+        const size_t N = (size_t)c->grid.n;
+        const size_t bytes = (size_t)5 * (c->mhd ? 8 : 5) * N * sizeof(float);
         if (int rc = cuda_check(c, cudaMalloc((void**)&c->G, bytes), "cudaMalloc learned guess")) return rc;
+        if (int rc = cuda_check(c, cudaMalloc((void**)&c->Glist, N * sizeof(int)), "cudaMalloc guess list")) return rc;
+        if (int rc = cuda_check(c, cudaMalloc((void**)&c->Gact, N), "cudaMalloc guess flags")) return rc;
+        if (int rc = cuda_check(c, cudaMalloc((void**)&c->Gcount, sizeof(unsigned)), "cudaMalloc guess count"))
+            return rc;
+        if (int rc = cuda_check(c, cudaMemset(c->Gcount, 0, sizeof(unsigned)), "cudaMemset guess count")) return rc;
     }
     c->guess = params;
     return ADER_OK;
@@ -522,12 +536,24 @@ int ader_guess_eval(ader_ctx* c, const double* U, const double* Bface, double dt
     a.G = G;
     if (c->fp32) {
         launch_recon<float>(a, U, st);
-        if (launch_guess<float>(a, U, st) < 0) return fail(c, ADER_ERR_CUDA, "guess kernel set-up");
+        if (launch_guess<float>(a, U, st, G) < 0) return fail(c, ADER_ERR_CUDA, "guess kernel set-up");
     } else {
         launch_recon<double>(a, U, st);
-        if (launch_guess<double>(a, U, st) < 0) return fail(c, ADER_ERR_CUDA, "guess kernel set-up");
+        if (launch_guess<double>(a, U, st, G) < 0) return fail(c, ADER_ERR_CUDA, "guess kernel set-up");
     }
     return cuda_check(c, cudaGetLastError(), "ader_guess_eval launch");
+}
+
+int ader_guess_count(ader_ctx* c, unsigned long long* out_host, void* stream) {
+    if (!c || !out_host) return ADER_ERR_ARG;
+    *out_host = 0;
+    if (!c->Gcount) return ADER_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned n = 0;
+    int rc = cuda_check(c, cudaMemcpyAsync(&n, c->Gcount, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "count read");
+    if (rc == ADER_OK) rc = cuda_check(c, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (rc == ADER_OK) *out_host = n;
+    return rc;
 }
 
 int ader_guess_samples(ader_ctx* c, const double* U, const double* Bface, double dt, float* X, float* Y, int* ok,

@@ -223,7 +223,8 @@ __global__ void __launch_bounds__(TM * GROUPS, 1) k_guess_tc(StepArgs a, const d
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
     const float cx = (float)(dt * a.idx[0]), cy = (float)(dt * a.idx[1]), cz = (float)(dt * a.idx[2]);
     const long long N = a.grid.n;
-    const long long ntiles = (N + TM - 1) / TM;
+    const long long cnt = *a.Gcount;                  // the zones with slopes (k_guess_compact)
+    const long long ntiles = (cnt + TM - 1) / TM;
     uint32_t parity = 0;
     bool timed_out = false;
     auto sync_mma = [&]() -> bool {          // the group waits for its committed layer
@@ -239,14 +240,14 @@ __global__ void __launch_bounds__(TM * GROUPS, 1) k_guess_tc(StepArgs a, const d
         fence_after();
     };
     for (long long t = (long long)blockIdx.x * GROUPS + g; t < ntiles; t += (long long)gridDim.x * GROUPS) {
-        const long long z = t * TM + row;
+        const long long z = t * TM + row < cnt ? (long long)a.Glist[t * TM + row] : -1;
         float sv[NV] = {};
         bool act = false;
         {
             float x[K1];
 #pragma unroll
             for (int k = 0; k < K1; ++k) x[k] = 0.f;
-            if (z < N) {
+            if (z >= 0) {
                 Vec<NV, R> m[11];
                 load_modes<3>(a, U, z, m);
                 const float mag = guess_features_f32<NV, R>(m, cx, cy, cz, x, sv);
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(TM * GROUPS, 1) k_guess_tc(StepArgs a, const d
         for (int c = 0; c < N3; c += 16) {
             float v[16];
             tmem_ld16(tlane + (uint32_t)c, v);
-            if (z < N) {
+            if (z >= 0) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int o = c + j;
@@ -316,8 +317,36 @@ __global__ void __launch_bounds__(TM * GROUPS, 1) k_guess_tc(StepArgs a, const d
                      : "memory");
 }
 
+// The zones whose guess is not exactly zero: a zone runs the network only when its slope magnitude g
+// exceeds GUESS_MAG_MIN (below it the guess is zero by definition).  Each zone writes its flag; the
+// zones with slopes get a slot in the list (warp-aggregated atomics: the order of the list is not
+// fixed, each zone's guess is its own).  Gzero (non-null for ader_guess_eval) receives the zero guess of
+// every other zone; the step's predictor reads the flag instead.
 template <int NV, class R>
-int launch_nv(const StepArgs& a, const double* U, cudaStream_t st) {
+__global__ void __launch_bounds__(256) k_guess_compact(StepArgs a, const double* __restrict__ U, float* Gzero) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool act = false;
+    if (z < a.grid.n) {
+        Vec<NV, R> m[11];
+        load_modes<3>(a, U, z, m);
+        act = guess_mag_f32<NV, R>(m) > (float)GUESS_MAG_MIN;
+        a.Gact[z] = act ? 1 : 0;
+        if (!act && Gzero) {
+#pragma unroll
+            for (int o = 0; o < 5 * NV; ++o) Gzero[(long long)o * a.grid.n + z] = 0.f;
+        }
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, act);
+    if (ballot == 0u) return;
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == __ffs(ballot) - 1) base = atomicAdd(a.Gcount, (unsigned)__popc(ballot));
+    base = __shfl_sync(0xffffffffu, base, __ffs(ballot) - 1);
+    if (act) a.Glist[base + __popc(ballot & ((1u << lane) - 1u))] = (int)z;
+}
+
+template <int NV, class R>
+int launch_nv(const StepArgs& a, const double* U, cudaStream_t st, float* Gzero) {
     static int max_blocks_dev[64] = {};     // per instantiation and device: resident CTAs per SM x SMs
     const size_t smem = sizeof(TcSmem<NV>) + 1024;
     int cur = 0;
@@ -340,21 +369,24 @@ int launch_nv(const StepArgs& a, const double* U, cudaStream_t st) {
         (void)smem_sm;
         max_blocks = sms;
     }
+    if (cudaMemsetAsync(a.Gcount, 0, sizeof(unsigned), st) != cudaSuccess) return -1;
+    k_guess_compact<NV, R><<<(unsigned)((a.grid.n + 255) / 256), 256, 0, st>>>(a, U, Gzero);
+    // the count lives on the device: one persistent CTA per SM walks the list's tiles
     const long long tiles = (a.grid.n + TM - 1) / TM;
     const long long want = (tiles + GROUPS - 1) / GROUPS;
     const unsigned blocks = (unsigned)(want < max_blocks ? want : max_blocks);
     k_guess_tc<NV, R><<<blocks, TM * GROUPS, smem, st>>>(a, U);
-    return 1;
+    return 2;
 }
 
 }  // namespace
 
 template <class R>
-int launch_guess(const StepArgs& a, const double* U, cudaStream_t st) {
-    return a.mhd ? launch_nv<8, R>(a, U, st) : launch_nv<5, R>(a, U, st);
+int launch_guess(const StepArgs& a, const double* U, cudaStream_t st, float* Gzero) {
+    return a.mhd ? launch_nv<8, R>(a, U, st, Gzero) : launch_nv<5, R>(a, U, st, Gzero);
 }
 
-template int launch_guess<double>(const StepArgs&, const double*, cudaStream_t);
-template int launch_guess<float>(const StepArgs&, const double*, cudaStream_t);
+template int launch_guess<double>(const StepArgs&, const double*, cudaStream_t, float*);
+template int launch_guess<float>(const StepArgs&, const double*, cudaStream_t, float*);
 
 }  // namespace ader

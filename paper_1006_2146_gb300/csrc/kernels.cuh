@@ -23,6 +23,9 @@ struct StepArgs {
     const float* guess; // learned initial guess: packed MLP weights (order 3), or null
     float* G;           // learned initial guess per zone: u_11..u_15 (5 x NV x N, FP32), written by the
                         // guess kernel and read by the predictor; null = start from zero
+    int* Glist;         // with a guess: the zones that carry slopes (the only ones the network runs on),
+    unsigned* Gcount;   // their number (device), and a per-zone flag the predictor reads before G;
+    unsigned char* Gact;    // a zone without the flag starts from zero (its guess is exactly zero)
     double gamma;
     double dx[3];
     double idx[3];      // 1 / dx, computed once on the host
@@ -96,7 +99,7 @@ int launch_max_dt(const Grid& g, const double* U, const double* Bf, double gamma
 template <class R> int launch_emf_ct(const StepArgs& a, double* Bf, double c_host, bool use_dt_dev, cudaStream_t st);
 int launch_guess_samples(const StepArgs& a, const double* U, float* X, float* Y, int* ok, cudaStream_t st);
 // learned guess of every zone into a.G (order 3; after launch_recon)
-template <class R> int launch_guess(const StepArgs& a, const double* U, cudaStream_t st);
+template <class R> int launch_guess(const StepArgs& a, const double* U, cudaStream_t st, float* Gzero);
 int launch_totals(const Grid& g, const double* U, const double* Bf, const double dx[3], double* totals_dev,
                   double* partial, int nblocks, cudaStream_t st);
 

@@ -102,6 +102,28 @@ ADER_DEV double guess_features(const Vec<NV, R>* m, const GuessScales<NV, R>& g,
     return mag;
 }
 
+// g of guess_features_f32 alone (the same FP32 arithmetic): the slope magnitude that decides whether a
+// zone runs the network; 0 where the scales are not positive.
+template <int NV, class R>
+ADER_DEV float guess_mag_f32(const Vec<NV, R>* m) {
+    const float rho = (float)m[1][0], E = (float)m[1][4];
+    if (!(rho > 0.f) || !(E > 0.f)) return 0.f;
+    const float c = sqrtf(E / rho);
+    float s[NV];
+    s[0] = rho;
+    s[1] = s[2] = s[3] = rho * c;
+    s[4] = E;
+    if constexpr (NV == 8) s[5] = s[6] = s[7] = sqrtf(8.0f * 3.14159265358979f * E);
+    float mag = 0.f;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const float inv = 1.0f / s[v];
+#pragma unroll
+        for (int k = 2; k <= 10; ++k) mag = fmaxf(mag, fabsf((float)m[k][v] * inv));
+    }
+    return mag;
+}
+
 // The same features in FP32 arithmetic (inference: they feed FP16 operands),
 // plus the output scale of each variable, s_v sigma g, in sv.  Returns g, or
 // 0 where the scales are not positive.

@@ -152,7 +152,7 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
     const R cx = dt * arg_idx<R>(a, 0), cy = dt * arg_idx<R>(a, 1), cz = dt * arg_idx<R>(a, 2);
     if (a.n_iter > 0) {      // n_iter = 0: spatial polynomial only (SSP-RK face rule)
         if constexpr (ORDER == 3) {
-            if (a.G) {          // learned initial guess of the evolutionary modes
+            if (a.G && (!a.Gact || a.Gact[z])) {          // learned initial guess of the evolutionary modes
 #pragma unroll
                 for (int j = 0; j < 5; ++j)
 #pragma unroll
