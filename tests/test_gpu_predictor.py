@@ -196,6 +196,7 @@ def test_tensor_core_guess_matches_oracle(ader, trained_guess, fp32):
     G = torch.full((25, n), 7.0, dtype=torch.float32, device="cuda")
     ader.ader_guess_eval(s.h, to_dev(U), None, dt, G)
     assert s.status() == 0
+    active = ader.ader_guess_count(s.h)
     s.close()
     got = G.cpu().numpy().reshape(5, 5, *shape)
     _, W = scheme.zone_state(U, None, 3)
@@ -206,8 +207,10 @@ def test_tensor_core_guess_matches_oracle(ader, trained_guess, fp32):
     w = want.reshape(25, n)
     if fp32:    # FP32 moments of uniform data keep round-off slopes: a guess of that size
         assert np.abs(g[:, ~mask]).max() <= 1e-5 * np.abs(w).max()
+        assert mask.sum() <= active <= n
     else:
         np.testing.assert_array_equal(g[:, ~mask], 0.0)
+        assert active == mask.sum()      # the network ran on the zones with slopes only
     err = np.linalg.norm(g[:, mask] - w[:, mask]) / np.linalg.norm(w[:, mask])
     print("tensor-core guess relative L2 error vs FP64 network: %.3e" % err)
     assert err <= 2e-2
