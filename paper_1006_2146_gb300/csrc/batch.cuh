@@ -57,7 +57,8 @@ ADER_DEV void batch_for(const BatchGroupDev& g, F f) {
 template <int ORDER, class R>
 __global__ void __launch_bounds__(256) kb_face_b(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) {
-        zone_face_b<ORDER, R>(it.a.grid, it.Bf, (R*)it.a.ZB, (R*)it.a.S1, z);
+        const Grid gr = it.a.grid;    // local copies: the loop's stores cannot alias them
+        zone_face_b<ORDER, R>(gr, it.Bf, (R*)it.a.ZB, (R*)it.a.S1, z);
     });
 }
 
@@ -74,20 +75,25 @@ static __global__ void __launch_bounds__(256) kb_to_f32(BatchGroupDev g) {
 template <int ORDER, int NV, class R>
 __global__ void __launch_bounds__(256) kb_weno1d(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) {
-        zone_weno1d<ORDER, NV, R>(it.a.grid, it.a.Uf, (const R*)it.a.ZB, (R*)it.a.S1, z);
+        const Grid gr = it.a.grid;
+        zone_weno1d<ORDER, NV, R>(gr, it.a.Uf, (const R*)it.a.ZB, (R*)it.a.S1, z);
     });
 }
 
 template <int ORDER, int NV, class R>
 __global__ void __launch_bounds__(256) kb_cross1(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) {
-        zone_cross1<ORDER, NV, R>(it.a.grid, (const R*)it.a.S1, (R*)it.a.S2, z);
+        const Grid gr = it.a.grid;
+        zone_cross1<ORDER, NV, R>(gr, (const R*)it.a.S1, (R*)it.a.S2, z);
     });
 }
 
 template <int NV, class R>
 __global__ void __launch_bounds__(256) kb_cross2(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) { zone_cross2<NV, R>(it.a.grid, (R*)it.a.S2, z); });
+    batch_for(g, [](const BatchItem& it, long long z) {
+        const Grid gr = it.a.grid;
+        zone_cross2<NV, R>(gr, (R*)it.a.S2, z);
+    });
 }
 
 // at most 128 zones per block, three blocks per SM (as the single-problem FP32 predictor): the tuner
@@ -96,7 +102,10 @@ constexpr int BATCH_PREDICT_MAX_THREADS = 128;
 
 template <int ORDER, int FORM, int NV, class R>
 __global__ void __launch_bounds__(BATCH_PREDICT_MAX_THREADS, 3) kb_predict_faces(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) { zone_predict_faces<ORDER, FORM, NV, R>(it.a, it.U, z); });
+    batch_for(g, [](const BatchItem& it, long long z) {
+        const StepArgs a = it.a;      // a local copy: the arguments stay in registers across the face stores
+        zone_predict_faces<ORDER, FORM, NV, R>(a, it.U, z);
+    });
 }
 
 // U += dt L(U) in place, dt from the problem's dt_dev (fused fluxes: the FP64 accumulation bounds the
@@ -104,18 +113,25 @@ __global__ void __launch_bounds__(BATCH_PREDICT_MAX_THREADS, 3) kb_predict_faces
 template <int SOLVER, int NV, class R>
 __global__ void __launch_bounds__(256) kb_flux_update(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) {
-        zone_flux_update<SOLVER, NV, R>(it.a, it.U, it.U, 1.0, 1, z);
+        const StepArgs a = it.a;
+        zone_flux_update<SOLVER, NV, R>(a, it.U, it.U, 1.0, 1, z);
     });
 }
 
 template <class R>
 __global__ void __launch_bounds__(256) kb_emf(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) { zone_emf<R>(it.a, z); });
+    batch_for(g, [](const BatchItem& it, long long z) {
+        const StepArgs a = it.a;
+        zone_emf<R>(a, z);
+    });
 }
 
 template <class R>
 __global__ void __launch_bounds__(256) kb_ct(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) { zone_ct<R>(it.a, it.Bf, 1.0, 1, z); });
+    batch_for(g, [](const BatchItem& it, long long z) {
+        const StepArgs a = it.a;
+        zone_ct<R>(a, it.Bf, 1.0, 1, z);
+    });
 }
 
 // Phases of one step, in order; a group runs those that apply to it.
