@@ -245,7 +245,7 @@ def mhd_learned_evaluation(ader, torch, stream, n=128, steps=3, train_n=96):
     linearized solver).  The MHD network is trained first (outside every timed region) on predictor samples
     of the seeded magnetised training states at train_n^3.  Each run starts from the same state, takes one
     warm-up step, then `steps` timed steps of one fixed dt; it reports the mean predictor iterations and,
-    for FP32, the error against the FP64 converged predictor (the judge of the guess's error)."""
+    for FP32, the error against the FP64 converged predictor (the reference for the guess's error)."""
     from paper_1006_2146_gb300 import _lib, inputs, learned
     out = {}
     try:
@@ -469,7 +469,7 @@ def learned_variants(ader, torch, n, U0, stream, steps=3):
 
     The guess is trained first (outside every timed region) on predictor samples of the seeded training
     states at 128^3 (about 10^7 samples).  Each variant is timed like the headline; its state after `steps`
-    steps of one fixed dt is compared with the FP64 converged predictor's (the judge of the guess's error)
+    steps of one fixed dt is compared with the FP64 converged predictor's (the reference for the guess's error)
     and with the FP64 fixed-iteration method.
     """
     from paper_1006_2146_gb300 import learned
