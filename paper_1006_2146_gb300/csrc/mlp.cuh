@@ -3,7 +3,7 @@
 // A small MLP (in -> 128 -> 128 -> out, GELU) maps a zone's normalised
 // spatial modes to its evolutionary modes u11..u15, which then start the
 // Picard iteration instead of zeros; the converged iteration stays the reference
-// of the result.  The normalisation makes the map dimensionless and exact for
+// for the result.  The normalisation makes the map dimensionless and exact for
 // uniform zones:
 //   scales   s_rho = w1(rho), s_E = w1(eps), c = sqrt(s_E / s_rho),
 //            s_m = s_rho c (momentum), s_B = sqrt(8 pi s_E) (field);
