@@ -314,6 +314,35 @@ def mhd_learned_evaluation(ader, torch, stream, n=128, steps=3, train_n=96):
     return out
 
 
+def convergence_variant(ader, torch, sizes=(32, 64, 128), T=0.05):
+    """L1 error of rho on the config-1 density wave (FP64, nodal, HLL, CFL 0.4) at each size and order,
+    and the rates between sizes: the 3-D analogue of the paper's Table IV (whose own setup differs)."""
+    from paper_1006_2146_gb300 import inputs
+    import numpy as np
+    out = {}
+    for order in (2, 3, 4):
+        errs = []
+        for n in sizes:
+            s = ader.Solver((n, n, n), order=order, form="nodal")
+            d = torch.from_numpy(inputs.density_wave(n)).to("cuda")
+            dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+            t = 0.0
+            while t < T - 1e-14:
+                s.max_dt(d, 0.4, dtv)
+                dt = min(float(dtv.item()), T - t)
+                s.step(d, dt)
+                t += dt
+            st = s.status()
+            s.close()
+            exact = torch.from_numpy(inputs.density_wave(n, t=T)[0]).to("cuda")
+            errs.append(float((d[0] - exact).abs().mean()) if st == 0 else None)
+        rates = [float(np.log2(errs[i] / errs[i + 1])) if errs[i] and errs[i + 1] else None
+                 for i in range(len(sizes) - 1)]
+        out["order%d" % order] = {"sizes": list(sizes), "l1_rho": errs, "rates": rates}
+    out["paper_table_iv_rates_64_to_96"] = {"order2": 2.31, "order3": 2.97, "order4": 4.01}
+    return out
+
+
 def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32, 48, 64, 80, 96, 112, 128)):
     """`count` seeded independent problems of uneven cubic sizes (Euler and MHD, orders 2-4, FP32 bulk):
     one tuned batch replayed from a captured graph vs one context per problem launched in sequence.
@@ -708,6 +737,10 @@ def gpu_arm(args):
         variants.update(learned_variants(ader, torch, n, U0, stream))
         variants.update(mhd_variants(ader, torch, stream))
         variants["learned_guess_mhd_ot_128"] = mhd_learned_evaluation(ader, torch, stream)
+        try:
+            variants["density_wave_convergence_fp64"] = convergence_variant(ader, torch)
+        except Exception as exc:
+            variants["density_wave_convergence_fp64"] = {"error": str(exc)[:200]}
         variants["batched_64_problems_fp32"] = batched_variant(ader, torch, stream)
         variants["batched_512_small_problems_fp32"] = batched_variant(ader, torch, stream, count=512,
                                                                       sizes=(16, 24, 32))
