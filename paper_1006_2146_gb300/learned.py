@@ -52,8 +52,10 @@ def mhd_training_states(n, seed=1006100):
     """MHD pairs (U, Bface) of the training mix (gamma 5/3)."""
     rng = np.random.default_rng(seed)
     out = []
-    for k, (amp, b_amp, B0) in enumerate(((0.05, 0.2, 0.5), (0.2, 0.5, 1.0), (0.4, 1.0, 2.0), (0.3, 0.3, 3.0))):
-        out.append(inputs.random_magnetised(n, seed=seed + 1 + k, amp=amp, b_amp=b_amp, B0=B0))
+    for k, (amp, b_amp, B0, P0) in enumerate(((0.05, 0.2, 0.5, 1.0), (0.2, 0.5, 1.0, 1.0), (0.4, 1.0, 2.0, 1.0),
+                                              (0.3, 0.3, 3.0, 1.0), (0.6, 0.6, 1.0, 0.3), (0.8, 1.0, 2.0, 0.2))):
+        # the last two: transonic flow (Mach near 1) at plasma beta of a few
+        out.append(inputs.random_magnetised(n, seed=seed + 1 + k, amp=amp, b_amp=b_amp, B0=B0, P0=P0))
     for ratio, B0 in ((10.0, 1.0), (100.0, 3.0)):
         c = tuple(rng.uniform(0.3, 0.7, 3))
         U = inputs.blast(n, gamma=5.0 / 3.0, p_in=ratio * 0.1, p_out=0.1, radius=rng.uniform(0.05, 0.15), center=c)
