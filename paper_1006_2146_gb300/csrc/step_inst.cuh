@@ -1,6 +1,8 @@
 // Instantiates the predictor + face kernel for one (order, variable count,
 // precision); included by the small step_o*_*.cu translation units so that
-// the build compiles them in parallel.  Expects ADER_ORDER, ADER_NV, ADER_REAL.
+// the build compiles them in parallel.  Expects ADER_ORDER, ADER_NV, ADER_REAL;
+// with ADER_SPLIT_VARIANTS the unit holds only the dispatch and the kernel
+// variants come from units that also define ADER_FORM and ADER_SRC.
 #include "step_kernels.cuh"
 #include "zone_o2.cuh"
 #include "zone_o3.cuh"
@@ -56,7 +58,24 @@ ADER_ZONEOPS(4)
 #endif
 
 #ifdef ADER_ORDER
+#ifdef ADER_FORM
+// a translation unit of one kernel variant (ADER_FORM, ADER_SRC)
+template void launch_pf_variant<ADER_ORDER, ADER_FORM, ADER_NV, ADER_REAL, ADER_SRC>(const StepArgs&, const double*,
+                                                                                     cudaStream_t);
+#else
+#ifdef ADER_SPLIT_VARIANTS
+// the variants are compiled in their own translation units (step_o*_*_<form>_<src>.cu)
+extern template void launch_pf_variant<ADER_ORDER, FORM_MODAL, ADER_NV, ADER_REAL, false>(const StepArgs&,
+                                                                                          const double*, cudaStream_t);
+extern template void launch_pf_variant<ADER_ORDER, FORM_NODAL, ADER_NV, ADER_REAL, false>(const StepArgs&,
+                                                                                          const double*, cudaStream_t);
+extern template void launch_pf_variant<ADER_ORDER, FORM_MODAL, ADER_NV, ADER_REAL, true>(const StepArgs&,
+                                                                                         const double*, cudaStream_t);
+extern template void launch_pf_variant<ADER_ORDER, FORM_NODAL, ADER_NV, ADER_REAL, true>(const StepArgs&,
+                                                                                         const double*, cudaStream_t);
+#endif
 template int launch_predict_faces_nv<ADER_ORDER, ADER_NV, ADER_REAL>(const StepArgs&, const double*, cudaStream_t);
+#endif
 #endif
 
 }  // namespace ader

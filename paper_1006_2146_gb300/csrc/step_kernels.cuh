@@ -443,26 +443,34 @@ __global__ void __launch_bounds__(128) k_ct(StepArgs a, double* Bf, double c_hos
     if (z < a.grid.n) zone_ct<R>(a, Bf, c_host, use_dt_dev, z);
 }
 
-template <int ORDER, int NV, class R>
-int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st) {
+// One variant of the predictor + face kernel, launched over the grid.  Each variant can be compiled in a
+// translation unit of its own (the fourth-order ones are, see step_inst.cuh), which keeps the parallel
+// build's longest compile short.
+template <int ORDER, int FORM, int NV, class R, bool SRC>
+void launch_pf_variant(const StepArgs& a, const double* U, cudaStream_t st) {
     const int T = 128;
     const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
+    k_predict_faces<ORDER, FORM, NV, R, SRC><<<blocks, T, 0, st>>>(a, U);
+}
+
+template <int ORDER, int NV, class R>
+int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st) {
     if constexpr (ZoneOps<ORDER>::HAS_SOURCE) {
         if (a.src_kind != SOURCE_NONE && a.Sb && a.n_iter > 0) {
             if (a.form == FORM_NODAL) {
-                k_predict_faces<ORDER, FORM_NODAL, NV, R, true><<<blocks, T, 0, st>>>(a, U);
+                launch_pf_variant<ORDER, FORM_NODAL, NV, R, true>(a, U, st);
                 return 1;
             }
             if constexpr (ZoneOps<ORDER>::HAS_SOURCE_MODAL) {
-                k_predict_faces<ORDER, FORM_MODAL, NV, R, true><<<blocks, T, 0, st>>>(a, U);
+                launch_pf_variant<ORDER, FORM_MODAL, NV, R, true>(a, U, st);
                 return 1;
             }
         }
     }
     if (a.form == FORM_MODAL)
-        k_predict_faces<ORDER, FORM_MODAL, NV, R><<<blocks, T, 0, st>>>(a, U);
+        launch_pf_variant<ORDER, FORM_MODAL, NV, R, false>(a, U, st);
     else
-        k_predict_faces<ORDER, FORM_NODAL, NV, R><<<blocks, T, 0, st>>>(a, U);
+        launch_pf_variant<ORDER, FORM_NODAL, NV, R, false>(a, U, st);
     return 1;
 }
 

@@ -1,5 +1,7 @@
-// Order-4 Euler predictor + face kernel in F32 (see step_inst.cuh).
+// Order-4 Euler predictor + face kernel in F32 (see step_inst.cuh): the dispatch; each
+// kernel variant is compiled in its own unit, step_o4_euler_f32_<form>_<source>.cu.
 #define ADER_ORDER 4
 #define ADER_NV 5
 #define ADER_REAL float
+#define ADER_SPLIT_VARIANTS 1
 #include "step_inst.cuh"

@@ -1,0 +1,7 @@
+// Order-4 Euler predictor + face kernel in F64, nodal form, with a source (see step_inst.cuh).
+#define ADER_ORDER 4
+#define ADER_NV 5
+#define ADER_REAL double
+#define ADER_FORM FORM_NODAL
+#define ADER_SRC true
+#include "step_inst.cuh"
