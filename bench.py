@@ -44,6 +44,8 @@ def parse():
                    help="train the third-order predictor guess first (untimed), then start the converged "
                         "predictor from it (tolerance 1e-6 in FP32, 1e-13 in FP64 unless --converged)")
     p.add_argument("--no-variants", action="store_true", help="skip the per-variant table")
+    p.add_argument("--vortex-sizes", default="64,128",
+                   help="grid sizes of the 2-D vortex tables (Tables I and II go to 512)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -340,6 +342,49 @@ def convergence_variant(ader, torch, sizes=(32, 64, 128), T=0.05):
                  for i in range(len(sizes) - 1)]
         out["order%d" % order] = {"sizes": list(sizes), "l1_rho": errs, "rates": rates}
     out["paper_table_iv_rates_64_to_96"] = {"order2": 2.31, "order3": 2.97, "order4": 4.01}
+    return out
+
+
+def vortex_tables(ader, torch, sizes=(64, 128, 256)):
+    """The paper's Tables I and II on this path: the 2-D isentropic (Sec. VI.1) and magnetised (Sec. VI.2)
+    vortices as one-zone z-slabs, FP64, modal, HLL, CFL 0.45, run for one period of the mean flow (t = 10 on
+    [-5, 5]^2; t = 20 on [-10, 10]^2 at fourth order).  Per zone L1 / Linf error of rho (Table I) and of the
+    x-face field (Table II), the rates, and the paper's printed L1 errors beside them."""
+    from paper_1006_2146_gb300 import inputs, run
+    import numpy as np
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "vortex_tables.json")) as fh:
+        paper = json.load(fh)
+    idx = [paper["sizes"].index(n) for n in sizes]
+    out = {}
+    for table, kind in (("table_i", "hydro"), ("table_ii", "mhd")):
+        res = {}
+        for order in (2, 3, 4):
+            L = 20.0 if order == 4 else 10.0
+            l1, linf, secs = [], [], 0.0
+            for n in sizes:
+                if kind == "hydro":
+                    U, B, G = inputs.isentropic_vortex(n, L=L), None, 1.4
+                else:
+                    (U, B), G = inputs.magnetized_vortex(n, L=L), 5.0 / 3.0
+                s = ader.Solver((1, n, n), order=order, form="modal", solver="hll", gamma=G,
+                                lengths=inputs.slab_lengths(L), mhd=(B is not None))
+                dU = torch.from_numpy(U).to("cuda")
+                dB = None if B is None else torch.from_numpy(B).to("cuda")
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                run.advance(s, dU, L, cfl=0.45, Bface=dB)
+                torch.cuda.synchronize()
+                secs += time.perf_counter() - t0
+                s.close()
+                err = (dU[0].cpu().numpy() - U[0]) if B is None else (dB[0].cpu().numpy() - B[0])
+                l1.append(float(np.abs(err).mean()))
+                linf.append(float(np.abs(err).max()))
+            res["order%d" % order] = {
+                "sizes": list(sizes), "l1": l1, "linf": linf,
+                "l1_rates": [float(np.log2(l1[i] / l1[i + 1])) for i in range(len(sizes) - 1)],
+                "paper_l1": [paper[table]["order%d" % order]["l1"][i] for i in idx],
+                "seconds": secs}
+        out[table] = res
     return out
 
 
@@ -741,6 +786,11 @@ def gpu_arm(args):
             variants["density_wave_convergence_fp64"] = convergence_variant(ader, torch)
         except Exception as exc:
             variants["density_wave_convergence_fp64"] = {"error": str(exc)[:200]}
+        try:
+            variants["vortex_tables_i_ii_fp64"] = vortex_tables(
+                ader, torch, sizes=tuple(int(v) for v in args.vortex_sizes.split(",")))
+        except Exception as exc:
+            variants["vortex_tables_i_ii_fp64"] = {"error": str(exc)[:200]}
         variants["batched_64_problems_fp32"] = batched_variant(ader, torch, stream)
         variants["batched_512_small_problems_fp32"] = batched_variant(ader, torch, stream, count=512,
                                                                       sizes=(16, 24, 32))

@@ -321,3 +321,95 @@ def batch_problems(count=64, seed=1006, sizes=(32, 48, 64, 80, 96, 112, 128), mh
         out.append(dict(shape=(n, n, n), order=order, mhd=False, form=form, solver=solver, gamma=1.4,
                         U=np.ascontiguousarray(U), B=None))
     return out
+
+
+# ----------------------------------------------------------------------------- 2-D problems as z-slabs
+SLAB_DEPTH = 2.0 ** 40
+"""Depth of a z-slab in units of its zone width.  A 2-D problem runs as one zone in z (periodic, so every
+z-difference is exactly zero); the large depth only takes the z signal speed out of the CFL time step,
+which then has the 2-D form."""
+
+
+def slab_lengths(L):
+    """Domain lengths (Lx, Ly, Lz) of an n x n slab over [-L/2, L/2]^2 for Solver(..., lengths=)."""
+    return (float(L), float(L), float(L) * SLAB_DEPTH)
+
+
+def _slab_average(fn, n, L, npts):
+    """Average of fn(x, y) over every zone of an n x n grid on [-L/2, L/2]^2, shape (1, n, n) [z, y, x]."""
+    xg, wg = _gauss(npts)
+    h = L / n
+    c = -0.5 * L + (np.arange(n) + 0.5) * h
+    out = 0.0
+    for a, wa in zip(xg, wg):
+        for b, wb in zip(xg, wg):
+            out = out + wa * wb * fn((c + a * h)[None, :], (c + b * h)[:, None])
+    return np.broadcast_to(out, (n, n))[None].astype(np.float64).copy()
+
+
+def isentropic_vortex(n, L=10.0, eps=5.0, gamma=1.4, npts=5):
+    """Isentropic hydrodynamic vortex of Sec. VI.1 on [-L/2, L/2]^2, shape (5, 1, n, n).
+
+    Mean flow rho = P = 1, v = (1, 1, 0); the vortex adds dv = eps/(2 pi) e^{(1 - r^2)/2} (-y, x) and
+    dT = -(gamma - 1) eps^2 / (8 gamma pi^2) e^{1 - r^2} to T = P / rho at constant entropy P / rho^gamma = 1,
+    so rho = T^{1/(gamma-1)} and P = rho T.  Zone averages of the conserved variables by npts^2 Gauss points.
+    After t = L the mean flow has carried the vortex once across the periodic domain: the exact solution
+    is the initial state again.
+    """
+    k = (gamma - 1.0) * eps ** 2 / (8.0 * gamma * np.pi ** 2)
+    s = eps / (2.0 * np.pi)
+
+    def prim(x, y):
+        r2 = x * x + y * y
+        T = 1.0 - k * np.exp(1.0 - r2)
+        rho = T ** (1.0 / (gamma - 1.0))
+        a = s * np.exp(0.5 * (1.0 - r2))
+        return rho, 1.0 - a * y, 1.0 + a * x, rho * T
+
+    def cons(c):
+        def f(x, y):
+            rho, vx, vy, P = prim(x, y)
+            return [rho, rho * vx, rho * vy, 0.0 * rho, P / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy)][c]
+        return f
+
+    return np.concatenate([_slab_average(cons(c), n, L, npts)[None] for c in range(5)])
+
+
+def magnetized_vortex(n, L=10.0, kappa=1.0, mu=np.sqrt(FOUR_PI), gamma=5.0 / 3.0, npts=5):
+    """Magnetised isodensity vortex of Sec. VI.2 on [-L/2, L/2]^2: (U (5, 1, n, n), Bface (3, 1, n, n)).
+
+    rho = 1, mean v = (1, 1, 0), mean B = 0; with f = e^{(1 - r^2)/2} the vortex adds
+    dv = kappa/(2 pi) f (-y, x), dB = mu/(2 pi) f (-y, x) and
+    dP = (mu/(2 pi))^2 (1 - r^2) f^2 / (8 pi) - (kappa/(2 pi))^2 f^2 / 2 (Gaussian units: it balances the
+    centrifugal, magnetic-pressure and tension forces).  The paper leaves kappa and mu to its ref. [8];
+    kappa = 1 and mu = sqrt(4 pi) are the values of that vortex.  B = curl(A_z z) with
+    A_z = mu/(2 pi) f, so the face averages are differences of A_z at the grid nodes (Stokes; divergence-free
+    to round-off).  The exact solution at t = L is the initial state.
+    """
+    b = mu / (2.0 * np.pi)
+    q = kappa / (2.0 * np.pi)
+
+    def f(x, y):
+        return np.exp(0.5 * (1.0 - x * x - y * y))
+
+    def prim(x, y):
+        r2 = x * x + y * y
+        e = f(x, y)
+        P = 1.0 + b * b * (1.0 - r2) * e * e / (2.0 * FOUR_PI) - 0.5 * q * q * e * e
+        return 1.0 - q * e * y, 1.0 + q * e * x, -b * e * y, b * e * x, P
+
+    def energy(x, y):
+        vx, vy, Bx, By, P = prim(x, y)
+        return P / (gamma - 1.0) + 0.5 * (vx * vx + vy * vy) + (Bx * Bx + By * By) / (2.0 * FOUR_PI)
+
+    rho = np.ones((1, n, n))
+    mx = _slab_average(lambda x, y: prim(x, y)[0], n, L, npts)
+    my = _slab_average(lambda x, y: prim(x, y)[1], n, L, npts)
+    U = np.stack([rho, mx, my, np.zeros_like(rho), _slab_average(energy, n, L, npts)])
+    h = L / n
+    xn = -0.5 * L + np.arange(n) * h
+    Az = b * f(xn[None, :], xn[:, None])                 # [j, i] at the grid node (x_i, y_j)
+    Bx = (np.roll(Az, -1, axis=0) - Az) / h               # face x_i - 1/2 of zone (i, j)
+    By = -(np.roll(Az, -1, axis=1) - Az) / h
+    Bface = np.stack([Bx[None], By[None], np.zeros((1, n, n))])
+    return U, Bface
