@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-variants", action="store_true", help="skip the per-variant table")
     p.add_argument("--vortex-sizes", default="64,128",
                    help="grid sizes of the 2-D vortex tables (Tables I and II go to 512)")
+    p.add_argument("--blast-symmetry", action="store_true",
+                   help="also run the 3-D hydrodynamic and MHD blasts to their end times (about ten minutes)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -385,6 +387,56 @@ def vortex_tables(ader, torch, sizes=(64, 128, 256)):
                 "paper_l1": [paper[table]["order%d" % order]["l1"][i] for i in idx],
                 "seconds": secs}
         out[table] = res
+    return out
+
+
+# Nodal asymmetry of the final velocities printed by the paper (fractions): Sec. VIII.3 (hydrodynamic blast,
+# 96^3, t = 0.1) and Sec. IX.4 (MHD blast, 97^3, t = 0.014); the modal schemes are symmetric to round-off.
+PAPER_NODAL_ASYMMETRY = {"hydro_blast_96": {"order2": 4e-4, "order3": 2e-6, "order4": 7e-5},
+                         "mhd_blast_97": {"order2": 2.1e-5, "order3": 1.4e-3, "order4": 7.1e-5}}
+
+
+def velocity_asymmetry(torch, U):
+    """Departures from the point symmetry through the domain centre that a centred blast keeps (v odd;
+    rho, P and B even): (pointwise, peak).  pointwise = max over zones and components of |v(x) + v(-x)|
+    / max |v|; peak = max over directions d of |max v_d - max(-v_d)| / max |v_d|, the difference between
+    the largest velocities in opposite directions."""
+    v = U[1:4] / U[0]
+    pointwise = float((v + torch.flip(v, dims=(1, 2, 3))).abs().max() / v.abs().max())
+    peak = max(float((v[d].max() - (-v[d]).max()).abs() / v[d].abs().max()) for d in range(3))
+    return pointwise, peak
+
+
+def blast_symmetry(ader, torch, orders=(2, 3, 4), forms=("modal", "nodal"),
+                   cases=(("hydro_blast_96", "hll"), ("mhd_blast_97", "hll"), ("mhd_blast_97", "linearized"))):
+    """The paper's 3-D blasts run to their end times at CFL 0.3 (FP64): the velocity asymmetry of each
+    order and form beside the printed nodal figures, the step count and wall time, or the error status
+    of a run that does not finish (the robustness half of the test)."""
+    from paper_1006_2146_gb300 import _lib, inputs, run
+    out = {}
+    for name, solver in cases:
+        mhd = name.startswith("mhd")
+        n, T = (97, 0.014) if mhd else (96, 0.1)
+        U, B = inputs.mhd_blast(n) if mhd else (inputs.blast(n), None)
+        res = {"n": n, "t_end": T, "solver": solver, "paper_nodal_asymmetry": PAPER_NODAL_ASYMMETRY[name]}
+        for order in orders:
+            for form in forms:
+                s = ader.Solver((n, n, n), order=order, form=form, solver=solver, gamma=1.4, mhd=mhd)
+                dU = torch.from_numpy(U).to("cuda")
+                dB = None if B is None else torch.from_numpy(B).to("cuda")
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                try:
+                    t, steps = run.advance(s, dU, T, cfl=0.3, Bface=dB, max_steps=20000)
+                    torch.cuda.synchronize()
+                    pw, pk = velocity_asymmetry(torch, dU)
+                    rec = {"asymmetry_pointwise": pw, "asymmetry_peak": pk, "steps": steps, "t": t,
+                           "seconds": time.perf_counter() - t0, "rho_min": float(dU[0].min())}
+                except _lib.AderError as exc:
+                    rec = {"error": str(exc)[:200]}
+                s.close()
+                res["%s_order%d" % (form, order)] = rec
+        out["%s_%s" % (name, solver)] = res
     return out
 
 
@@ -791,6 +843,8 @@ def gpu_arm(args):
                 ader, torch, sizes=tuple(int(v) for v in args.vortex_sizes.split(",")))
         except Exception as exc:
             variants["vortex_tables_i_ii_fp64"] = {"error": str(exc)[:200]}
+        if args.blast_symmetry:
+            variants["blast_symmetry_fp64"] = blast_symmetry(ader, torch)
         variants["batched_64_problems_fp32"] = batched_variant(ader, torch, stream)
         variants["batched_512_small_problems_fp32"] = batched_variant(ader, torch, stream, count=512,
                                                                       sizes=(16, 24, 32))

@@ -172,6 +172,23 @@ int ader_predictor_stats(ader_ctx* ctx, unsigned long long* out3_host, void* str
 #define ADER_SOURCE_GRAVITY 2
 int ader_set_source(ader_ctx* ctx, int kind, const double* params);
 
+/* Dense output inside a step (Sec. VII: the predictor's space-time polynomial
+ * gives the solution at any time within the step, which is what the finer
+ * levels of an adaptive mesh, taking shorter steps, need from a coarse zone).
+ * ader_set_dense_output(ctx, 1) makes every later ader_step / ader_step_devdt
+ * keep all L space-time modes of each zone's predictor (L = 5 / 15 / 35 at
+ * orders 2 / 3 / 4; L x nvar x zones values of the bulk precision, allocated
+ * and held by the context); 0 frees them.  ADER_ERR_CUDA if the allocation
+ * fails.  SSP-RK steps keep nothing. */
+int ader_set_dense_output(ader_ctx* ctx, int enable);
+/* Writes, for the last step that kept its modes, the LS spatial modes (LS = 4
+ * / 10 / 20) of every zone's polynomial at time t^n + tau dt, 0 <= tau <= 1:
+ * out[(s*nvar + v)*zones + zone], FP64 device memory, s = 0..LS-1 the spatial
+ * modes in the order of Eqs. 14-16 (s = 0 is the zone average; for MHD the
+ * field variables are the zone field's modes).  Asynchronous on the stream.
+ * ADER_ERR_ARG for tau outside [0, 1], a NULL out, or no step since enabling. */
+int ader_dense_output(ader_ctx* ctx, double tau, double* out, void* stream);
+
 /* Learned initial guess (third order; the paper has no learned component and
  * starts its Picard iteration of Sec. IV from zero).  params (device, FP32,
  * layout and size from ader_mlp_shape) is an MLP mapping a zone's normalised

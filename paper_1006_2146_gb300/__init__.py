@@ -12,6 +12,7 @@ from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_FP32_BULK, ADER_HLL, ADER_LINE
                    AderError, ader_create, ader_destroy, ader_diagnostics, ader_last_error, ader_launches_per_step,
                    ader_guess_count, ader_guess_eval, ader_guess_samples, ader_max_dt, ader_mlp_grad, ader_mlp_shape, ader_mlp_train, ader_predictor_stats,
                    ader_profile, ader_profile_read, ader_profile_reset, ader_rk_step, ader_set_guess, ader_set_source,
+                   ader_set_dense_output, ader_dense_output,
                    ader_set_predictor, ader_step, ader_step_devdt, ader_step_host, ader_sync_status, load)
 
 
@@ -53,6 +54,14 @@ class Solver:
         """Non-stiff source: "linear" with params (k,), "gravity" with (gx, gy, gz), or None to remove it."""
         code = {None: ADER_SOURCE_NONE, "linear": ADER_SOURCE_LINEAR, "gravity": ADER_SOURCE_GRAVITY}[kind]
         ader_set_source(self.h, code, params)
+
+    def set_dense_output(self, enable=True):
+        """Keep each later step's space-time polynomial for dense_output (Sec. VII)."""
+        ader_set_dense_output(self.h, enable)
+
+    def dense_output(self, tau, out, stream=None):
+        """Spatial modes (LS, nvar, nz, ny, nx) FP64 at t^n + tau dt of the last kept step, into out."""
+        ader_dense_output(self.h, tau, out, stream)
 
     def set_guess(self, params):
         ader_set_guess(self.h, params)

@@ -19,7 +19,7 @@ ADER_SOURCE_NONE, ADER_SOURCE_LINEAR, ADER_SOURCE_GRAVITY = 0, 1, 2
 
 EXPORTS = ("ader_create", "ader_step", "ader_step_devdt", "ader_max_dt", "ader_rk_step", "ader_step_host",
            "ader_diagnostics", "ader_sync_status", "ader_launches_per_step", "ader_profile", "ader_profile_reset",
-           "ader_profile_read", "ader_set_predictor", "ader_predictor_stats", "ader_set_source", "ader_set_guess",
+           "ader_profile_read", "ader_set_predictor", "ader_predictor_stats", "ader_set_source", "ader_set_dense_output", "ader_dense_output", "ader_set_guess",
            "ader_mlp_shape", "ader_guess_samples", "ader_guess_count", "ader_guess_eval", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy",
            "ader_max_dt_static", "ader_batch_create", "ader_batch_tune", "ader_batch_step", "ader_batch_advance",
            "ader_batch_status", "ader_batch_tuning", "ader_batch_groups", "ader_batch_last_error",
@@ -67,6 +67,8 @@ def load(path=None):
     lib.ader_predictor_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), vp]
     lib.ader_set_guess.argtypes = [vp, vp]
     lib.ader_set_source.argtypes = [vp, ctypes.c_int, vp]
+    lib.ader_set_dense_output.argtypes = [vp, ctypes.c_int]
+    lib.ader_dense_output.argtypes = [vp, ctypes.c_double, vp, vp]
     lib.ader_guess_count.argtypes = [vp, vp, vp]
     lib.ader_mlp_shape.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(ctypes.c_longlong)]
@@ -212,6 +214,16 @@ def ader_set_source(h, kind, params=None):
         vals = [float(v) for v in params]
         arr = (ctypes.c_double * len(vals))(*vals)
     return _check(h, load().ader_set_source(h, int(kind), arr))
+
+
+def ader_set_dense_output(h, enable):
+    """Keep (True) or drop (False) every later step's space-time modes for ader_dense_output."""
+    return _check(h, load().ader_set_dense_output(h, 1 if enable else 0))
+
+
+def ader_dense_output(h, tau, out, stream=None):
+    """The LS spatial modes at t^n + tau dt of the last kept step into out (device FP64, (LS, nvar) + grid)."""
+    return _check(h, load().ader_dense_output(h, float(tau), _ptr(out), _stream(stream)))
 
 
 def ader_guess_count(h, stream=None):

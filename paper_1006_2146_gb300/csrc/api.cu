@@ -46,6 +46,8 @@ struct ader_ctx {
     int src_kind = SOURCE_NONE;               // non-stiff source (ader_set_source)
     double src_par[3] = {0.0, 0.0, 0.0};
     void* Sb = nullptr;                       // dt S-bar per zone (5 x N, bulk precision), allocated with the source
+    void* Dm = nullptr;                       // dense output: the last step's space-time modes (L x NV x N, bulk)
+    bool dense_valid = false;                 // a step has written Dm since it was allocated
     bool setup_failed = false;                // a kernel could not be configured while enqueuing
     int launches = 0;
     std::string err;
@@ -135,6 +137,7 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.src_kind = n_iter > 0 ? c->src_kind : SOURCE_NONE;
     for (int i = 0; i < 3; ++i) a.src_par[i] = c->src_par[i];
     a.Sb = a.src_kind != SOURCE_NONE ? c->Sb : nullptr;
+    a.modes_out = nullptr;
     return a;
 }
 
@@ -247,7 +250,7 @@ void ader_destroy(ader_ctx* c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->spare) cudaEventDestroy(e);
-    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Glist, c->Gact, c->Gcount, c->Uf, c->Sb, c->flag,
+    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Glist, c->Gact, c->Gcount, c->Uf, c->Sb, c->Dm, c->flag,
                     c->stats, c->dtscr, c->partial, c->dt_dev,
                     c->Ustage, c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6],
                     c->rkB[0], c->rkB[1], c->rkB[2], c->rkB[3], c->rkB[4], c->rkB[5]};
@@ -322,8 +325,10 @@ static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const d
     cudaStream_t st = (cudaStream_t)stream;
     StepArgs a = make_args(c, dt, dt_dev, c->order - 1);
     a.Bface = Bface;
+    a.modes_out = c->Dm;
     const double coef = dt_dev ? 1.0 : dt;
     c->launches = enqueue_operator(c, a, U, U, U, coef, dt_dev != nullptr, st);
+    if (c->Dm) c->dense_valid = true;
     if (c->setup_failed) {
         c->setup_failed = false;
         return fail(c, ADER_ERR_CUDA, "learned-guess kernel set-up failed");
@@ -607,4 +612,31 @@ int ader_step_host(ader_ctx* c, double* U_host, double* Bface_host, double cfl, 
     return rc;
 }
 
+// ----------------------------------------------------------------------------- dense output (Sec. VII)
+static int mode_count(int order) { return order == 2 ? 5 : (order == 3 ? 15 : 35); }
+
+int ader_set_dense_output(ader_ctx* c, int enable) {
+    if (!c) return ADER_ERR_ARG;
+    if (c->Dm) {
+        if (int rc = cuda_check(c, cudaFree(c->Dm), "cudaFree dense modes")) return rc;
+        c->Dm = nullptr;
+    }
+    c->dense_valid = false;
+    if (!enable) return ADER_OK;
+    const size_t bytes = (size_t)mode_count(c->order) * (c->mhd ? 8 : 5) * (size_t)c->grid.n * c->rsize;
+    return cuda_check(c, cudaMalloc(&c->Dm, bytes), "cudaMalloc dense modes");
+}
+
+int ader_dense_output(ader_ctx* c, double tau, double* out, void* stream) {
+    if (!c) return ADER_ERR_ARG;
+    if (!out) return fail(c, ADER_ERR_ARG, "out is null");
+    if (!(tau >= 0.0 && tau <= 1.0)) return fail(c, ADER_ERR_ARG, "tau must lie in [0, 1]");
+    if (!c->Dm || !c->dense_valid) return fail(c, ADER_ERR_ARG, "no step has kept its modes (ader_set_dense_output)");
+    cudaStream_t st = (cudaStream_t)stream;
+    Trace t(c, "dense_output", st);
+    launch_dense_eval(c->order, c->mhd ? 8 : 5, c->fp32, c->Dm, c->grid.n, tau, out, st);
+    return cuda_check(c, cudaGetLastError(), "ader_dense_output launch");
+}
+
 }  // extern "C"
+

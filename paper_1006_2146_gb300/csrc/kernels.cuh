@@ -45,6 +45,7 @@ struct StepArgs {
     int src_kind;       // SOURCE_NONE / SOURCE_LINEAR / SOURCE_GRAVITY
     double src_par[3];  // k (linear) or g (gravity)
     void* Sb;           // with a source: dt S-bar of Eq. 6 per zone (5 x N, R), written by the predictor
+    void* modes_out;    // dense output: every space-time mode of the predictor (L x NV x N, R), or null
 };
 
 // gamma, gamma - 1 and 1 / dx_d in the bulk precision R
@@ -84,6 +85,9 @@ inline int s3_per_zone(int mhd, int linearized = 0) {
 template <class R> int launch_recon(const StepArgs& a, const double* U, cudaStream_t st);
 // out[i] = (float)U[i], i < count (the FP32 copy of the state the FP32 WENO reads)
 int launch_to_f32(float* out, const double* U, long long count, cudaStream_t st);
+// dense output: the LS spatial modes at time tau of the space-time modes kept by a step (dense.cu)
+int launch_dense_eval(int order, int nv, bool fp32, const void* modes, long long N, double tau, double* out,
+                      cudaStream_t st);
 template <int ORDER, int NV, class R> int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st);
 // out = base + c * L(U) with L = -sum_d (F(i+1/2) - F(i-1/2)) / dx_d from the face data in S3;
 // c = c_host, multiplied by *a.dt_dev when use_dt_dev; base may equal out (in place) or be null (out = c L).

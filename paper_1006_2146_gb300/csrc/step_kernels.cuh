@@ -181,6 +181,13 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
         if (a.tol > 0.0 && a.stats) record_iterations(a.stats, ctl);
         if (ctl.capped) raise_flag(a.flag, FLAG_NOT_CONVERGED);
     }
+    if (a.modes_out) {      // dense output (Sec. VII): keep the whole space-time polynomial of the step
+        R* o = (R*)a.modes_out;
+#pragma unroll
+        for (int k = 1; k <= L; ++k)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) o[(long long)((k - 1) * NV + v) * a.grid.n + z] = m[k][v];
+    }
     store_faces<ORDER, 0>(a, z, m, gm1);
     store_faces<ORDER, 1>(a, z, m, gm1);
     store_faces<ORDER, 2>(a, z, m, gm1);

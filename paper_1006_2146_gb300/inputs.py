@@ -107,6 +107,13 @@ def blast(n, gamma=1.4, p_in=1000.0, p_out=0.1, radius=0.1, center=(0.5, 0.5, 0.
     return _cons(rho, [z, z, z], P, gamma)
 
 
+def mhd_blast(n, B0=20.0, direction=(1.0, 1.0, 1.0), gamma=1.4, p_in=1000.0, p_out=0.1, radius=0.1, sub=4):
+    """MHD blast (Sec. IX.4): the blast of Sec. VIII.3 threaded by the uniform field B0 along `direction`
+    (the paper: |B| = 20 along the diagonal, plasma beta 0.00628 outside).  Returns (U, Bface)."""
+    B = uniform_field(n, B0, direction)
+    return with_field(blast(n, gamma, p_in, p_out, radius, sub=sub), B)
+
+
 def random_smooth(n, seed, amp=0.1, kmax=None, gamma=1.4, P0=1.0):
     """Seeded Gaussian random fields for rho and v (|k|^-2 spectrum, |k| <= kmax), P = P0."""
     rng = np.random.default_rng(seed)
