@@ -440,6 +440,43 @@ def blast_symmetry(ader, torch, orders=(2, 3, 4), forms=("modal", "nodal"),
     return out
 
 
+def dense_output_variant(ader, torch, stream, n, U0, reps=5):
+    """Dense output (Sec. VII) on the headline workload: the step with and without keeping the space-time
+    modes, and the evaluation kernel at tau = 1/2 with its HBM rate (it reads L x 5 and writes LS x 5 FP64
+    values per zone: 1,000 B at third order)."""
+    L, LS = 15, 10
+    s = ader.Solver((n, n, n), order=3, form="nodal")
+    d = U0.clone()
+    out = torch.empty((LS, 5, n, n, n), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+    res = {}
+    with torch.cuda.stream(stream):
+        s.max_dt(d, 0.4, dtv, stream)
+        dt = 0.5 * float(dtv.item())
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / reps
+        res["step_ms_plain"] = timed(lambda: s.step(d, dt, stream))
+        s.set_dense_output(True)
+        res["step_ms_keeping_modes"] = timed(lambda: s.step(d, dt, stream))
+        ms = timed(lambda: s.dense_output(0.5, out, stream))
+    s.close()
+    zones = n ** 3
+    gbs = (L + LS) * 5 * 8 * zones / (ms * 1e-3) / 1e9
+    res.update({"eval_ms": ms, "eval_bytes_per_zone": (L + LS) * 5 * 8, "eval_gbs": gbs,
+                "eval_frac_of_measured_hbm": gbs / peaks().get("hbm_gbs", 6800.0)})
+    return res
+
+
 def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32, 48, 64, 80, 96, 112, 128)):
     """`count` seeded independent problems of uneven cubic sizes (Euler and MHD, orders 2-4, FP32 bulk):
     one tuned batch replayed from a captured graph vs one context per problem launched in sequence.
@@ -831,6 +868,10 @@ def gpu_arm(args):
                                   "kernel_ms": {k: round(v[1] / v[0], 3) for k, v in vprof.items()}}
             except Exception as exc:          # a variant that fails is reported, not hidden
                 variants[name] = {"error": str(exc)[:200]}
+        try:
+            variants["dense_output_o3_nodal_fp64"] = dense_output_variant(ader, torch, stream, n, U0)
+        except Exception as exc:
+            variants["dense_output_o3_nodal_fp64"] = {"error": str(exc)[:200]}
         variants.update(learned_variants(ader, torch, n, U0, stream))
         variants.update(mhd_variants(ader, torch, stream))
         variants["learned_guess_mhd_ot_128"] = mhd_learned_evaluation(ader, torch, stream)
