@@ -26,7 +26,16 @@ def _safe(ub, uzone, gamma):
     return np.where(ok[None], ub, uzone)
 
 
-def hll(d, gamma, ubL, ubR, uL, uR, FL, FR, zL, zR):
+def transonic(vL, cL, vR, cR):
+    """A face's Riemann problem is transonic when a fast wave speed changes sign between its two
+    barycentre states, (v - c)_L (v - c)_R < 0 or (v + c)_L (v + c)_R < 0: a sonic point lies in the
+    fan (the reading of Sec. II.3's "transonic", which the paper does not define)."""
+    return ((vL - cL) * (vR - cR) < 0.0) | ((vL + cL) * (vR + cR) < 0.0)
+
+
+def hll(d, gamma, ubL, ubR, uL, uR, FL, FR, zL, zR, double_transonic=False):
+    """Eq. 56 (the HLL form of Eq. 17).  double_transonic: twice the third (dissipative) term at
+    transonic faces, the option Sec. V gives for the electric fields."""
     ubL = _safe(ubL, zL, gamma)
     ubR = _safe(ubR, zR, gamma)
     vL = ubL[1 + d] / ubL[0]
@@ -36,7 +45,8 @@ def hll(d, gamma, ubL, ubR, uL, uR, FL, FR, zL, zR):
     lamL = np.minimum(np.minimum(vL - cL, vR - cR), 0.0)
     lamR = np.maximum(np.maximum(vL + cL, vR + cR), 0.0)
     den = lamR - lamL
-    return (lamR * FL - lamL * FR + lamR * lamL * (uR - uL)) / den     # Eq. 56
+    w = np.where(transonic(vL, cL, vR, cR), 2.0, 1.0) if double_transonic else 1.0
+    return (lamR * FL - lamL * FR + w * lamR * lamL * (uR - uL)) / den     # Eq. 56
 
 
 def _prim(U, gamma):
@@ -127,7 +137,9 @@ def _mhd_abs_jacobian(Ustar, gamma, d, A, keep):
     return M @ (Ti @ absAp @ T) @ np.linalg.inv(M)
 
 
-def linearized(d, gamma, ubL, ubR, uL, uR, FL, FR, zL, zR):
+def linearized(d, gamma, ubL, ubR, uL, uR, FL, FR, zL, zR, double_transonic=False):
+    """F = (F_L + F_R)/2 - |A| (u_R - u_L)/2 with |A| at the mean barycentre state (Sec. II.3).
+    double_transonic: twice the dissipative term at transonic faces (see `transonic`)."""
     ubL = _safe(ubL, zL, gamma)
     ubR = _safe(ubR, zR, gamma)
     pL, pR = _prim(ubL, gamma), _prim(ubR, gamma)
@@ -142,7 +154,12 @@ def linearized(d, gamma, ubL, ubR, uL, uR, FL, FR, zL, zR):
     out = 0.5 * (FL + FR)
     D = np.zeros_like(out).reshape(out.shape[0], -1)
     D[keep] = diss
-    return out - 0.5 * D.reshape(out.shape)
+    D = D.reshape(out.shape)
+    if double_transonic:
+        vL, vR = ubL[1 + d] / ubL[0], ubR[1 + d] / ubR[0]
+        cL, cR = physics.fast_speed(ubL, gamma, d), physics.fast_speed(ubR, gamma, d)
+        D = D * np.where(transonic(vL, cL, vR, cR), 2.0, 1.0)
+    return out - 0.5 * D
 
 
 SOLVERS = {"hll": hll, "linearized": linearized}

@@ -50,7 +50,7 @@ def zone_state(U, Bface, order):
 
 
 def ader_step(U, dx, dt, order, form="nodal", solver="hll", gamma=1.4, Bface=None,
-              n_iter=None, tol=None, guess=None, return_iters=False, source=None):
+              n_iter=None, tol=None, guess=None, return_iters=False, source=None, emf_transonic=False):
     """Ubar^{n+1} by Eq. 6 (and B_face^{n+1} by Eq. 8 for MHD) after one ADER step of size dt.
 
     `source`: a non-stiff source model of ``oracle.source`` (None: S = 0); it enters the predictor and
@@ -67,7 +67,7 @@ def ader_step(U, dx, dt, order, form="nodal", solver="hll", gamma=1.4, Bface=Non
         Un = Un + res[2][:5]
     out = Un
     if mhd:
-        Bn = ct_update(Bface, F, edge_data, Uz, order, gamma, solver, dt, dx)
+        Bn = ct_update(Bface, F, edge_data, Uz, order, gamma, solver, dt, dx, emf_transonic)
         out = (Un, Bn)
     if return_iters:
         return out, iters
@@ -92,7 +92,7 @@ def max_dt(U, dx, cfl, gamma=1.4, Bface=None):
 
 
 # ----------------------------------------------------------------------------- constrained transport
-def edge_fluxes(edge_data, Uz, order, gamma, solver):
+def edge_fluxes(edge_data, Uz, order, gamma, solver, emf_transonic=False):
     """Numerical flux of each face evaluated with the face's edge averages (Sec. II.3, Eq. 57).
 
     The frozen wave speeds (or eigen-structure) are the face's own (barycentre
@@ -110,7 +110,8 @@ def edge_fluxes(edge_data, Uz, order, gamma, solver):
         out = {}
         for key, (uL, FL) in up[3].items():
             uR, FR = um[3][key]
-            out[key] = solve(d, gamma, up[0], ubR, uL, weno.shift(uR, d, 1), FL, weno.shift(FR, d, 1), Uz, zR)
+            out[key] = solve(d, gamma, up[0], ubR, uL, weno.shift(uR, d, 1), FL, weno.shift(FR, d, 1), Uz, zR,
+                             double_transonic=emf_transonic)
         Fe.append(out)
     return Fe
 
@@ -129,9 +130,10 @@ def edge_emfs(Fe):
     return Ex, Ey, Ez
 
 
-def ct_update(Bface, F, edge_data, Uz, order, gamma, solver, dt, dx):
-    """Face-averaged B at t^{n+1} by the discrete Stokes theorem of Eq. 8."""
-    Ex, Ey, Ez = edge_emfs(edge_fluxes(edge_data, Uz, order, gamma, solver))
+def ct_update(Bface, F, edge_data, Uz, order, gamma, solver, dt, dx, emf_transonic=False):
+    """Face-averaged B at t^{n+1} by the discrete Stokes theorem of Eq. 8.  emf_transonic: the electric
+    fields take twice the dissipation at transonic faces (Sec. V's option for Eq. 17)."""
+    Ex, Ey, Ez = edge_emfs(edge_fluxes(edge_data, Uz, order, gamma, solver, emf_transonic))
     sh = weno.shift
     # Bface[d][..., i_d] is the face i_d - 1/2: its edges are stored one zone lower along d
     Ez_x, Ey_x = sh(Ez, 0, -1), sh(Ey, 0, -1)
