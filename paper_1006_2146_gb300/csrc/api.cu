@@ -138,6 +138,7 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     for (int i = 0; i < 3; ++i) a.src_par[i] = c->src_par[i];
     a.Sb = a.src_kind != SOURCE_NONE ? c->Sb : nullptr;
     a.modes_out = nullptr;
+    a.emf_transonic = (c->flags & ADER_EMF_TRANSONIC) ? 1 : 0;
     return a;
 }
 
@@ -192,7 +193,7 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
         return ADER_ERR_ARG;
     if (order < 2 || order > 4 || !(gamma > 1.0) || (solver != ADER_HLL && solver != ADER_LINEARIZED))
         return ADER_ERR_ARG;
-    const unsigned known = ADER_MHD | ADER_NODAL | ADER_FP32_BULK;
+    const unsigned known = ADER_MHD | ADER_NODAL | ADER_FP32_BULK | ADER_EMF_TRANSONIC;
     if (flags & ~known) return ADER_ERR_ARG;        // the converged predictor is set by ader_set_predictor
     ader_ctx* c = new ader_ctx();
     c->g = *g;

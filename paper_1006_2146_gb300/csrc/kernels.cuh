@@ -46,6 +46,7 @@ struct StepArgs {
     double src_par[3];  // k (linear) or g (gravity)
     void* Sb;           // with a source: dt S-bar of Eq. 6 per zone (5 x N, R), written by the predictor
     void* modes_out;    // dense output: every space-time mode of the predictor (L x NV x N, R), or null
+    int emf_transonic;  // MHD: twice the dissipative term of the EMF fluxes at transonic faces
 };
 
 // gamma, gamma - 1 and 1 / dx_d in the bulk precision R

@@ -340,6 +340,12 @@ __global__ void __launch_bounds__(128) k_flux_update_stored(StepArgs a, double* 
 // evaluated with its edge slot e (0: t1+, 1: t1-, 2: t2+, 3: t2-): the face's
 // own frozen wave speeds (from its barycentre states) applied to the edge
 // averages of its two sides.
+// A face's Riemann problem is transonic when a fast wave speed changes sign between its two states.
+template <class R>
+ADER_DEV bool transonic(R vl, R cl, R vr, R cr) {
+    return (vl - cl) * (vr - cr) < R(0) || (vl + cl) * (vr + cr) < R(0);
+}
+
 template <int D, class R>
 ADER_DEV R edge_hll(const StepArgs& a, long long zl, long long zr, int e, R gamma, R gm1) {
     constexpr int NQ = side_values(8);
@@ -360,7 +366,9 @@ ADER_DEV R edge_hll(const StepArgs& a, long long zl, long long zr, int e, R gamm
     const R lamR = fmax(fmax(vl + cl, vr + cr), R(0));
     const R uL = S3[(sl * NQ + 24 + 2 * e) * N + zl], FL = S3[(sl * NQ + 25 + 2 * e) * N + zl];
     const R uR = S3[(sr * NQ + 24 + 2 * e) * N + zr], FR = S3[(sr * NQ + 25 + 2 * e) * N + zr];
-    return (lamR * FL - lamL * FR + lamR * lamL * (uR - uL)) / (lamR - lamL);
+    // optional: twice the third (dissipative) term of Eq. 17 where a fast speed changes sign (Sec. V)
+    const R w = (a.emf_transonic && transonic(vl, cl, vr, cr)) ? R(2) : R(1);
+    return (lamR * FL - lamL * FR + (w * lamR) * lamL * (uR - uL)) / (lamR - lamL);
 }
 
 // The same flux with the linearized solver: |A| at the mean of the face's two
@@ -384,7 +392,14 @@ ADER_DEV R edge_linearized(const StepArgs& a, long long zl, long long zr, int e,
     const Vec<8, R> diss = mhd_abs_jacobian_apply<D, R>(m.rho, m.v, m.p, m.B, gamma, gm1, dU);
     const int c = 5 + (e < 2 ? T1 : T2);
     const R FL = S3[(sl * NQ + 25 + 2 * e) * N + zl], FR = S3[(sr * NQ + 25 + 2 * e) * N + zr];
-    return R(0.5) * (FL + FR) - R(0.5) * diss[c];
+    R w = R(1);
+    if (a.emf_transonic) {           // optional doubled dissipation at transonic faces (Sec. V)
+        const Prim<8, R> pl = primitives(ubl, gm1), pr = primitives(ubr, gm1);
+        const R vl = D == 0 ? pl.vx : (D == 1 ? pl.vy : pl.vz);
+        const R vr = D == 0 ? pr.vx : (D == 1 ? pr.vy : pr.vz);
+        if (transonic(vl, fast_speed<D>(ubl, pl, gamma), vr, fast_speed<D>(ubr, pr, gamma))) w = R(2);
+    }
+    return R(0.5) * (FL + FR) - (R(0.5) * w) * diss[c];
 }
 
 template <int D, class R>
