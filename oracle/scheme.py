@@ -50,7 +50,8 @@ def zone_state(U, Bface, order):
 
 
 def ader_step(U, dx, dt, order, form="nodal", solver="hll", gamma=1.4, Bface=None,
-              n_iter=None, tol=None, guess=None, return_iters=False, source=None, emf_transonic=False):
+              n_iter=None, tol=None, guess=None, return_iters=False, source=None, emf_transonic=False,
+              positivity=False):
     """Ubar^{n+1} by Eq. 6 (and B_face^{n+1} by Eq. 8 for MHD) after one ADER step of size dt.
 
     `source`: a non-stiff source model of ``oracle.source`` (None: S = 0); it enters the predictor and
@@ -65,6 +66,8 @@ def ader_step(U, dx, dt, order, form="nodal", solver="hll", gamma=1.4, Bface=Non
         Un = Un - (dt / dx[d]) * (F[d][:5] - weno.shift(F[d][:5], d, -1))
     if source is not None:
         Un = Un + res[2][:5]
+    if positivity:
+        Un = positivity_fallback(U, Un, F, dx, dt, gamma, None if source is None else res[2][:5])
     out = Un
     if mhd:
         Bn = ct_update(Bface, F, edge_data, Uz, order, gamma, solver, dt, dx, emf_transonic)
@@ -72,6 +75,34 @@ def ader_step(U, dx, dt, order, form="nodal", solver="hll", gamma=1.4, Bface=Non
     if return_iters:
         return out, iters
     return out
+
+
+def positivity_fallback(U, Un, F, dx, dt, gamma, extra=None, passes=3):
+    """A posteriori positivity fallback (an option of this implementation; the paper names none).
+
+    Zones whose updated average is non-physical (rho <= 0, P <= 0 or not finite) are marked; every face
+    of a marked zone takes the first-order HLL flux of the two zone averages of U^n (Eq. 56 with the
+    zone averages as both the barycentre and the averaged states), and every zone is updated again from
+    U^n with the modified fluxes, which its neighbour across each face shares (so the update stays
+    conservative).  `passes` rounds, the marks accumulating.  Euler only; `extra` is the source part
+    (dt S-bar) of the update."""
+    mark = np.zeros(U.shape[1:], dtype=bool)
+    F = [f[:5].copy() for f in F]
+    for _ in range(passes):
+        mark |= ~physics.physical(Un, gamma)
+        if not mark.any():
+            break
+        for d in range(3):
+            face = mark | weno.shift(mark, d, 1)          # face i+1/2 is stored at zone i
+            UR = weno.shift(U, d, 1)
+            f1 = riemann.hll(d, gamma, U, UR, U, UR, physics.flux(U, gamma, d), physics.flux(UR, gamma, d), U, UR)
+            F[d] = np.where(face[None], f1, F[d])
+        Un = U.copy()
+        for d in range(3):
+            Un = Un - (dt / dx[d]) * (F[d] - weno.shift(F[d], d, -1))
+        if extra is not None:
+            Un = Un + extra
+    return Un
 
 
 def max_dt(U, dx, cfl, gamma=1.4, Bface=None):
