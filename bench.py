@@ -411,7 +411,7 @@ def velocity_asymmetry(torch, U):
 
 def blast_symmetry(ader, torch, orders=(2, 3, 4), forms=("modal", "nodal"),
                    cases=(("hydro_blast_96", "hll"), ("mhd_blast_97", "hll"), ("mhd_blast_97", "linearized"),
-                          ("mhd_blast_97", "hll_emf_transonic"))):
+                          ("mhd_blast_97", "hll_emf_transonic"), ("hydro_blast_96", "hll_positivity"))):
     """The paper's 3-D blasts run to their end times at CFL 0.3 (FP64): the velocity asymmetry of each
     order and form beside the printed nodal figures, the step count and wall time, or the error status
     of a run that does not finish (the robustness half of the test)."""
@@ -425,7 +425,8 @@ def blast_symmetry(ader, torch, orders=(2, 3, 4), forms=("modal", "nodal"),
         for order in orders:
             for form in forms:
                 s = ader.Solver((n, n, n), order=order, form=form, solver=solver.split("_")[0], gamma=1.4,
-                                mhd=mhd, emf_transonic=solver.endswith("emf_transonic"))
+                                mhd=mhd, emf_transonic=solver.endswith("emf_transonic"),
+                                positivity=solver.endswith("positivity"))
                 dU = torch.from_numpy(U).to("cuda")
                 dB = None if B is None else torch.from_numpy(B).to("cuda")
                 torch.cuda.synchronize()

@@ -55,9 +55,15 @@ enum {
     ADER_NODAL = 1u << 1,               /* nodal predictor (Apps. A-C); default modal (Sec. IV) */
     ADER_FP32_BULK = 1u << 2,           /* FP32 reconstruction/predictor/fluxes, FP64 update and reductions */
     ADER_CONVERGED_PREDICTOR = 1u << 4, /* iterate the predictor to tolerance instead of M-1 times */
-    ADER_EMF_TRANSONIC = 1u << 5        /* MHD: twice the dissipative term of Eq. 17 in the electric fields
+    ADER_EMF_TRANSONIC = 1u << 5,       /* MHD: twice the dissipative term of Eq. 17 in the electric fields
                                            at transonic faces (Secs. II.3, V); transonic = a fast wave
                                            speed v -/+ c_f changes sign between the face's two states */
+    ADER_POSITIVITY_FALLBACK = 1u << 6  /* FP64 Euler only (else ADER_ERR_ARG): after each ader_step, the
+                                           faces of zones left with rho <= 0 or P <= 0 take the first-order
+                                           HLL flux of the zone averages of U^n and the zones around them
+                                           are updated again (conservative; three passes).  Costs a copy
+                                           of U (5 x zones FP64) held by the context.  The paper names
+                                           no positivity safeguard; this is an option of the library. */
 };
 
 enum {
@@ -78,7 +84,8 @@ typedef struct ader_ctx ader_ctx;
  *            modes, L = 5/15/35 space-time modes, Eqs. 10-16)
  *   gamma  : ratio of specific heats (> 1)
  *   solver : ADER_HLL or ADER_LINEARIZED
- *   flags  : bitwise OR of ADER_MHD, ADER_NODAL, ADER_FP32_BULK, ADER_EMF_TRANSONIC (ADER_CONVERGED_PREDICTOR is
+ *   flags  : bitwise OR of ADER_MHD, ADER_NODAL, ADER_FP32_BULK, ADER_EMF_TRANSONIC,
+ *            ADER_POSITIVITY_FALLBACK (ADER_CONVERGED_PREDICTOR is
  *            rejected: use ader_set_predictor)
  * Allocates the device scratch for one step of this grid on the current
  * device.  *out receives the context; on failure *out is NULL. */

@@ -7,7 +7,7 @@ built from csrc/ (C ABI: include/ader.h); this package is its ctypes binding
 plus the seeded input generators (``inputs``).
 """
 from . import inputs  # noqa: F401
-from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_EMF_TRANSONIC, ADER_FP32_BULK, ADER_HLL, ADER_LINEARIZED, ADER_MHD, ADER_NODAL,  # noqa: F401
+from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_EMF_TRANSONIC, ADER_FP32_BULK, ADER_POSITIVITY_FALLBACK, ADER_HLL, ADER_LINEARIZED, ADER_MHD, ADER_NODAL,  # noqa: F401
                    ADER_SOURCE_GRAVITY, ADER_SOURCE_LINEAR, ADER_SOURCE_NONE,
                    AderError, ader_create, ader_destroy, ader_diagnostics, ader_last_error, ader_launches_per_step,
                    ader_guess_count, ader_guess_eval, ader_guess_samples, ader_max_dt, ader_mlp_grad, ader_mlp_shape, ader_mlp_train, ader_predictor_stats,
@@ -21,16 +21,17 @@ class Solver:
 
     mhd=True makes an ideal-MHD context: every call then takes the face field Bface (device, (3, nz, ny, nx)
     FP64), which ader_step and ader_rk_step advance in place by constrained transport.  emf_transonic=True
-    doubles the dissipative term of the electric fields at transonic faces (Secs. II.3, V)."""
+    doubles the dissipative term of the electric fields at transonic faces (Secs. II.3, V).  positivity=True
+    (FP64 Euler) re-solves the faces of zones a step leaves non-physical at first order."""
 
     def __init__(self, shape, order=3, form="modal", solver="hll", gamma=1.4, fp32=False, lengths=(1.0, 1.0, 1.0),
-                 mhd=False, emf_transonic=False):
+                 mhd=False, emf_transonic=False, positivity=False):
         nz, ny, nx = shape
         self.shape = tuple(shape)
         self.mhd = mhd
         self.dx = (lengths[0] / nx, lengths[1] / ny, lengths[2] / nz)
         flags = (ADER_NODAL if form == "nodal" else 0) | (ADER_FP32_BULK if fp32 else 0) | (ADER_MHD if mhd else 0) | \
-            (ADER_EMF_TRANSONIC if emf_transonic else 0)
+            (ADER_EMF_TRANSONIC if emf_transonic else 0) | (ADER_POSITIVITY_FALLBACK if positivity else 0)
         sol = ADER_HLL if solver == "hll" else ADER_LINEARIZED
         self.h = ader_create(nx, ny, nz, self.dx[0], self.dx[1], self.dx[2], order, gamma, sol, flags)
 

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libader_gb300.so")
 
 ADER_HLL, ADER_LINEARIZED = 0, 1
 ADER_MHD, ADER_NODAL, ADER_FP32_BULK, ADER_CONVERGED_PREDICTOR, ADER_EMF_TRANSONIC = 1, 2, 4, 16, 32
+ADER_POSITIVITY_FALLBACK = 64
 ADER_OK, ADER_ERR_ARG, ADER_ERR_CUDA, ADER_ERR_UNPHYSICAL, ADER_ERR_NONFINITE, ADER_ERR_NOT_CONVERGED = 0, -1, -2, -3, -4, -5
 ADER_ERR_TIMEOUT = -6
 ADER_SOURCE_NONE, ADER_SOURCE_LINEAR, ADER_SOURCE_GRAVITY = 0, 1, 2

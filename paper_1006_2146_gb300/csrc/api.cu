@@ -47,6 +47,8 @@ struct ader_ctx {
     double src_par[3] = {0.0, 0.0, 0.0};
     void* Sb = nullptr;                       // dt S-bar per zone (5 x N, bulk precision), allocated with the source
     void* Dm = nullptr;                       // dense output: the last step's space-time modes (L x NV x N, bulk)
+    double* Uold = nullptr;                   // positivity fallback: U^n of the current step (5 x N FP64)
+    unsigned char* pmark = nullptr;           // positivity fallback: zones marked non-physical (N bytes)
     bool dense_valid = false;                 // a step has written Dm since it was allocated
     bool setup_failed = false;                // a kernel could not be configured while enqueuing
     int launches = 0;
@@ -193,7 +195,8 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
         return ADER_ERR_ARG;
     if (order < 2 || order > 4 || !(gamma > 1.0) || (solver != ADER_HLL && solver != ADER_LINEARIZED))
         return ADER_ERR_ARG;
-    const unsigned known = ADER_MHD | ADER_NODAL | ADER_FP32_BULK | ADER_EMF_TRANSONIC;
+    const unsigned known = ADER_MHD | ADER_NODAL | ADER_FP32_BULK | ADER_EMF_TRANSONIC | ADER_POSITIVITY_FALLBACK;
+    if ((flags & ADER_POSITIVITY_FALLBACK) && (flags & (ADER_MHD | ADER_FP32_BULK))) return ADER_ERR_ARG;
     if (flags & ~known) return ADER_ERR_ARG;        // the converged predictor is set by ader_set_predictor
     ader_ctx* c = new ader_ctx();
     c->g = *g;
@@ -223,6 +226,10 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
         alloc(&c->E, N * 3 * c->rsize, "cudaMalloc EMF");
     }
     if (c->fp32) alloc((void**)&c->Uf, N * 5 * sizeof(float), "cudaMalloc FP32 state copy");
+    if (flags & ADER_POSITIVITY_FALLBACK) {
+        alloc((void**)&c->Uold, N * 5 * sizeof(double), "cudaMalloc U^n copy");
+        alloc((void**)&c->pmark, N, "cudaMalloc positivity marks");
+    }
     alloc((void**)&c->flag, sizeof(unsigned), "cudaMalloc flag");
     alloc((void**)&c->stats, 3 * sizeof(unsigned long long), "cudaMalloc predictor statistics");
     alloc((void**)&c->dtscr, 2 * sizeof(unsigned long long), "cudaMalloc dt scratch");
@@ -251,7 +258,7 @@ void ader_destroy(ader_ctx* c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->spare) cudaEventDestroy(e);
-    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Glist, c->Gact, c->Gcount, c->Uf, c->Sb, c->Dm, c->flag,
+    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Glist, c->Gact, c->Gcount, c->Uf, c->Sb, c->Dm, c->Uold, c->pmark, c->flag,
                     c->stats, c->dtscr, c->partial, c->dt_dev,
                     c->Ustage, c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6],
                     c->rkB[0], c->rkB[1], c->rkB[2], c->rkB[3], c->rkB[4], c->rkB[5]};
@@ -328,7 +335,15 @@ static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const d
     a.Bface = Bface;
     a.modes_out = c->Dm;
     const double coef = dt_dev ? 1.0 : dt;
+    if (c->Uold)
+        if (int rc = cuda_check(c, cudaMemcpyAsync(c->Uold, U, (size_t)c->grid.n * 5 * sizeof(double),
+                                                   cudaMemcpyDeviceToDevice, st), "copy of U^n"))
+            return rc;
     c->launches = enqueue_operator(c, a, U, U, U, coef, dt_dev != nullptr, st);
+    if (c->Uold) {
+        Trace t(c, "positivity_fallback", st);
+        c->launches += launch_positivity_fallback(a, U, c->Uold, c->pmark, coef, dt_dev != nullptr, st);
+    }
     if (c->Dm) c->dense_valid = true;
     if (c->setup_failed) {
         c->setup_failed = false;

@@ -1,0 +1,96 @@
+// A-posteriori positivity fallback for the FP64 Euler step (an option of this library; the paper names
+// no safeguard).  After the update, zones whose average is non-physical (rho <= 0, P <= 0 or not finite)
+// are marked; every face of a marked zone gets the first-order HLL flux of the two zone averages of U^n
+// (Eq. 56 with the zone averages as barycentre and averaged states), written over the stored face flux;
+// every zone next to a marked one is then updated again from U^n with the stored fluxes, which both
+// zones of a face share, so the step stays conservative.  Three passes, the marks accumulating; a pass
+// with no mark changes nothing.
+#include "kernels.cuh"
+#include "riemann.cuh"
+#include "step_kernels.cuh"
+
+namespace ader {
+
+namespace {
+
+ADER_DEV bool unphysical(const double* U, long long N, long long z, double gm1) {
+    const double rho = U[z];
+    const double m1 = U[N + z], m2 = U[2 * N + z], m3 = U[3 * N + z];
+    const double p = gm1 * (U[4 * N + z] - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / rho);
+    return !(rho > 0.0) || !(p > 0.0);
+}
+
+__global__ void __launch_bounds__(256) k_pos_mark(Grid g, const double* __restrict__ U, double gm1,
+                                                  unsigned char* __restrict__ mark) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z < g.n && unphysical(U, g.n, z, gm1)) mark[z] = 1;
+}
+
+template <int D>
+ADER_DEV void first_order_face(const StepArgs& a, const double* Uold, long long z, long long zp) {
+    const long long N = a.grid.n;
+    FaceSide<5, double> L, Rt;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        L.ub[v] = L.avg[v] = Uold[v * N + z];
+        Rt.ub[v] = Rt.avg[v] = Uold[v * N + zp];
+    }
+    L.F = flux<D>(L.ub, a.gm1);
+    Rt.F = flux<D>(Rt.ub, a.gm1);
+    const Vec<5, double> f = riemann_hll<D>(L, Rt, a.gamma, a.gm1);
+    double* F = (double*)a.S1;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[(D * 5 + v) * N + z] = f[v];
+}
+
+// the three upper faces of zone z (stored at z) that touch a marked zone
+__global__ void __launch_bounds__(128) k_pos_faces(StepArgs a, const double* __restrict__ Uold,
+                                                   const unsigned char* __restrict__ mark) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= a.grid.n) return;
+    int i, j, k;
+    zone_ijk(a.grid, z, i, j, k);
+    const long long zx = nbr_along(a.grid, z, i, j, k, 0, 1), zy = nbr_along(a.grid, z, i, j, k, 1, 1),
+                    zz = nbr_along(a.grid, z, i, j, k, 2, 1);
+    const bool mz = mark[z];
+    if (mz || mark[zx]) first_order_face<0>(a, Uold, z, zx);
+    if (mz || mark[zy]) first_order_face<1>(a, Uold, z, zy);
+    if (mz || mark[zz]) first_order_face<2>(a, Uold, z, zz);
+}
+
+// zones with a marked zone among themselves and their six face neighbours: Eq. 6 again from U^n
+__global__ void __launch_bounds__(128) k_pos_update(StepArgs a, double* U, const double* __restrict__ Uold,
+                                                    const unsigned char* __restrict__ mark, double c_host,
+                                                    int use_dt_dev) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= a.grid.n) return;
+    int i, j, k;
+    zone_ijk(a.grid, z, i, j, k);
+    bool near = mark[z];
+#pragma unroll
+    for (int D = 0; D < 3; ++D) {
+        near |= mark[nbr_along(a.grid, z, i, j, k, D, 1)] != 0;
+        near |= mark[nbr_along(a.grid, z, i, j, k, D, -1)] != 0;
+    }
+    if (near) zone_flux_update_stored<double>(a, U, Uold, c_host, use_dt_dev, z);
+}
+
+}  // namespace
+
+int launch_positivity_fallback(const StepArgs& a, double* U, const double* Uold, unsigned char* mark, double c_host,
+                               bool use_dt_dev, cudaStream_t st) {
+    const long long N = a.grid.n;
+    if (N <= 0) return 0;
+    cudaMemsetAsync(mark, 0, (size_t)N, st);
+    const unsigned b256 = (unsigned)((N + 255) / 256), b128 = (unsigned)((N + 127) / 128);
+    int n = 0;
+    for (int pass = 0; pass < 3; ++pass) {
+        k_pos_mark<<<b256, 256, 0, st>>>(a.grid, U, a.gm1, mark);
+        k_pos_faces<<<b128, 128, 0, st>>>(a, Uold, mark);
+        k_pos_update<<<b128, 128, 0, st>>>(a, U, Uold, mark, c_host, use_dt_dev ? 1 : 0);
+        n += 3;
+    }
+    return n;
+}
+
+}  // namespace ader

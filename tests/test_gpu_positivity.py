@@ -1,0 +1,67 @@
+"""The a-posteriori positivity fallback (ADER_POSITIVITY_FALLBACK, FP64 Euler) on the GPU against the
+oracle's (scheme.positivity_fallback, pinned in tests/test_oracle_positivity.py)."""
+import numpy as np
+import pytest
+
+from gpu_util import ensure_built, rel_l1, to_dev, to_host
+from oracle import physics, scheme
+from paper_1006_2146_gb300 import _lib, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ader():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    import paper_1006_2146_gb300 as p
+    return p
+
+
+def _double_rarefaction(n, v0=4.0, p0=0.4, gamma=1.4):
+    x = (np.arange(n) + 0.5) / n
+    vx = np.where(x < 0.5, -v0, v0)[None, None, :] * np.ones((1, 1, n))
+    rho = np.ones((1, 1, n))
+    z = np.zeros_like(rho)
+    return np.stack([rho, rho * vx, z, z, p0 / (gamma - 1.0) * rho + 0.5 * rho * vx ** 2])
+
+
+@pytest.mark.parametrize("order,form", [(3, "modal"), (4, "modal"), (4, "nodal")])
+def test_fallback_parity_on_the_double_rarefaction(ader, order, form):
+    n = 32
+    dx = (1 / n, 1.0, 1.0)
+    U = _double_rarefaction(n)
+    s = ader.Solver((1, 1, n), order=order, form=form, lengths=(1.0, 1.0, 1.0), positivity=True)
+    d = to_dev(U)
+    triggered = False
+    for _ in range(20):
+        Uh = to_host(d)
+        dt = scheme.max_dt(Uh, (1 / n, 1.0, 1.0), 0.3)
+        want = scheme.ader_step(Uh, dx, dt, order, form, "hll", positivity=True)
+        triggered |= not physics.physical(scheme.ader_step(Uh, dx, dt, order, form, "hll"), 1.4).all()
+        s.step(d, dt)
+        assert s.status() == 0
+        assert rel_l1(to_host(d), want) <= 1e-12
+    s.close()
+    assert triggered
+
+
+def test_fallback_changes_nothing_on_smooth_data_and_checks_flags(ader):
+    import torch
+    shape = (8, 9, 10)
+    U = inputs.random_smooth(shape, seed=78, amp=0.3)
+    dt = 0.5 * scheme.max_dt(U, (1 / 10, 1 / 9, 1 / 8), 0.4)
+    a, b = to_dev(U), to_dev(U)
+    s0 = ader.Solver(shape, order=4, form="modal")
+    s1 = ader.Solver(shape, order=4, form="modal", positivity=True)
+    s0.step(a, dt)
+    s1.step(b, dt)
+    assert s0.status() == 0 and s1.status() == 0
+    assert torch.equal(a, b)
+    s0.close()
+    s1.close()
+    for kw in ({"fp32": True}, {"mhd": True, "gamma": 5.0 / 3.0}):
+        with pytest.raises(_lib.AderError):
+            ader.Solver(shape, order=3, positivity=True, **kw)
