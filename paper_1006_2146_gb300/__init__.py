@@ -7,13 +7,15 @@ built from csrc/ (C ABI: include/ader.h); this package is its ctypes binding
 plus the seeded input generators (``inputs``).
 """
 from . import inputs  # noqa: F401
-from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_EMF_TRANSONIC, ADER_FP32_BULK, ADER_POSITIVITY_FALLBACK, ADER_HLL, ADER_LINEARIZED, ADER_MHD, ADER_NODAL,  # noqa: F401
+from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_EMF_TRANSONIC, ADER_FP32_BULK, ADER_HLL,  # noqa: F401
+                   ADER_LINEARIZED, ADER_MHD, ADER_NODAL, ADER_POSITIVITY_FALLBACK,
                    ADER_SOURCE_GRAVITY, ADER_SOURCE_LINEAR, ADER_SOURCE_NONE,
-                   AderError, ader_create, ader_destroy, ader_diagnostics, ader_last_error, ader_launches_per_step,
-                   ader_guess_count, ader_guess_eval, ader_guess_samples, ader_max_dt, ader_mlp_grad, ader_mlp_shape, ader_mlp_train, ader_predictor_stats,
-                   ader_profile, ader_profile_read, ader_profile_reset, ader_rk_step, ader_set_guess, ader_set_source,
-                   ader_set_dense_output, ader_dense_output,
-                   ader_set_predictor, ader_step, ader_step_devdt, ader_step_host, ader_sync_status, load)
+                   AderError, ader_create, ader_dense_output, ader_destroy, ader_diagnostics, ader_guess_count,
+                   ader_guess_eval, ader_guess_samples, ader_last_error, ader_launches_per_step, ader_max_dt,
+                   ader_mlp_grad, ader_mlp_shape, ader_mlp_train, ader_predictor_stats, ader_profile,
+                   ader_profile_read, ader_profile_reset, ader_rk_step, ader_set_dense_output, ader_set_guess,
+                   ader_set_predictor, ader_set_source, ader_step, ader_step_devdt, ader_step_host,
+                   ader_sync_status, load)
 
 
 class Solver:
