@@ -66,37 +66,46 @@ def ader_step(U, dx, dt, order, form="nodal", solver="hll", gamma=1.4, Bface=Non
         Un = Un - (dt / dx[d]) * (F[d][:5] - weno.shift(F[d][:5], d, -1))
     if source is not None:
         Un = Un + res[2][:5]
-    if positivity:
-        Un = positivity_fallback(U, Un, F, dx, dt, gamma, None if source is None else res[2][:5])
     out = Un
     if mhd:
         Bn = ct_update(Bface, F, edge_data, Uz, order, gamma, solver, dt, dx, emf_transonic)
+        if positivity:
+            Un = positivity_fallback(U, Un, F, dx, dt, gamma, None if source is None else res[2][:5], Uz=Uz, Bnew=Bn)
         out = (Un, Bn)
+    elif positivity:
+        out = positivity_fallback(U, Un, F, dx, dt, gamma, None if source is None else res[2][:5])
     if return_iters:
         return out, iters
     return out
 
 
-def positivity_fallback(U, Un, F, dx, dt, gamma, extra=None, passes=3):
+def positivity_fallback(U, Un, F, dx, dt, gamma, extra=None, passes=3, Uz=None, Bnew=None):
     """A posteriori positivity fallback (an option of this implementation; the paper names none).
 
     Zones whose updated average is non-physical (rho <= 0, P <= 0 or not finite) are marked; every face
-    of a marked zone takes the first-order HLL flux of the two zone averages of U^n (Eq. 56 with the
+    of a marked zone takes the first-order HLL flux of the two zone averages of step n (Eq. 56 with the
     zone averages as both the barycentre and the averaged states), and every zone is updated again from
     U^n with the modified fluxes, which its neighbour across each face shares (so the update stays
-    conservative).  `passes` rounds, the marks accumulating.  Euler only; `extra` is the source part
-    (dt S-bar) of the update."""
+    conservative).  `passes` rounds, the marks accumulating.  `extra` is the source part (dt S-bar) of the
+    update.  MHD (Uz: the zone states of step n with the zone field of the face-B reconstruction; Bnew:
+    the face field after constrained transport, which the fallback leaves alone): a zone's pressure is
+    taken with the mean of its two new face values per direction, and the first-order flux is the MHD
+    one, of which the five hydrodynamic components replace the stored fluxes."""
     mark = np.zeros(U.shape[1:], dtype=bool)
     F = [f[:5].copy() for f in F]
+    if Bnew is not None:
+        zB = np.stack([0.5 * (Bnew[d] + weno.shift(Bnew[d], d, 1)) for d in range(3)])
+    W = U if Uz is None else Uz
     for _ in range(passes):
-        mark |= ~physics.physical(Un, gamma)
+        state = Un if Bnew is None else np.concatenate([Un, zB])
+        mark |= ~physics.physical(state, gamma)
         if not mark.any():
             break
         for d in range(3):
             face = mark | weno.shift(mark, d, 1)          # face i+1/2 is stored at zone i
-            UR = weno.shift(U, d, 1)
-            f1 = riemann.hll(d, gamma, U, UR, U, UR, physics.flux(U, gamma, d), physics.flux(UR, gamma, d), U, UR)
-            F[d] = np.where(face[None], f1, F[d])
+            WR = weno.shift(W, d, 1)
+            f1 = riemann.hll(d, gamma, W, WR, W, WR, physics.flux(W, gamma, d), physics.flux(WR, gamma, d), W, WR)
+            F[d] = np.where(face[None], f1[:5], F[d])
         Un = U.copy()
         for d in range(3):
             Un = Un - (dt / dx[d]) * (F[d] - weno.shift(F[d], d, -1))

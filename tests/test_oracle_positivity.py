@@ -63,3 +63,35 @@ def test_fallback_is_local():
         near = near | np.roll(near, 1) | np.roll(near, -1)
     changed = np.any(fixed[:, 0, 0] != plain[:, 0, 0], axis=0)
     assert changed.any() and not (changed & ~near).any()
+
+
+def _mhd_double_rarefaction(n, v0=4.0, by=5.0, p0=0.4, gamma=1.4):
+    U = _double_rarefaction(n, v0, p0, gamma)
+    U[4] += by ** 2 / (8.0 * np.pi)
+    z = np.zeros((1, 1, n))
+    return U, np.stack([z, by + z, z])
+
+
+def _mhd_physical(U, B):
+    zB = np.stack([0.5 * (B[d] + np.roll(B[d], -1, axis=2 - d)) for d in range(3)])
+    return physics.physical(np.concatenate([U, zB]), 1.4)
+
+
+def test_mhd_fallback_keeps_the_field_and_stays_physical():
+    """MHD (transverse field 5, beta 0.4): the fallback leaves the constrained-transport field alone and
+    keeps the hydrodynamic state physical where the plain fourth-order step fails."""
+    n = 32
+    dx = (1 / n, 1.0, 1.0)
+    U, B = _mhd_double_rarefaction(n)
+    tot0 = U.sum(axis=(1, 2, 3))
+    failed_plain = False
+    for _ in range(15):
+        dt = scheme.max_dt(U, dx, 0.3, 1.4, Bface=B)
+        pU, pB = scheme.ader_step(U, dx, dt, 4, "modal", "hll", 1.4, Bface=B)
+        failed_plain |= not _mhd_physical(pU, pB).all()
+        U, B2 = scheme.ader_step(U, dx, dt, 4, "modal", "hll", 1.4, Bface=B, positivity=True)
+        assert np.array_equal(B2, pB)
+        B = B2
+        assert _mhd_physical(U, B).all()
+    assert failed_plain
+    assert np.abs(U.sum(axis=(1, 2, 3)) - tot0).max() <= 1e-13 * np.abs(tot0).max()
