@@ -58,12 +58,14 @@ enum {
     ADER_EMF_TRANSONIC = 1u << 5,       /* MHD: twice the dissipative term of Eq. 17 in the electric fields
                                            at transonic faces (Secs. II.3, V); transonic = a fast wave
                                            speed v -/+ c_f changes sign between the face's two states */
-    ADER_POSITIVITY_FALLBACK = 1u << 6  /* FP64 Euler only (else ADER_ERR_ARG): after each ader_step, the
-                                           faces of zones left with rho <= 0 or P <= 0 take the first-order
-                                           HLL flux of the zone averages of U^n and the zones around them
-                                           are updated again (conservative; three passes).  Costs a copy
-                                           of U (5 x zones FP64) held by the context.  The paper names
-                                           no positivity safeguard; this is an option of the library. */
+    ADER_POSITIVITY_FALLBACK = 1u << 6  /* FP64 only (with ADER_FP32_BULK: ADER_ERR_ARG): after each
+                                           ader_step, the faces of zones left with rho <= 0 or P <= 0
+                                           (MHD: P with the mean of the new face field) take the
+                                           first-order HLL flux of the zone averages of step n and the
+                                           zones around them are updated again (conservative; three
+                                           passes; the face field is left to constrained transport).
+                                           Costs a copy of U (5 x zones FP64) held by the context.  The
+                                           paper names no positivity safeguard; this is an option. */
 };
 
 enum {

@@ -24,7 +24,7 @@ class Solver:
     mhd=True makes an ideal-MHD context: every call then takes the face field Bface (device, (3, nz, ny, nx)
     FP64), which ader_step and ader_rk_step advance in place by constrained transport.  emf_transonic=True
     doubles the dissipative term of the electric fields at transonic faces (Secs. II.3, V).  positivity=True
-    (FP64 Euler) re-solves the faces of zones a step leaves non-physical at first order."""
+    (FP64) re-solves the faces of zones a step leaves non-physical at first order."""
 
     def __init__(self, shape, order=3, form="modal", solver="hll", gamma=1.4, fp32=False, lengths=(1.0, 1.0, 1.0),
                  mhd=False, emf_transonic=False, positivity=False):

@@ -196,7 +196,7 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
     if (order < 2 || order > 4 || !(gamma > 1.0) || (solver != ADER_HLL && solver != ADER_LINEARIZED))
         return ADER_ERR_ARG;
     const unsigned known = ADER_MHD | ADER_NODAL | ADER_FP32_BULK | ADER_EMF_TRANSONIC | ADER_POSITIVITY_FALLBACK;
-    if ((flags & ADER_POSITIVITY_FALLBACK) && (flags & (ADER_MHD | ADER_FP32_BULK))) return ADER_ERR_ARG;
+    if ((flags & ADER_POSITIVITY_FALLBACK) && (flags & ADER_FP32_BULK)) return ADER_ERR_ARG;
     if (flags & ~known) return ADER_ERR_ARG;        // the converged predictor is set by ader_set_predictor
     ader_ctx* c = new ader_ctx();
     c->g = *g;
@@ -340,10 +340,6 @@ static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const d
                                                    cudaMemcpyDeviceToDevice, st), "copy of U^n"))
             return rc;
     c->launches = enqueue_operator(c, a, U, U, U, coef, dt_dev != nullptr, st);
-    if (c->Uold) {
-        Trace t(c, "positivity_fallback", st);
-        c->launches += launch_positivity_fallback(a, U, c->Uold, c->pmark, coef, dt_dev != nullptr, st);
-    }
     if (c->Dm) c->dense_valid = true;
     if (c->setup_failed) {
         c->setup_failed = false;
@@ -353,6 +349,10 @@ static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const d
         Trace t(c, "emf_ct", st);
         c->launches += c->fp32 ? launch_emf_ct<float>(a, Bface, coef, dt_dev != nullptr, st)
                                : launch_emf_ct<double>(a, Bface, coef, dt_dev != nullptr, st);
+    }
+    if (c->Uold) {          // after constrained transport: an MHD zone's pressure takes the new face field
+        Trace t(c, "positivity_fallback", st);
+        c->launches += launch_positivity_fallback(a, U, c->Uold, c->pmark, coef, dt_dev != nullptr, st);
     }
     return cuda_check(c, cudaGetLastError(), "ader_step launch");
 }

@@ -1,4 +1,4 @@
-// A-posteriori positivity fallback for the FP64 Euler step (an option of this library; the paper names
+// A-posteriori positivity fallback for the FP64 step (Euler and MHD) (an option of this library; the paper names
 // no safeguard).  After the update, zones whose average is non-physical (rho <= 0, P <= 0 or not finite)
 // are marked; every face of a marked zone gets the first-order HLL flux of the two zone averages of U^n
 // (Eq. 56 with the zone averages as barycentre and averaged states), written over the stored face flux;
@@ -13,37 +13,62 @@ namespace ader {
 
 namespace {
 
-ADER_DEV bool unphysical(const double* U, long long N, long long z, double gm1) {
+// rho <= 0, P <= 0 or not finite; MHD: P with the mean of the zone's two new face values per direction
+template <int NV>
+ADER_DEV bool unphysical(const Grid& g, const double* U, const double* Bf, long long z, double gm1) {
+    const long long N = g.n;
     const double rho = U[z];
     const double m1 = U[N + z], m2 = U[2 * N + z], m3 = U[3 * N + z];
-    const double p = gm1 * (U[4 * N + z] - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / rho);
-    return !(rho > 0.0) || !(p > 0.0);
+    double e = U[4 * N + z] - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / rho;
+    if constexpr (NV == 8) {
+        int i, j, k;
+        zone_ijk(g, z, i, j, k);
+        const double bx = 0.5 * (Bf[z] + Bf[nbr_along(g, z, i, j, k, 0, 1)]);
+        const double by = 0.5 * (Bf[N + z] + Bf[N + nbr_along(g, z, i, j, k, 1, 1)]);
+        const double bz = 0.5 * (Bf[2 * N + z] + Bf[2 * N + nbr_along(g, z, i, j, k, 2, 1)]);
+        e = e - (bx * bx + by * by + bz * bz) / (8.0 * 3.141592653589793);
+    }
+    return !(rho > 0.0) || !(gm1 * e > 0.0);
 }
 
-__global__ void __launch_bounds__(256) k_pos_mark(Grid g, const double* __restrict__ U, double gm1,
-                                                  unsigned char* __restrict__ mark) {
+template <int NV>
+__global__ void __launch_bounds__(256) k_pos_mark(Grid g, const double* __restrict__ U, const double* __restrict__ Bf,
+                                                  double gm1, unsigned char* __restrict__ mark) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (z < g.n && unphysical(U, g.n, z, gm1)) mark[z] = 1;
+    if (z < g.n && unphysical<NV>(g, U, Bf, z, gm1)) mark[z] = 1;
 }
 
-template <int D>
+// the zone states of step n: U^n and, for MHD, the zone field of the face-B reconstruction (ZB)
+template <int NV>
+ADER_DEV Vec<NV, double> state_n(const StepArgs& a, const double* Uold, long long z) {
+    const long long N = a.grid.n;
+    Vec<NV, double> u;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = Uold[v * N + z];
+    if constexpr (NV == 8) {
+        const double* ZB = (const double*)a.ZB;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[5 + c] = ZB[c * N + z];
+    }
+    return u;
+}
+
+template <int D, int NV>
 ADER_DEV void first_order_face(const StepArgs& a, const double* Uold, long long z, long long zp) {
     const long long N = a.grid.n;
-    FaceSide<5, double> L, Rt;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        L.ub[v] = L.avg[v] = Uold[v * N + z];
-        Rt.ub[v] = Rt.avg[v] = Uold[v * N + zp];
-    }
+    FaceSide<NV, double> L, Rt;
+    L.ub = L.avg = state_n<NV>(a, Uold, z);
+    Rt.ub = Rt.avg = state_n<NV>(a, Uold, zp);
     L.F = flux<D>(L.ub, a.gm1);
     Rt.F = flux<D>(Rt.ub, a.gm1);
-    const Vec<5, double> f = riemann_hll<D>(L, Rt, a.gamma, a.gm1);
+    const Vec<NV, double> f = riemann_hll<D>(L, Rt, a.gamma, a.gm1);
     double* F = (double*)a.S1;
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[(D * 5 + v) * N + z] = f[v];
 }
 
 // the three upper faces of zone z (stored at z) that touch a marked zone
+template <int NV>
 __global__ void __launch_bounds__(128) k_pos_faces(StepArgs a, const double* __restrict__ Uold,
                                                    const unsigned char* __restrict__ mark) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -53,9 +78,9 @@ __global__ void __launch_bounds__(128) k_pos_faces(StepArgs a, const double* __r
     const long long zx = nbr_along(a.grid, z, i, j, k, 0, 1), zy = nbr_along(a.grid, z, i, j, k, 1, 1),
                     zz = nbr_along(a.grid, z, i, j, k, 2, 1);
     const bool mz = mark[z];
-    if (mz || mark[zx]) first_order_face<0>(a, Uold, z, zx);
-    if (mz || mark[zy]) first_order_face<1>(a, Uold, z, zy);
-    if (mz || mark[zz]) first_order_face<2>(a, Uold, z, zz);
+    if (mz || mark[zx]) first_order_face<0, NV>(a, Uold, z, zx);
+    if (mz || mark[zy]) first_order_face<1, NV>(a, Uold, z, zy);
+    if (mz || mark[zz]) first_order_face<2, NV>(a, Uold, z, zz);
 }
 
 // zones with a marked zone among themselves and their six face neighbours: Eq. 6 again from U^n
@@ -85,8 +110,13 @@ int launch_positivity_fallback(const StepArgs& a, double* U, const double* Uold,
     const unsigned b256 = (unsigned)((N + 255) / 256), b128 = (unsigned)((N + 127) / 128);
     int n = 0;
     for (int pass = 0; pass < 3; ++pass) {
-        k_pos_mark<<<b256, 256, 0, st>>>(a.grid, U, a.gm1, mark);
-        k_pos_faces<<<b128, 128, 0, st>>>(a, Uold, mark);
+        if (a.mhd) {
+            k_pos_mark<8><<<b256, 256, 0, st>>>(a.grid, U, a.Bface, a.gm1, mark);
+            k_pos_faces<8><<<b128, 128, 0, st>>>(a, Uold, mark);
+        } else {
+            k_pos_mark<5><<<b256, 256, 0, st>>>(a.grid, U, nullptr, a.gm1, mark);
+            k_pos_faces<5><<<b128, 128, 0, st>>>(a, Uold, mark);
+        }
         k_pos_update<<<b128, 128, 0, st>>>(a, U, Uold, mark, c_host, use_dt_dev ? 1 : 0);
         n += 3;
     }

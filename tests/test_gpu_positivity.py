@@ -1,4 +1,4 @@
-"""The a-posteriori positivity fallback (ADER_POSITIVITY_FALLBACK, FP64 Euler) on the GPU against the
+"""The a-posteriori positivity fallback (ADER_POSITIVITY_FALLBACK, FP64, Euler and MHD) on the GPU against the
 oracle's (scheme.positivity_fallback, pinned in tests/test_oracle_positivity.py)."""
 import numpy as np
 import pytest
@@ -62,6 +62,26 @@ def test_fallback_changes_nothing_on_smooth_data_and_checks_flags(ader):
     assert torch.equal(a, b)
     s0.close()
     s1.close()
-    for kw in ({"fp32": True}, {"mhd": True, "gamma": 5.0 / 3.0}):
-        with pytest.raises(_lib.AderError):
-            ader.Solver(shape, order=3, positivity=True, **kw)
+    with pytest.raises(_lib.AderError):
+        ader.Solver(shape, order=3, positivity=True, fp32=True)
+
+
+def test_mhd_fallback_parity(ader):
+    """Magnetised double rarefaction (transverse field 5): per-step parity with the oracle's MHD fallback."""
+    n = 32
+    dx = (1 / n, 1.0, 1.0)
+    U = _double_rarefaction(n)
+    U[4] += 25.0 / (8.0 * np.pi)
+    z = np.zeros((1, 1, n))
+    B = np.stack([z, 5.0 + z, z])
+    s = ader.Solver((1, 1, n), order=4, form="modal", positivity=True, mhd=True)
+    dU, dB = to_dev(U), to_dev(B)
+    for _ in range(12):
+        Uh, Bh = to_host(dU), to_host(dB)
+        dt = scheme.max_dt(Uh, dx, 0.3, 1.4, Bface=Bh)
+        wU, wB = scheme.ader_step(Uh, dx, dt, 4, "modal", "hll", 1.4, Bface=Bh, positivity=True)
+        s.step(dU, dt, Bface=dB)
+        assert s.status() == 0
+        assert rel_l1(to_host(dU), wU) <= 1e-12
+        assert np.abs(to_host(dB) - wB).max() <= 1e-12 * np.abs(wB).max()
+    s.close()
