@@ -141,6 +141,7 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.Sb = a.src_kind != SOURCE_NONE ? c->Sb : nullptr;
     a.modes_out = nullptr;
     a.emf_transonic = (c->flags & ADER_EMF_TRANSONIC) ? 1 : 0;
+    a.defer_nonfinite = 0;
     return a;
 }
 
@@ -334,6 +335,7 @@ static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const d
     StepArgs a = make_args(c, dt, dt_dev, c->order - 1);
     a.Bface = Bface;
     a.modes_out = c->Dm;
+    a.defer_nonfinite = c->Uold ? 1 : 0;     // the fallback mends non-finite zones, then checks them
     const double coef = dt_dev ? 1.0 : dt;
     if (c->Uold)
         if (int rc = cuda_check(c, cudaMemcpyAsync(c->Uold, U, (size_t)c->grid.n * 5 * sizeof(double),

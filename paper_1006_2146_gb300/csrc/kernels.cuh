@@ -47,6 +47,7 @@ struct StepArgs {
     void* Sb;           // with a source: dt S-bar of Eq. 6 per zone (5 x N, R), written by the predictor
     void* modes_out;    // dense output: every space-time mode of the predictor (L x NV x N, R), or null
     int emf_transonic;  // MHD: twice the dissipative term of the EMF fluxes at transonic faces
+    int defer_nonfinite;  // the positivity fallback checks the updated state itself (after its passes)
 };
 
 // gamma, gamma - 1 and 1 / dx_d in the bulk precision R

@@ -4,7 +4,8 @@
 // (Eq. 56 with the zone averages as barycentre and averaged states), written over the stored face flux;
 // every zone next to a marked one is then updated again from U^n with the stored fluxes, which both
 // zones of a face share, so the step stays conservative.  Three passes, the marks accumulating; a pass
-// with no mark changes nothing.
+// with no mark changes nothing.  The update leaves the non-finite check to the fallback, which mends such
+// zones like non-physical ones and checks the state after its passes.
 #include "kernels.cuh"
 #include "riemann.cuh"
 #include "step_kernels.cuh"
@@ -100,6 +101,16 @@ __global__ void __launch_bounds__(128) k_pos_update(StepArgs a, double* U, const
     if (near) zone_flux_update_stored<double>(a, U, Uold, c_host, use_dt_dev, z);
 }
 
+// after the passes: a zone still not finite is an error of the step (the update deferred this check)
+__global__ void __launch_bounds__(256) k_pos_check(Grid g, const double* __restrict__ U, unsigned* flag) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= g.n) return;
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) bad |= !isfinite(U[v * g.n + z]);
+    if (bad) raise_flag(flag, FLAG_NONFINITE);
+}
+
 }  // namespace
 
 int launch_positivity_fallback(const StepArgs& a, double* U, const double* Uold, unsigned char* mark, double c_host,
@@ -120,7 +131,8 @@ int launch_positivity_fallback(const StepArgs& a, double* U, const double* Uold,
         k_pos_update<<<b128, 128, 0, st>>>(a, U, Uold, mark, c_host, use_dt_dev ? 1 : 0);
         n += 3;
     }
-    return n;
+    k_pos_check<<<b256, 256, 0, st>>>(a.grid, U, a.flag);
+    return n + 1;
 }
 
 }  // namespace ader

@@ -262,7 +262,7 @@ ADER_DEV void store_update(const StepArgs& a, double* out, const double* base, d
         bad |= !isfinite(val);
         out[v * N + z] = val;
     }
-    if (bad) raise_flag(a.flag, FLAG_NONFINITE);
+    if (bad && !a.defer_nonfinite) raise_flag(a.flag, FLAG_NONFINITE);
 }
 
 template <int SOLVER, int NV, class R>
