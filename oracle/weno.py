@@ -76,7 +76,25 @@ _MAPS3 = [_candidate_map(s, 2) for s in STENCILS_O3]
 _MAPS4 = [_candidate_map(s, 3) for s in STENCILS_O4]
 
 
+def smoothness_quadratic(b, c):
+    """Eq. 24: smoothness of the candidate a + b P1 + c P2 on its zone, b^2 + 13 c^2 / 3.
+
+    This is the Jiang-Shu measure, the sum over l = 1, 2 of the integral over
+    the zone of (d^l p / d xi^l)^2 (unit zone width).
+    """
+    return b * b + (13.0 / 3.0) * c * c
+
+
+def smoothness_cubic(b, c, d):
+    """Eq. 29: smoothness of a + b P1 + c P2 + d P3, (b + d/10)^2 + 13 c^2 / 3 + 781 d^2 / 20.
+
+    The Jiang-Shu measure of the cubic (derivatives of order 1 to 3).
+    """
+    return (b + 0.1 * d) ** 2 + (13.0 / 3.0) * c * c + (781.0 / 20.0) * d * d
+
+
 def _weights(IS, gam):
+    """Nonlinear weights omega_s = gamma_s / (EPS + IS_s)^2, normalised to sum to one."""
     alpha = [g / (EPS + s) ** 2 for g, s in zip(gam, IS)]
     tot = sum(alpha)
     return [a / tot for a in alpha]
@@ -90,7 +108,7 @@ def weno3(a, d):
         b = M[0, 0] * diff[0] + M[0, 1] * diff[1]
         c = M[1, 0] * diff[0] + M[1, 1] * diff[1]
         cands.append((b, c))
-    IS = [b * b + (13.0 / 3.0) * c * c for b, c in cands]
+    IS = [smoothness_quadratic(b, c) for b, c in cands]
     w = _weights(IS, GAMMA_O3)
     return (sum(wi * bc[0] for wi, bc in zip(w, cands)),
             sum(wi * bc[1] for wi, bc in zip(w, cands)))
@@ -102,7 +120,7 @@ def weno4(a, d):
     for ks, M in _MAPS4:
         diff = [shift(a, d, k) - a for k in ks]
         cands.append(tuple(sum(M[r, j] * diff[j] for j in range(3)) for r in range(3)))
-    IS = [(b + 0.1 * e) ** 2 + (13.0 / 3.0) * c * c + (781.0 / 20.0) * e * e for b, c, e in cands]
+    IS = [smoothness_cubic(b, c, e) for b, c, e in cands]
     w = _weights(IS, GAMMA_O4)
     return tuple(sum(wi * cand[r] for wi, cand in zip(w, cands)) for r in range(3))
 
@@ -171,7 +189,7 @@ def face_b_moments(Bf, d, order):
         s1 = ((8.0 * Bm - Bmm + 5.0 * Bp) / 12.0, Bp - Bm, (Bp + Bmm - 2.0 * Bm) / 2.0)   # Eq. 22
         s2 = ((8.0 * Bp - Bpp + 5.0 * Bm) / 12.0, Bp - Bm, (Bm + Bpp - 2.0 * Bp) / 2.0)   # Eq. 23
         cands = (s1, s2)
-        IS = [c[1] ** 2 + 13.0 * c[2] ** 2 / 3.0 for c in cands]                          # Eq. 24
+        IS = [smoothness_quadratic(c[1], c[2]) for c in cands]                             # Eq. 24
         w = _weights(IS, GAMMA_B_O3)
         out = [sum(wi * c[r] for wi, c in zip(w, cands)) for r in range(3)]
         return out[0], (out[1], out[2])
@@ -192,7 +210,7 @@ def face_b_moments(Bf, d, order):
           (-Bppp + 5 * Bpp - 7 * Bp + 3 * Bm) / 4.0,
           (Bppp - 3 * Bpp + 3 * Bp - Bm) / 6.0)                                         # Eq. 28
     cands = (s1, s2, s3)
-    IS = [(c[1] + 0.1 * c[3]) ** 2 + 13.0 * c[2] ** 2 / 3.0 + 781.0 * c[3] ** 2 / 20.0 for c in cands]  # Eq. 29
+    IS = [smoothness_cubic(c[1], c[2], c[3]) for c in cands]                            # Eq. 29
     w = _weights(IS, GAMMA_B_O4)
     out = [sum(wi * c[r] for wi, c in zip(w, cands)) for r in range(4)]
     return out[0], (out[1], out[2], out[3])
