@@ -81,6 +81,14 @@ def cores_used(cpu_s, wall_s):
     return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
 
 
+def host_cores():
+    """The host's logical CPU count (the cores the oracle could have used)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -987,7 +995,8 @@ def cpu_baseline(args, budget_s=15.0):
         steps += 1
     el = time.perf_counter() - t0
     threads = cores_used(time.process_time() - c0, el)
-    return {"value": m ** 3 * steps / el, "unit": "zone-updates/s", "cores": threads, "kind": "oracle",
+    return {"value": m ** 3 * steps / el, "unit": "zone-updates/s", "cores": threads, "host_cores": host_cores(),
+            "kind": "oracle",
             "sample": "%d steps of the same scheme on a %d^3 Sod tube (numpy FP64 oracle, %.1f s)" % (steps, m, el)}
 
 
@@ -1015,7 +1024,7 @@ def reference_arm(args):
     el = time.perf_counter() - t0
     threads = cores_used(time.process_time() - c0, el)
     value = m ** 3 * args.steps / el
-    cpu = {"value": value, "unit": "zone-updates/s", "cores": threads, "kind": "oracle",
+    cpu = {"value": value, "unit": "zone-updates/s", "cores": threads, "host_cores": host_cores(), "kind": "oracle",
            "sample": "%d timed steps (after %d untimed) of the same scheme on a %d^3 Sod tube (numpy FP64 "
                      "oracle, %.1f s)" % (args.steps, args.warmup, m, el)}
     line = {"metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": world, "steps": args.steps,

@@ -64,8 +64,12 @@ enum {
                                            first-order HLL flux of the zone averages of step n and the
                                            zones around them are updated again (conservative; three
                                            passes; the face field is left to constrained transport).
-                                           Costs a copy of U (5 x zones FP64) held by the context.  The
-                                           paper names no positivity safeguard; this is an option. */
+                                           Costs a copy of U (5 x zones FP64) held by the context.  After
+                                           the passes the step itself reports what is left: a non-finite
+                                           zone value or (MHD) face value raises ADER_ERR_NONFINITE, a zone
+                                           still non-physical ADER_ERR_UNPHYSICAL (read by
+                                           ader_sync_status).  The paper names no positivity safeguard;
+                                           this is an option. */
 };
 
 enum {
@@ -316,8 +320,10 @@ void ader_batch_destroy(ader_batch* b);
  * first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  All calls
  * share the array, so calls that overlap on the GPU race: serialise them.
- * Returns ADER_OK, ADER_ERR_ARG or ADER_ERR_CUDA; non-physical zones are
- * skipped (use ader_max_dt / ader_sync_status to have them reported). */
+ * Returns ADER_OK, ADER_ERR_ARG or ADER_ERR_CUDA.  A zone with rho <= 0,
+ * P <= 0 or a non-finite value has no signal speed: *dt_dev is then a quiet
+ * NaN (a step taken with it turns the state non-finite, which
+ * ader_sync_status reports). */
 #define ADER_STATIC_MAX_ZONES 268435456LL
 int ader_max_dt_static(const ader_grid* g, double gamma, const double* U, double cfl, double* dt_dev, void* stream);
 

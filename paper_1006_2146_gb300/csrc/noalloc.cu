@@ -13,8 +13,13 @@
 // (cudaGetSymbolAddress, with that device current) on the first call made on
 // it; that first call should therefore come before any stream capture.  All
 // calls share the array, so calls that overlap on the GPU (two streams, two
-// threads) race and must be serialised by the caller.  The counter starts at
-// zero (cleared at set-up) and the last block of each call clears it again.
+// threads) race and must be serialised by the caller.  The counter is zero
+// when the module loads (a __device__ variable starts zeroed) and the last
+// block of each call clears it again, so set-up issues no device work.
+//
+// A zone with rho <= 0, P <= 0 or a value that is not finite has no signal
+// speed: the call then writes a quiet NaN as dt, so a step taken with it
+// turns the state non-finite, which ader_sync_status reports.
 #include <mutex>
 
 #include "../../include/ader.h"
@@ -43,6 +48,7 @@ __global__ void __launch_bounds__(STATIC_THREADS) k_max_dt_static(Grid g, const 
     const long long N = g.n;
     const long long base = (long long)blockIdx.x * STATIC_ZONES_PER_BLOCK;
     double s = 0.0;
+    bool bad = false;
     for (int r = 0; r < STATIC_ZONES_PER_THREAD; ++r) {
         const long long z = base + (long long)r * STATIC_THREADS + threadIdx.x;
         if (z >= N) break;
@@ -50,7 +56,10 @@ __global__ void __launch_bounds__(STATIC_THREADS) k_max_dt_static(Grid g, const 
         const double ir = 1.0 / rho;
         const double vx = mx * ir, vy = my * ir, vz = mz * ir;
         const double p = (gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy + mz * vz));
-        if (!(rho > 0.0) || !(p > 0.0)) continue;
+        if (!(rho > 0.0) || !(p > 0.0) || !isfinite(p) || !isfinite(vx + vy + vz)) {
+            bad = true;
+            continue;
+        }
         const double a = sqrt(gamma * p * ir);
         s = fmax(s, (fabs(vx) + a) * idx + (fabs(vy) + a) * idy + (fabs(vz) + a) * idz);
     }
@@ -59,11 +68,12 @@ __global__ void __launch_bounds__(STATIC_THREADS) k_max_dt_static(Grid g, const 
     __shared__ double warp_max[STATIC_THREADS / 32];
     __shared__ bool last;
     if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = s;
-    __syncthreads();
+    // a block that met a non-physical zone stores -1 (speeds are never negative)
+    const bool block_bad = __syncthreads_or(bad) != 0;
     if (threadIdx.x == 0) {
         double b = 0.0;
         for (int w = 0; w < STATIC_THREADS / 32; ++w) b = fmax(b, warp_max[w]);
-        scr->partial[blockIdx.x] = b;
+        scr->partial[blockIdx.x] = block_bad ? -1.0 : b;
         __threadfence();
         last = (atomicAdd(&scr->done, 1u) == gridDim.x - 1);
     }
@@ -71,15 +81,20 @@ __global__ void __launch_bounds__(STATIC_THREADS) k_max_dt_static(Grid g, const 
     if (!last) return;
     __threadfence();
     double m = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += STATIC_THREADS) m = fmax(m, ((volatile double*)scr->partial)[b]);
+    bool any_bad = false;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += STATIC_THREADS) {
+        const double v = ((volatile double*)scr->partial)[b];
+        any_bad |= v < 0.0;
+        m = fmax(m, v);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = m;
-    __syncthreads();
+    any_bad = __syncthreads_or(any_bad) != 0;
     if (threadIdx.x == 0) {
         double b = 0.0;
         for (int w = 0; w < STATIC_THREADS / 32; ++w) b = fmax(b, warp_max[w]);
-        *dt_out = b > 0.0 ? cfl / b : 0.0;
+        *dt_out = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : (b > 0.0 ? cfl / b : 0.0);
         scr->done = 0u;
     }
 }
@@ -105,11 +120,9 @@ extern "C" int ader_max_dt_static(const ader_grid* g, double gamma, const double
     {
         std::lock_guard<std::mutex> lock(g_setup_mutex);
         if (!g_scratch_ptr[dev]) {
-            // set-up on this device: device address of the array, counter cleared
+            // set-up on this device: the device address of the array (its counter starts at zero)
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_dt_scratch) != cudaSuccess || !p) return ADER_ERR_CUDA;
-            if (cudaMemset((char*)p + offsetof(StaticScratch, done), 0, sizeof(unsigned int)) != cudaSuccess)
-                return ADER_ERR_CUDA;
             g_scratch_ptr[dev] = (StaticScratch*)p;
         }
         scr = g_scratch_ptr[dev];

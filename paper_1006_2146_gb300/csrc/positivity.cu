@@ -5,7 +5,7 @@
 // every zone next to a marked one is then updated again from U^n with the stored fluxes, which both
 // zones of a face share, so the step stays conservative.  Three passes, the marks accumulating; a pass
 // with no mark changes nothing.  The update leaves the non-finite check to the fallback, which mends such
-// zones like non-physical ones and checks the state after its passes.
+// zones like non-physical ones and checks the state (and, for MHD, the face field) after its passes.
 #include "kernels.cuh"
 #include "riemann.cuh"
 #include "step_kernels.cuh"
@@ -101,14 +101,27 @@ __global__ void __launch_bounds__(128) k_pos_update(StepArgs a, double* U, const
     if (near) zone_flux_update_stored<double>(a, U, Uold, c_host, use_dt_dev, z);
 }
 
-// after the passes: a zone still not finite is an error of the step (the update deferred this check)
-__global__ void __launch_bounds__(256) k_pos_check(Grid g, const double* __restrict__ U, unsigned* flag) {
+// After the passes (the update deferred its own check to here): a zone value that is not finite raises
+// FLAG_NONFINITE, and so does, for MHD, a face field value that is not finite: the fallback replaces only
+// hydrodynamic face fluxes, so a non-finite edge field written by constrained transport survives its
+// passes.  A zone left finite but non-physical (rho <= 0 or P <= 0 after the third pass) raises
+// FLAG_UNPHYSICAL, so the step itself reports what the fallback could not mend.
+template <int NV>
+__global__ void __launch_bounds__(256) k_pos_check(Grid g, const double* __restrict__ U, const double* __restrict__ Bf,
+                                                   double gm1, unsigned* flag) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= g.n) return;
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < 5; ++v) bad |= !isfinite(U[v * g.n + z]);
-    if (bad) raise_flag(flag, FLAG_NONFINITE);
+    if constexpr (NV == 8) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bad |= !isfinite(Bf[c * g.n + z]);
+    }
+    if (bad)
+        raise_flag(flag, FLAG_NONFINITE);
+    else if (unphysical<NV>(g, U, Bf, z, gm1))
+        raise_flag(flag, FLAG_UNPHYSICAL);
 }
 
 }  // namespace
@@ -131,7 +144,10 @@ int launch_positivity_fallback(const StepArgs& a, double* U, const double* Uold,
         k_pos_update<<<b128, 128, 0, st>>>(a, U, Uold, mark, c_host, use_dt_dev ? 1 : 0);
         n += 3;
     }
-    k_pos_check<<<b256, 256, 0, st>>>(a.grid, U, a.flag);
+    if (a.mhd)
+        k_pos_check<8><<<b256, 256, 0, st>>>(a.grid, U, a.Bface, a.gm1, a.flag);
+    else
+        k_pos_check<5><<<b256, 256, 0, st>>>(a.grid, U, nullptr, a.gm1, a.flag);
     return n + 1;
 }
 

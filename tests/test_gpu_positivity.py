@@ -85,3 +85,90 @@ def test_mhd_fallback_parity(ader):
         assert rel_l1(to_host(dU), wU) <= 1e-12
         assert np.abs(to_host(dB) - wB).max() <= 1e-12 * np.abs(wB).max()
     s.close()
+
+
+def _mhd_physical(U, B):
+    zB = np.stack([0.5 * (B[d] + np.roll(B[d], -1, axis=2 - d)) for d in range(3)])
+    return physics.physical(np.concatenate([U, zB]), 1.4)
+
+
+def test_mhd_fallback_fires_on_the_magnetised_double_rarefaction(ader):
+    """The MHD parity case above is one where the fallback acts: the oracle's plain fourth-order MHD step
+    leaves a non-physical zone in one of its steps, and the GPU fallback step stays physical."""
+    n = 32
+    dx = (1 / n, 1.0, 1.0)
+    U = _double_rarefaction(n)
+    U[4] += 25.0 / (8.0 * np.pi)
+    z = np.zeros((1, 1, n))
+    B = np.stack([z, 5.0 + z, z])
+    s = ader.Solver((1, 1, n), order=4, form="modal", positivity=True, mhd=True)
+    dU, dB = to_dev(U), to_dev(B)
+    failed_plain = False
+    for _ in range(12):
+        Uh, Bh = to_host(dU), to_host(dB)
+        dt = scheme.max_dt(Uh, dx, 0.3, 1.4, Bface=Bh)
+        pU, pB = scheme.ader_step(Uh, dx, dt, 4, "modal", "hll", 1.4, Bface=Bh)
+        failed_plain |= not _mhd_physical(pU, pB).all()
+        s.step(dU, dt, Bface=dB)
+        assert s.status() == 0
+        assert _mhd_physical(to_host(dU), to_host(dB)).all()
+    s.close()
+    assert failed_plain
+
+
+@pytest.mark.parametrize("mhd", [False, True])
+def test_fallback_step_reports_a_non_finite_zone(ader, mhd):
+    """A NaN planted on the host in one zone of U cannot be mended (the first-order fluxes take U^n): the
+    step ends with ADER_ERR_NONFINITE, for Euler and MHD, and the context stays usable."""
+    shape = (6, 7, 8)
+    U = inputs.random_smooth(shape, seed=31, amp=0.2)
+    B = np.ones((3,) + shape) * 0.5 if mhd else None
+    if mhd:
+        U[4] += 3 * 0.25 / (8.0 * np.pi)
+    dx = (1 / 8, 1 / 7, 1 / 6)
+    dt = 0.5 * scheme.max_dt(U, dx, 0.4, 1.4, Bface=B) if mhd else 0.5 * scheme.max_dt(U, dx, 0.4)
+    bad = U.copy()
+    bad[0, 3, 3, 3] = np.nan
+    s = ader.Solver(shape, order=3, form="modal", positivity=True, mhd=mhd)
+    dU = to_dev(bad)
+    dB = to_dev(B) if mhd else None
+    s.step(dU, dt, Bface=dB)
+    assert s.status() == _lib.ADER_ERR_NONFINITE
+    # the context stays usable: a clean step afterwards reports nothing
+    dU = to_dev(U)
+    dB = to_dev(B) if mhd else None
+    s.step(dU, dt, Bface=dB)
+    assert s.status() == 0
+    s.close()
+
+
+def test_fallback_step_reports_a_non_finite_face_field(ader):
+    """MHD: a NaN planted on the host in the face field is reported by the step (ADER_ERR_NONFINITE)."""
+    shape = (6, 7, 8)
+    U = inputs.random_smooth(shape, seed=32, amp=0.2)
+    U[4] += 3 * 0.25 / (8.0 * np.pi)
+    B = np.ones((3,) + shape) * 0.5
+    dx = (1 / 8, 1 / 7, 1 / 6)
+    dt = 0.5 * scheme.max_dt(U, dx, 0.4, 1.4, Bface=B)
+    B[1, 2, 2, 2] = np.nan
+    s = ader.Solver(shape, order=3, form="modal", positivity=True, mhd=True)
+    dU, dB = to_dev(U), to_dev(B)
+    s.step(dU, dt, Bface=dB)
+    assert s.status() == _lib.ADER_ERR_NONFINITE
+    s.close()
+
+
+def test_fallback_step_reports_a_zone_it_cannot_mend(ader):
+    """A zone with negative pressure in U^n stays non-physical (its own first-order fluxes start from it):
+    the step ends with an error status (non-physical, or non-finite where its sound speed is not real)."""
+    shape = (6, 7, 8)
+    U = inputs.random_smooth(shape, seed=33, amp=0.2)
+    dx = (1 / 8, 1 / 7, 1 / 6)
+    dt = 0.5 * scheme.max_dt(U, dx, 0.4)
+    m = U[1:4, 2, 2, 2]
+    U[4, 2, 2, 2] = 0.5 * (m * m).sum() / U[0, 2, 2, 2] - 1e-3       # P < 0
+    s = ader.Solver(shape, order=3, form="modal", positivity=True)
+    dU = to_dev(U)
+    s.step(dU, dt)
+    assert s.status() in (_lib.ADER_ERR_UNPHYSICAL, _lib.ADER_ERR_NONFINITE)
+    s.close()

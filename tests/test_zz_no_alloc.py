@@ -1,4 +1,4 @@
-"""The allocation-free CFL entry point (ader_max_dt_static) against ader_max_dt.
+"""The allocation-free CFL entry point (ader_max_dt_static) against ader_max_dt and the oracle.
 
 Callers that cannot allocate device memory (inside another library's stream
 capture, fixed-budget real-time loops) use ader_max_dt_static: no context, the
@@ -41,18 +41,44 @@ def _static_dt(torch, lib, grid, U, cfl):
 def test_static_dt_matches_context_dt_twice(env, shape):
     torch, lib = env
     import paper_1006_2146_gb300 as ader
+    from oracle import scheme
     from paper_1006_2146_gb300 import _lib, inputs
     nz, ny, nx = shape
-    grid = _lib.ader_grid(nx, ny, nz, 1.0 / nx, 1.0 / ny, 1.0 / nz)
+    dx = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    grid = _lib.ader_grid(nx, ny, nz, *dx)
     s = ader.Solver(shape, order=3)
     for seed in (1, 2):                       # two calls in a row, different data
-        U = torch.from_numpy(inputs.random_smooth(shape, seed=seed, amp=0.4)).cuda()
+        Uh = inputs.random_smooth(shape, seed=seed, amp=0.4)
+        U = torch.from_numpy(Uh).cuda()
         ref = torch.zeros(1, dtype=torch.float64, device="cuda")
         s.max_dt(U, 0.4, ref)
         torch.cuda.synchronize()
         got = _static_dt(torch, lib, grid, U, 0.4)
         assert got == pytest.approx(float(ref.item()), rel=1e-14)
+        assert got == pytest.approx(scheme.max_dt(Uh, dx, 0.4), rel=1e-14)      # the oracle's CFL rule
     s.close()
+
+
+@pytest.mark.parametrize("where", ["negative_pressure", "nan_density"])
+def test_static_dt_reports_a_non_physical_zone(env, where):
+    """A zone without a real signal speed makes dt a quiet NaN; the next call on clean data is exact again."""
+    torch, lib = env
+    from oracle import scheme
+    from paper_1006_2146_gb300 import _lib, inputs
+    shape = (20, 30, 40)                       # several blocks of the reduction
+    nz, ny, nx = shape
+    dx = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    grid = _lib.ader_grid(nx, ny, nz, *dx)
+    Uh = inputs.random_smooth(shape, seed=5, amp=0.3)
+    bad = Uh.copy()
+    if where == "nan_density":
+        bad[0, 17, 3, 29] = np.nan
+    else:
+        m = bad[1:4, 17, 3, 29]
+        bad[4, 17, 3, 29] = 0.5 * (m * m).sum() / bad[0, 17, 3, 29] - 1e-6
+    assert np.isnan(_static_dt(torch, lib, grid, torch.from_numpy(bad).cuda(), 0.4))
+    got = _static_dt(torch, lib, grid, torch.from_numpy(Uh).cuda(), 0.4)
+    assert got == pytest.approx(scheme.max_dt(Uh, dx, 0.4), rel=1e-14)
 
 
 def test_static_dt_rejects_oversized_grid(env):
