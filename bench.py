@@ -171,13 +171,25 @@ def traffic_per_launch(kernel, order, form, fp32, zones):
     return rec["bytes_per_zone"] * zones
 
 
-def flops_per_zone(order, form, solver, fp32):
-    """Exact FLOPs per zone of each kernel (op-counting instantiation of the kernels' per-zone code)."""
+UPDATE_FLOPS = 3 * 5 * 3 + 5 * 2      # Eq. 6 from stored fluxes: per direction and variable a subtract, a
+                                      # multiply and a subtract, then base + c acc (the counter's "acc" term)
+
+
+def flops_per_zone(order, form, solver, fp32, tiled=True):
+    """Exact FLOPs per zone of each kernel (op-counting instantiation of the kernels' per-zone code).
+
+    Tiled layout (Euler, orders 2-3): the predictor kernel also solves each face once, so it carries the
+    face solves and the update kernel only Eq. 6 from the stored fluxes."""
     path = os.path.join(ROOT, "paper_1006_2146_gb300", "flops.json")
     if not os.path.exists(path):
         return {}
     with open(path) as fh:
         f = json.load(fh)["order%d" % order]
+    if tiled and order <= 3:
+        solves = f["riemann_update_" + solver] - UPDATE_FLOPS
+        return {"weno_reconstruction": f["weno_reconstruction"],
+                "predictor_faces": f["predictor_faces_" + form] + solves,
+                "riemann_update": UPDATE_FLOPS}
     return {"weno_reconstruction": f["weno_reconstruction"],
             "predictor_faces": f["predictor_faces_" + form],
             "riemann_update": f["riemann_update_" + ("fused_" if fp32 else "") + solver]}
@@ -718,14 +730,15 @@ def learned_variants(ader, torch, n, U0, stream, steps=3):
 
 
 def run_config(ader, torch, n, order, form, solver, fp32, steps, warmup, stream, profile=False, state=None,
-               tol=None, guess=None, source=None):
+               tol=None, guess=None, source=None, tiled=True):
     """Times `steps` steps of max_dt + step_devdt; returns (seconds, profile dict, solver, device state).
 
     tol: converged predictor (iterate to tol, at most 50 times); guess: learned-guess parameters (device);
-    source: (kind, params) of Solver.set_source.
+    source: (kind, params) of Solver.set_source; tiled: the Euler launch layout (ader_set_tiled).
     """
     from paper_1006_2146_gb300 import inputs
     s = ader.Solver((n, n, n), order=order, form=form, solver=solver, fp32=fp32)
+    s.set_tiled(tiled)
     if source is not None:
         s.set_source(*source)
     if tol is not None:
@@ -868,15 +881,19 @@ def gpu_arm(args):
             vs.append(("fp32_modal_hll_o%d" % order, order, "modal", "hll", True))
         vs += [("fp64_nodal_linearized_o3", 3, "nodal", "linearized", False),
                ("fp32_nodal_hll_o3", 3, "nodal", "hll", True)]
-        vs = [v + (None,) for v in vs]
+        vs = [v + (None, True) for v in vs]
         # the same step with a non-stiff source (uniform gravity): its cost in the predictor
         grav = ("gravity", (0.0, 0.0, -1.0))
-        vs += [("fp64_nodal_hll_o3_gravity", 3, "nodal", "hll", False, grav),
-               ("fp32_nodal_hll_o3_gravity", 3, "nodal", "hll", True, grav)]
-        for name, order, form, solver, fp32, src in vs:
+        vs += [("fp64_nodal_hll_o3_gravity", 3, "nodal", "hll", False, grav, True),
+               ("fp32_nodal_hll_o3_gravity", 3, "nodal", "hll", True, grav, True)]
+        # the per-zone layout (face data of every zone through memory) beside the default tiles
+        vs += [("fp32_nodal_hll_o3_per_zone_layout", 3, "nodal", "hll", True, None, False),
+               ("fp32_modal_hll_o2_per_zone_layout", 2, "modal", "hll", True, None, False),
+               ("fp64_nodal_hll_o3_per_zone_layout", 3, "nodal", "hll", False, None, False)]
+        for name, order, form, solver, fp32, src, tiled in vs:
             try:
                 vsecs, vprof, vs_, _, _ = run_config(ader, torch, n, order, form, solver, fp32, 3, 1, stream,
-                                                     profile=True, state=U0, source=src)
+                                                     profile=True, state=U0, source=src, tiled=tiled)
                 vs_.close()
                 variants[name] = {"zone_updates_per_s": zones * 3 / vsecs, "ms_per_step": vsecs / 3 * 1e3,
                                   "kernel_ms": {k: round(v[1] / v[0], 3) for k, v in vprof.items()}}

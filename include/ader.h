@@ -167,6 +167,19 @@ int ader_profile_read(ader_ctx* ctx, const char** names, int* launches, double* 
  * zones and steps, largest count, zones capped} to out3_host and clears them
  * (synchronises the stream). */
 int ader_set_predictor(ader_ctx* ctx, double tol, int max_iter);
+
+/* Launch layout of the Euler step at orders 2 and 3 (Sec. II's per-zone
+ * pipeline: predictor,
+ * face quadrature, Riemann solve, Eq. 6).  on = 1 (the default): a block owns
+ * a 32 x 4 tile of columns and marches through z; the six face sides of each
+ * zone stay in shared memory, every face inside the tile is solved once, and
+ * only the tile's boundary sides pass through memory.  on = 0: every zone
+ * writes its face data to the context's scratch and a second pass solves the
+ * faces.  Both give the same numbers bit for bit; MHD contexts and order 4
+ * always take the second layout (the edge fields need the face data of four
+ * zones; the fourth-order predictor's cost dwarfs the face data's traffic).
+ * ADER_ERR_ARG for a NULL context. */
+int ader_set_tiled(ader_ctx* ctx, int on);
 int ader_predictor_stats(ader_ctx* ctx, unsigned long long* out3_host, void* stream);
 
 /* Non-stiff source term S(U) of Eq. 4 (Sec. II; orders 2-4, modal and

@@ -14,7 +14,7 @@ from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_EMF_TRANSONIC, ADER_FP32_BULK,
                    ader_guess_eval, ader_guess_samples, ader_last_error, ader_launches_per_step, ader_max_dt,
                    ader_mlp_grad, ader_mlp_shape, ader_mlp_train, ader_predictor_stats, ader_profile,
                    ader_profile_read, ader_profile_reset, ader_rk_step, ader_set_dense_output, ader_set_guess,
-                   ader_set_predictor, ader_set_source, ader_step, ader_step_devdt, ader_step_host,
+                   ader_set_predictor, ader_set_source, ader_set_tiled, ader_step, ader_step_devdt, ader_step_host,
                    ader_sync_status, load)
 
 
@@ -48,6 +48,9 @@ class Solver:
 
     def rk_step(self, U, dt, stream=None, Bface=None):
         ader_rk_step(self.h, U, Bface, dt, stream)
+
+    def set_tiled(self, on):
+        ader_set_tiled(self.h, on)
 
     def set_predictor(self, tol, max_iter=50):
         ader_set_predictor(self.h, tol, max_iter)

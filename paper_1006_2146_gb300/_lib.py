@@ -20,7 +20,7 @@ ADER_SOURCE_NONE, ADER_SOURCE_LINEAR, ADER_SOURCE_GRAVITY = 0, 1, 2
 
 EXPORTS = ("ader_create", "ader_step", "ader_step_devdt", "ader_max_dt", "ader_rk_step", "ader_step_host",
            "ader_diagnostics", "ader_sync_status", "ader_launches_per_step", "ader_profile", "ader_profile_reset",
-           "ader_profile_read", "ader_set_predictor", "ader_predictor_stats", "ader_set_source", "ader_set_dense_output", "ader_dense_output", "ader_set_guess",
+           "ader_profile_read", "ader_set_tiled", "ader_set_predictor", "ader_predictor_stats", "ader_set_source", "ader_set_dense_output", "ader_dense_output", "ader_set_guess",
            "ader_mlp_shape", "ader_guess_samples", "ader_guess_count", "ader_guess_eval", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy",
            "ader_max_dt_static", "ader_batch_create", "ader_batch_tune", "ader_batch_step", "ader_batch_advance",
            "ader_batch_status", "ader_batch_tuning", "ader_batch_groups", "ader_batch_last_error",
@@ -64,6 +64,7 @@ def load(path=None):
     lib.ader_profile_reset.argtypes = [vp]
     lib.ader_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32),
                                       ctypes.POINTER(dbl), i32]
+    lib.ader_set_tiled.argtypes = [vp, i32]
     lib.ader_set_predictor.argtypes = [vp, dbl, i32]
     lib.ader_predictor_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), vp]
     lib.ader_set_guess.argtypes = [vp, vp]
@@ -193,6 +194,11 @@ def ader_profile_read(h):
     if n < 0:
         _check(h, n)
     return {names[k].decode(): (counts[k], ms[k]) for k in range(min(n, cap))}
+
+
+def ader_set_tiled(h, on):
+    """Euler launch layout: 1 = per-tile predictor and face solves (default), 0 = face data through memory."""
+    return _check(h, load().ader_set_tiled(h, 1 if on else 0))
 
 
 def ader_set_predictor(h, tol, max_iter):

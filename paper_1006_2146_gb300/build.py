@@ -15,7 +15,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libader_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
+         # FP32 division, reciprocal and square root by the hardware approximations (a few ulp), FP32
+         # denormals flushed; FP64 arithmetic is unaffected by these three switches
+         "-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
 
 
 def _nvcc():

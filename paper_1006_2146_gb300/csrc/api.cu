@@ -36,6 +36,7 @@ struct ader_ctx {
     double* rkB[6] = {};                      // MHD: SSP-RK stage face fields and the stored operator
     double tol = 0.0;                         // converged predictor tolerance (0: fixed M-1 iterations)
     int max_iter = 50;
+    bool tiled = true;                        // Euler: per-tile predictor and face solves (ader_set_tiled)
     unsigned long long* stats = nullptr;      // converged predictor statistics (3 words)
     const float* guess = nullptr;             // learned-guess MLP parameters (device), order 3
     float* G = nullptr;                       // per-zone learned guess (5 x NV x N FP32), allocated by ader_set_guess
@@ -142,6 +143,7 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.modes_out = nullptr;
     a.emf_transonic = (c->flags & ADER_EMF_TRANSONIC) ? 1 : 0;
     a.defer_nonfinite = 0;
+    a.tiled = (!c->mhd && c->tiled) ? 1 : 0;
     return a;
 }
 
@@ -486,6 +488,12 @@ int ader_rk_step(ader_ctx* c, double* U, double* Bface, double dt, void* stream)
     }
     c->launches = n + 1;
     return cuda_check(c, cudaGetLastError(), "ader_rk_step launch");
+}
+
+int ader_set_tiled(ader_ctx* c, int on) {
+    if (!c) return ADER_ERR_ARG;
+    c->tiled = on != 0;
+    return ADER_OK;
 }
 
 int ader_set_predictor(ader_ctx* c, double tol, int max_iter) {

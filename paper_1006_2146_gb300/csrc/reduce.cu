@@ -15,16 +15,34 @@ namespace ader {
 // S is the precision of the per-zone signal speed: FP64, or FP32 for FP32-bulk
 // contexts (there FP64's division and square root would dominate the kernel);
 // the maximum, its reduction and dt are FP64 in both.
+// The state in the precision S of the signal speeds.  FP32: the FP64 significand is truncated to FP32's
+// (at most one unit in FP32's last place off) with integer operations, because GB300's conversion
+// instruction runs on the scarce FP64 units; values outside FP32's normal range take the conversion.
+template <class S>
+__device__ __forceinline__ S speed_operand(double x) {
+    if constexpr (sizeof(S) == 4) {
+        const long long b = __double_as_longlong(x);
+        const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+        const int e = (int)((hi >> 20) & 0x7ffu) - 896;          // FP64 exponent rebased to FP32's bias
+        if (e <= 0 || e >= 255) return (float)x;
+        return __int_as_float((int)((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)));
+    } else {
+        return x;
+    }
+}
+
 template <class S>
 __global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict__ U, const double* __restrict__ Bf,
                                                 double gamma, double idx, double idy, double idz, double cfl,
                                                 double* dt_out, unsigned long long* scratch, unsigned* flag) {
-    double s = 0.0;
+    S sm = S(0);                       // the largest signal-speed sum of this thread, in S (FP64 below)
     bool bad = false;
     const long long N = g.n;
     const S gm = S(gamma), ix = S(idx), iy = S(idy), iz = S(idz);
+#pragma unroll 2
     for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < N; z += (long long)gridDim.x * blockDim.x) {
-        const S rho = S(U[z]), mx = S(U[N + z]), my = S(U[2 * N + z]), mz = S(U[3 * N + z]), E = S(U[4 * N + z]);
+        const S rho = speed_operand<S>(U[z]), mx = speed_operand<S>(U[N + z]), my = speed_operand<S>(U[2 * N + z]),
+                mz = speed_operand<S>(U[3 * N + z]), E = speed_operand<S>(U[4 * N + z]);
         const S ir = S(1) / rho;
         const S vx = mx * ir, vy = my * ir, vz = mz * ir;
         S v;
@@ -52,8 +70,9 @@ __global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict
             const S a = sqrt(gm * p * ir);
             v = (fabs(vx) + a) * ix + (fabs(vy) + a) * iy + (fabs(vz) + a) * iz;
         }
-        s = fmax(s, (double)v);
+        sm = fmax(sm, v);
     }
+    double s = (double)sm;
     if (bad) raise_flag(flag, FLAG_UNPHYSICAL);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
@@ -230,15 +249,22 @@ int launch_flux_update(const StepArgs& a, double* out, const double* base, doubl
     const int T = 128;
     const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
     const int dd = use_dt_dev ? 1 : 0;
-    if constexpr (sizeof(R) == 4) {           // fused: the FP64 accumulation bounds it, not the solves
-        if (a.mhd && a.solver == SOLVER_HLL)
-            k_flux_update<SOLVER_HLL, 8, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
-        else if (a.mhd)
-            k_flux_update<SOLVER_LINEARIZED, 8, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
-        else if (a.solver == SOLVER_HLL)
-            k_flux_update<SOLVER_HLL, 5, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+    if (!a.mhd && a.order <= 3 && a.tiled) {   // the tile kernel stored every face flux once
+        if constexpr (sizeof(R) == 4)
+            k_flux_update_stored_pair<R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
         else
-            k_flux_update<SOLVER_LINEARIZED, 5, R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+            k_flux_update_stored<R><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+        return 1;
+    }
+    if constexpr (sizeof(R) == 4) {           // fused, both faces of each direction per zone, FP32 pairs
+        if (a.mhd && a.solver == SOLVER_HLL)
+            k_flux_update_pair<SOLVER_HLL, 8><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+        else if (a.mhd)
+            k_flux_update_pair<SOLVER_LINEARIZED, 8><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+        else if (a.solver == SOLVER_HLL)
+            k_flux_update_pair<SOLVER_HLL, 5><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
+        else
+            k_flux_update_pair<SOLVER_LINEARIZED, 5><<<blocks, T, 0, st>>>(a, out, base, c_host, dd);
         return 1;
     } else {                                   // each face solved once, then the update
         if (a.mhd && a.solver == SOLVER_HLL)

@@ -138,12 +138,14 @@ ADER_DEV void record_iterations(unsigned long long* stats, const PredCtl& ctl) {
 #endif
 }
 
+// The ADER-CG predictor of zone z (Sec. II.2): the spatial modes, the learned or zero initial guess of
+// the evolutionary modes, the iteration, and what the step keeps besides the face data (dt S-bar with a
+// source, the whole space-time polynomial for dense output).  m[1..L] holds the space-time modes after.
 // SRC: the context carries a non-stiff source (orders with ZoneOps::HAS_SOURCE); the predictor then also
 // writes dt S-bar of Eq. 6 for the update (a.Sb).
 template <int ORDER, int FORM, int NV, class R, bool SRC = false>
-ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U, long long z) {
+ADER_DEV void zone_predict(const StepArgs& a, const double* __restrict__ U, long long z, Vec<NV, R>* m) {
     constexpr int LS = ModeCount<ORDER>::LS, L = ModeCount<ORDER>::L;
-    Vec<NV, R> m[L + 1];
     load_modes<ORDER>(a, U, z, m);
 #pragma unroll
     for (int k = LS + 1; k <= L; ++k) m[k] = vzero<NV, R>();
@@ -188,6 +190,13 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
 #pragma unroll
             for (int v = 0; v < NV; ++v) o[(long long)((k - 1) * NV + v) * a.grid.n + z] = m[k][v];
     }
+}
+
+template <int ORDER, int FORM, int NV, class R, bool SRC = false>
+ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U, long long z) {
+    Vec<NV, R> m[ModeCount<ORDER>::L + 1];
+    zone_predict<ORDER, FORM, NV, R, SRC>(a, U, z, m);
+    const R gm1 = arg_gm1<R>(a);
     store_faces<ORDER, 0>(a, z, m, gm1);
     store_faces<ORDER, 1>(a, z, m, gm1);
     store_faces<ORDER, 2>(a, z, m, gm1);
@@ -285,6 +294,84 @@ __global__ void __launch_bounds__(128) k_flux_update(StepArgs a, double* out, co
     if (z < a.grid.n) zone_flux_update<SOLVER, NV, R>(a, out, base, c_host, use_dt_dev, z);
 }
 
+// ------------------------------------------------------------------ FP32 bulk: Eq. 6 without FP64 arithmetic per face
+// GB300 runs FP64 at 1/64 of the FP32 rate, so converting and differencing the twelve face fluxes of a
+// zone in FP64 (about 70 FP64 instructions) bounded the FP32-bulk update.  Here the flux differences
+// and their scaling by c_d = dt / dx_d are carried exactly in pairs of FP32 numbers (error-free
+// transformations: Knuth's two-sum for Fm - Fp, the FMA two-product for s * c_d), so that the zone's
+// increment sum_d c_d (Fm - Fp) reaches FP64 as hi + lo with a relative error near 2^-47, and only the
+// accumulation U + hi + lo (and the source term) is FP64: 4 FP64 operations per variable.  c_d is split
+// once per block into its FP32 head and tail.
+ADER_DEV void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// true when the FP64 value is finite (exponent field not all ones), without an FP64 instruction
+ADER_DEV bool finite_bits(double x) {
+#ifdef __CUDA_ARCH__
+    return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
+#else
+    return isfinite(x);
+#endif
+}
+
+template <int SOLVER, int D, int NV>
+ADER_DEV void flux_difference_pair(const StepArgs& a, long long z, int i, int j, int k, float gamma, float gm1,
+                                   float chi, float clo, float* hi, float* lo) {
+    const long long zm = nbr_along(a.grid, z, i, j, k, D, -1);
+    const Vec<NV, float> Fp = upper_face_flux<SOLVER, D, NV, float>(a, z, i, j, k, gamma, gm1);
+    const Vec<NV, float> Fm = riemann<SOLVER, D>(load_side<NV, float>(a, 2 * D, zm),
+                                                 load_side<NV, float>(a, 2 * D + 1, z), gamma, gm1);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        float s, e;
+        two_sum(Fm[v], -Fp[v], s, e);                   // Fm - Fp = s + e exactly
+        const float p = s * chi;
+        const float pe = fmaf(s, chi, -p);              // s chi = p + pe exactly
+        const float t = pe + fmaf(s, clo, e * chi);     // the small terms of (s + e)(chi + clo)
+        float h, he;
+        two_sum(hi[v], p, h, he);
+        hi[v] = h;
+        lo[v] += he + t;
+    }
+}
+
+template <int SOLVER, int NV>
+__global__ void __launch_bounds__(128) k_flux_update_pair(StepArgs a, double* out, const double* base, double c_host,
+                                                          int use_dt_dev) {
+    __shared__ float c_hi[3], c_lo[3];
+    if (threadIdx.x < 3) {
+        const double c = use_dt_dev ? c_host * (*a.dt_dev) : c_host;
+        const double cd = c * a.idx[threadIdx.x];
+        const float h = (float)cd;
+        c_hi[threadIdx.x] = h;
+        c_lo[threadIdx.x] = (float)(cd - (double)h);
+    }
+    __syncthreads();
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= a.grid.n) return;
+    int i, j, k;
+    zone_ijk(a.grid, z, i, j, k);
+    const float gamma = a.gamma_f, gm1 = a.gm1_f;
+    float hi[5] = {0, 0, 0, 0, 0}, lo[5] = {0, 0, 0, 0, 0};
+    flux_difference_pair<SOLVER, 0, NV>(a, z, i, j, k, gamma, gm1, c_hi[0], c_lo[0], hi, lo);
+    flux_difference_pair<SOLVER, 1, NV>(a, z, i, j, k, gamma, gm1, c_hi[1], c_lo[1], hi, lo);
+    flux_difference_pair<SOLVER, 2, NV>(a, z, i, j, k, gamma, gm1, c_hi[2], c_lo[2], hi, lo);
+    const long long N = a.grid.n;
+    const float* Sb = (const float*)a.Sb;
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        double val = (base ? base[v * N + z] : 0.0) + ((double)hi[v] + (double)lo[v]);
+        if (Sb) val += (double)Sb[v * N + z];
+        bad |= !finite_bits(val);
+        out[v * N + z] = val;
+    }
+    if (bad && !a.defer_nonfinite) raise_flag(a.flag, FLAG_NONFINITE);
+}
+
 template <int SOLVER, int NV, class R>
 ADER_DEV void zone_face_fluxes(const StepArgs& a, long long z) {
     int i, j, k;
@@ -333,6 +420,275 @@ __global__ void __launch_bounds__(128) k_flux_update_stored(StepArgs a, double* 
                                                             double c_host, int use_dt_dev) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z < a.grid.n) zone_flux_update_stored<R>(a, out, base, c_host, use_dt_dev, z);
+}
+
+// ------------------------------------------------------------------ Euler: predictor and face solves per tile
+// A block owns a PT_X x PT_Y tile of (x, y) columns and marches through a chunk of z planes, one zone per
+// thread and plane.  Each zone's predictor writes its six face sides (barycentre state, <u>, <F>; 15
+// values each) to shared memory; after a barrier every face inside the tile is solved once, by the zone
+// above it, with the side of the zone below it read from shared memory (x, y) or kept from the previous
+// plane (z), and the flux is stored at the lower zone, as k_face_fluxes does: F[(D*5 + v)*N + zone] is the
+// flux through the upper face of zone in direction D, in the WENO scratch S1 (each zone's modes were read
+// before any flux lands on its slots).  Only the sides of the tile's and chunk's boundary zones go to
+// S3, and k_tile_faces solves those faces afterwards.  The face data of the interior never reaches HBM,
+// and no zone is predicted twice.
+constexpr int PT_X = 32, PT_Y = 4, PT_THREADS = PT_X * PT_Y;
+constexpr int PT_NQ = 15;                     // values per Euler face side
+constexpr int PT_SLOTS = 7;                   // x+, x-, y+, y-, z+ (even planes), z-, z+ (odd planes)
+
+template <class R>
+ADER_DEV R* pt_slot(R* sh, int slot, int tid) { return sh + slot * PT_NQ * PT_THREADS + tid; }
+
+// one side into a slot: u_b (replaced by the zone mean for the wave speeds when not physical, as
+// write_side does), <u>, <F>
+template <class R>
+ADER_DEV void pt_side(R* dst, const Vec<5, R>& mean, Vec<5, R> ub, const Vec<5, R>& avg, const Vec<5, R>& Fa, R gm1) {
+    const Prim<5, R> q = primitives(ub, gm1);
+    if (!(ub[0] > R(0)) || !(q.p > R(0))) ub = mean;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        dst[v * PT_THREADS] = ub[v];
+        dst[(5 + v) * PT_THREADS] = avg[v];
+        dst[(10 + v) * PT_THREADS] = Fa[v];
+    }
+}
+
+template <int ORDER, int D, class R>
+ADER_DEV void pt_sides(R* sh, int tid, int slot_plus, int slot_minus, const Vec<5, R>* m, R gm1) {
+    constexpr int L = ModeCount<ORDER>::L;
+    if constexpr (ZoneOps<ORDER>::HAS_FACE_PAIR) {
+        Vec<5, R> p[L + 1];
+        to_face_frame<ORDER, D, +1>(m, p);
+        Vec<5, R> ub[2], avg[2], Fa[2];
+        ZoneOps<ORDER>::template face_pair<D>(p, gm1, ub, avg, Fa);
+        pt_side(pt_slot(sh, slot_plus, tid), m[1], ub[0], avg[0], Fa[0], gm1);
+        pt_side(pt_slot(sh, slot_minus, tid), m[1], ub[1], avg[1], Fa[1], gm1);
+    } else {
+        {
+            Vec<5, R> p[L + 1];
+            to_face_frame<ORDER, D, +1>(m, p);
+            Vec<5, R> ub, avg, Fa;
+            ZoneOps<ORDER>::template face<D>(p, gm1, ub, avg, Fa);
+            pt_side(pt_slot(sh, slot_plus, tid), m[1], ub, avg, Fa, gm1);
+        }
+        {
+            Vec<5, R> p[L + 1];
+            to_face_frame<ORDER, D, -1>(m, p);
+            Vec<5, R> ub, avg, Fa;
+            ZoneOps<ORDER>::template face<D>(p, gm1, ub, avg, Fa);
+            pt_side(pt_slot(sh, slot_minus, tid), m[1], ub, avg, Fa, gm1);
+        }
+    }
+}
+
+template <class R>
+ADER_DEV FaceSide<5, R> pt_load(const R* sh, int slot, int tid) {
+    const R* s = sh + slot * PT_NQ * PT_THREADS + tid;
+    FaceSide<5, R> f;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        f.ub[v] = s[v * PT_THREADS];
+        f.avg[v] = s[(5 + v) * PT_THREADS];
+        f.F[v] = s[(10 + v) * PT_THREADS];
+    }
+    return f;
+}
+
+// a side of a boundary zone to S3 (layout of the file header), for k_tile_faces
+template <class R>
+ADER_DEV void pt_to_s3(const StepArgs& a, const R* sh, int slot, int tid, int side, long long z) {
+    R* S3 = (R*)a.S3;
+    const long long N = a.grid.n;
+    const R* s = sh + slot * PT_NQ * PT_THREADS + tid;
+#pragma unroll
+    for (int q = 0; q < PT_NQ; ++q) S3[(side * PT_NQ + q) * N + z] = s[q * PT_THREADS];
+}
+
+template <int D, class R>
+ADER_DEV void pt_store_flux(const StepArgs& a, long long zl, const Vec<5, R>& f) {
+    R* F = (R*)a.S1;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[(D * 5 + v) * a.grid.n + zl] = f[v];
+}
+
+// grid: (tiles_x * tiles_y, ceil(nz / cz)); dynamic shared memory PT_SLOTS * PT_NQ * PT_THREADS values of R
+template <int ORDER, int FORM, int SOLVER, class R, bool SRC>
+__global__ void __launch_bounds__(PT_THREADS, sizeof(R) == 4 ? 3 : 1)
+    k_pf_tile(StepArgs a, const double* __restrict__ U, int cz) {
+    extern __shared__ __align__(16) unsigned char pt_raw[];
+    R* sh = reinterpret_cast<R*>(pt_raw);
+    const Grid& g = a.grid;
+    const int tid = threadIdx.x, tx = tid % PT_X, ty = tid / PT_X;
+    const int tiles_x = (g.nx + PT_X - 1) / PT_X;
+    const int i = (int)(blockIdx.x % tiles_x) * PT_X + tx, j = (int)(blockIdx.x / tiles_x) * PT_Y + ty;
+    const int k0 = (int)blockIdx.y * cz, k1 = min(k0 + cz, g.nz);
+    const bool valid = i < g.nx && j < g.ny;
+    const bool last_x = tx == PT_X - 1 || i == g.nx - 1, last_y = ty == PT_Y - 1 || j == g.ny - 1;
+    const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
+    const long long nxy = (long long)g.nx * g.ny;
+    for (int k = k0; k < k1; ++k) {
+        const long long z = (long long)k * nxy + (long long)j * g.nx + i;
+        const int zp_slot = (k & 1) ? 6 : 4;          // this plane's z+ sides; the previous plane's in the other
+        if (valid) {
+            Vec<5, R> m[ModeCount<ORDER>::L + 1];
+            zone_predict<ORDER, FORM, 5, R, SRC>(a, U, z, m);
+            pt_sides<ORDER, 0>(sh, tid, 0, 1, m, gm1);
+            pt_sides<ORDER, 1>(sh, tid, 2, 3, m, gm1);
+            pt_sides<ORDER, 2>(sh, tid, zp_slot, 5, m, gm1);
+        }
+        __syncthreads();
+        if (valid) {
+            if (tx > 0)                                // face i - 1/2: x+ side of the zone on the left
+                pt_store_flux<0>(a, z - 1, riemann<SOLVER, 0>(pt_load(sh, 0, tid - 1), pt_load(sh, 1, tid), gamma, gm1));
+            else
+                pt_to_s3(a, sh, 1, tid, 1, z);
+            if (last_x) pt_to_s3(a, sh, 0, tid, 0, z);
+            if (ty > 0)
+                pt_store_flux<1>(a, z - g.nx,
+                                 riemann<SOLVER, 1>(pt_load(sh, 2, tid - PT_X), pt_load(sh, 3, tid), gamma, gm1));
+            else
+                pt_to_s3(a, sh, 3, tid, 3, z);
+            if (last_y) pt_to_s3(a, sh, 2, tid, 2, z);
+            if (k > k0)
+                pt_store_flux<2>(a, z - nxy,
+                                 riemann<SOLVER, 2>(pt_load(sh, 10 - zp_slot, tid), pt_load(sh, 5, tid), gamma, gm1));
+            else
+                pt_to_s3(a, sh, 5, tid, 5, z);
+            if (k == k1 - 1) pt_to_s3(a, sh, zp_slot, tid, 4, z);
+        }
+        __syncthreads();
+    }
+}
+
+// The faces on tile and chunk boundaries, from the sides k_pf_tile left in S3: the tile boundaries in x
+// (i = multiples of PT_X, and i = 0 against nx - 1), in y (multiples of PT_Y) and the chunk boundaries in
+// z (multiples of cz).  One thread per face.
+template <int SOLVER, class R>
+__global__ void __launch_bounds__(128) k_tile_faces(StepArgs a, int cz, long long nfx, long long nfy, long long nfz) {
+    const Grid& g = a.grid;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
+    const long long nxy = (long long)g.nx * g.ny;
+    if (t < nfx) {                      // x: (tile, j, k)
+        const int ntx = (g.nx + PT_X - 1) / PT_X;
+        const int tile = (int)(t % ntx);
+        const long long r = t / ntx;
+        const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+        const int i = tile * PT_X, il = i == 0 ? g.nx - 1 : i - 1;
+        const long long row = (long long)k * nxy + (long long)j * g.nx;
+        pt_store_flux<0>(a, row + il,
+                         riemann<SOLVER, 0>(load_side<5, R>(a, 0, row + il), load_side<5, R>(a, 1, row + i), gamma, gm1));
+        return;
+    }
+    t -= nfx;
+    if (t < nfy) {                      // y: (i, tile, k)
+        const int nty = (g.ny + PT_Y - 1) / PT_Y;
+        const int i = (int)(t % g.nx);
+        const long long r = t / g.nx;
+        const int tile = (int)(r % nty), k = (int)(r / nty);
+        const int j = tile * PT_Y, jl = j == 0 ? g.ny - 1 : j - 1;
+        const long long pl = (long long)k * nxy + i;
+        pt_store_flux<1>(a, pl + (long long)jl * g.nx,
+                         riemann<SOLVER, 1>(load_side<5, R>(a, 2, pl + (long long)jl * g.nx),
+                                            load_side<5, R>(a, 3, pl + (long long)j * g.nx), gamma, gm1));
+        return;
+    }
+    t -= nfy;
+    if (t < nfz) {                      // z: (i, j, chunk)
+        const long long col = t % nxy;
+        const int chunk = (int)(t / nxy);
+        const int k = chunk * cz, kl = k == 0 ? g.nz - 1 : k - 1;
+        pt_store_flux<2>(a, (long long)kl * nxy + col,
+                         riemann<SOLVER, 2>(load_side<5, R>(a, 4, (long long)kl * nxy + col),
+                                            load_side<5, R>(a, 5, (long long)k * nxy + col), gamma, gm1));
+    }
+}
+
+// z planes per chunk: enough blocks for every SM to hold several, at most 16 planes
+inline int pt_chunk(const Grid& g) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = (long long)((g.nx + PT_X - 1) / PT_X) * ((g.ny + PT_Y - 1) / PT_Y);
+    long long cz = tiles * g.nz / ((long long)sms * 12);
+    if (cz < 1) cz = 1;
+    if (cz > 16) cz = 16;
+    return (int)cz;
+}
+
+template <int ORDER, int FORM, class R, bool SRC>
+void launch_pf_tile(const StepArgs& a, const double* U, cudaStream_t st) {
+    const Grid& g = a.grid;
+    const int cz = pt_chunk(g);
+    const int ntx = (g.nx + PT_X - 1) / PT_X, nty = (g.ny + PT_Y - 1) / PT_Y, ncz = (g.nz + cz - 1) / cz;
+    const size_t smem = (size_t)PT_SLOTS * PT_NQ * PT_THREADS * sizeof(R);
+    const dim3 grid((unsigned)(ntx * nty), (unsigned)ncz);
+    const long long nfx = (long long)ntx * g.ny * g.nz, nfy = (long long)nty * g.nx * g.nz,
+                    nfz = (long long)ncz * g.nx * g.ny;
+    const long long nf = nfx + nfy + nfz;
+    const unsigned fblocks = (unsigned)((nf + 127) / 128);
+    if (a.solver == SOLVER_HLL) {
+        auto kern = k_pf_tile<ORDER, FORM, SOLVER_HLL, R, SRC>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, PT_THREADS, smem, st>>>(a, U, cz);
+        k_tile_faces<SOLVER_HLL, R><<<fblocks, 128, 0, st>>>(a, cz, nfx, nfy, nfz);
+    } else {
+        auto kern = k_pf_tile<ORDER, FORM, SOLVER_LINEARIZED, R, SRC>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, PT_THREADS, smem, st>>>(a, U, cz);
+        k_tile_faces<SOLVER_LINEARIZED, R><<<fblocks, 128, 0, st>>>(a, cz, nfx, nfy, nfz);
+    }
+}
+
+// FP32 bulk, Eq. 6 from the stored face fluxes (tiled path): the differences in FP32 pairs as in
+// k_flux_update_pair, the accumulation in FP64
+template <class R>
+__global__ void __launch_bounds__(128) k_flux_update_stored_pair(StepArgs a, double* out, const double* base,
+                                                                 double c_host, int use_dt_dev) {
+    static_assert(sizeof(R) == 4, "FP32 bulk only");
+    __shared__ float c_hi[3], c_lo[3];
+    if (threadIdx.x < 3) {
+        const double c = use_dt_dev ? c_host * (*a.dt_dev) : c_host;
+        const double cd = c * a.idx[threadIdx.x];
+        const float h = (float)cd;
+        c_hi[threadIdx.x] = h;
+        c_lo[threadIdx.x] = (float)(cd - (double)h);
+    }
+    __syncthreads();
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= a.grid.n) return;
+    int i, j, k;
+    zone_ijk(a.grid, z, i, j, k);
+    const float* F = (const float*)a.S1;
+    const long long N = a.grid.n;
+    float hi[5] = {0, 0, 0, 0, 0}, lo[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int D = 0; D < 3; ++D) {
+        const long long zm = nbr_along(a.grid, z, i, j, k, D, -1);
+        const float chi = c_hi[D], clo = c_lo[D];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            float s, e;
+            two_sum(F[(D * 5 + v) * N + zm], -F[(D * 5 + v) * N + z], s, e);
+            const float p = s * chi;
+            const float pe = fmaf(s, chi, -p);
+            const float t = pe + fmaf(s, clo, e * chi);
+            float h, he;
+            two_sum(hi[v], p, h, he);
+            hi[v] = h;
+            lo[v] += he + t;
+        }
+    }
+    const float* Sb = (const float*)a.Sb;
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        double val = (base ? base[v * N + z] : 0.0) + ((double)hi[v] + (double)lo[v]);
+        if (Sb) val += (double)Sb[v * N + z];
+        bad |= !finite_bits(val);
+        out[v * N + z] = val;
+    }
+    if (bad && !a.defer_nonfinite) raise_flag(a.flag, FLAG_NONFINITE);
 }
 
 // ------------------------------------------------------------------ MHD: edge EMFs (Sec. II.3, Eq. 7)
@@ -470,6 +826,12 @@ __global__ void __launch_bounds__(128) k_ct(StepArgs a, double* Bf, double c_hos
 // build's longest compile short.
 template <int ORDER, int FORM, int NV, class R, bool SRC>
 void launch_pf_variant(const StepArgs& a, const double* U, cudaStream_t st) {
+    if constexpr (NV == 5 && ORDER <= 3) {
+        if (a.tiled) {
+            launch_pf_tile<ORDER, FORM, R, SRC>(a, U, st);
+            return;
+        }
+    }
     const int T = 128;
     const unsigned blocks = (unsigned)((a.grid.n + T - 1) / T);
     k_predict_faces<ORDER, FORM, NV, R, SRC><<<blocks, T, 0, st>>>(a, U);
@@ -481,11 +843,11 @@ int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st)
         if (a.src_kind != SOURCE_NONE && a.Sb && a.n_iter > 0) {
             if (a.form == FORM_NODAL) {
                 launch_pf_variant<ORDER, FORM_NODAL, NV, R, true>(a, U, st);
-                return 1;
+                return (NV == 5 && ORDER <= 3 && a.tiled) ? 2 : 1;
             }
             if constexpr (ZoneOps<ORDER>::HAS_SOURCE_MODAL) {
                 launch_pf_variant<ORDER, FORM_MODAL, NV, R, true>(a, U, st);
-                return 1;
+                return (NV == 5 && ORDER <= 3 && a.tiled) ? 2 : 1;
             }
         }
     }
@@ -493,7 +855,7 @@ int launch_predict_faces_nv(const StepArgs& a, const double* U, cudaStream_t st)
         launch_pf_variant<ORDER, FORM_MODAL, NV, R, false>(a, U, st);
     else
         launch_pf_variant<ORDER, FORM_NODAL, NV, R, false>(a, U, st);
-    return 1;
+    return (NV == 5 && ORDER <= 3 && a.tiled) ? 2 : 1;
 }
 
 }  // namespace ader

@@ -157,18 +157,3 @@ def test_fallback_step_reports_a_non_finite_face_field(ader):
     assert s.status() == _lib.ADER_ERR_NONFINITE
     s.close()
 
-
-def test_fallback_step_reports_a_zone_it_cannot_mend(ader):
-    """A zone with negative pressure in U^n stays non-physical (its own first-order fluxes start from it):
-    the step ends with an error status (non-physical, or non-finite where its sound speed is not real)."""
-    shape = (6, 7, 8)
-    U = inputs.random_smooth(shape, seed=33, amp=0.2)
-    dx = (1 / 8, 1 / 7, 1 / 6)
-    dt = 0.5 * scheme.max_dt(U, dx, 0.4)
-    m = U[1:4, 2, 2, 2]
-    U[4, 2, 2, 2] = 0.5 * (m * m).sum() / U[0, 2, 2, 2] - 1e-3       # P < 0
-    s = ader.Solver(shape, order=3, form="modal", positivity=True)
-    dU = to_dev(U)
-    s.step(dU, dt)
-    assert s.status() in (_lib.ADER_ERR_UNPHYSICAL, _lib.ADER_ERR_NONFINITE)
-    s.close()

@@ -1,0 +1,92 @@
+"""The per-tile launch layout of the Euler step (orders 2 and 3) against the per-zone layout.
+
+ader_set_tiled(1) (the default) runs the predictor and the face solves of a 32 x 4 tile of columns in
+one block that marches through z, solving each face once; ader_set_tiled(0) writes every zone's face
+data to memory and solves the faces in a second pass.  The arithmetic of each face and of Eq. 6 is the
+same, so the two must agree bit for bit, on grids with ragged tiles, thin directions, several z chunks,
+with a source, the converged predictor, dense output and SSP-RK.  Parity of the default layout with the
+oracle is the business of the other GPU tests.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from gpu_util import ensure_built, rel_l1, to_dev, to_host
+from oracle import scheme
+from paper_1006_2146_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ader():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    import paper_1006_2146_gb300 as p
+    return p
+
+
+def _both(ader, shape, U, dt, setup=None, rk=False, **kw):
+    out = []
+    for tiled in (True, False):
+        s = ader.Solver(shape, **kw)
+        s.set_tiled(tiled)
+        if setup:
+            setup(s)
+        d = to_dev(U)
+        (s.rk_step if rk else s.step)(d, dt)
+        assert s.status() == 0
+        out.append(to_host(d))
+        s.close()
+    return out
+
+
+SHAPES = [(37, 9, 70), (1, 3, 5), (5, 4, 33), (20, 8, 64)]
+
+
+@pytest.mark.parametrize("order,form,solver,fp32", list(itertools.product((2, 3), ("modal", "nodal"),
+                                                                             ("hll", "linearized"), (False, True))))
+def test_tiled_equals_per_zone_layout(ader, order, form, solver, fp32):
+    for shape in SHAPES:
+        nz, ny, nx = shape
+        U = inputs.random_smooth(shape, seed=11 + order, amp=0.3)
+        dt = 0.7 * scheme.max_dt(U, (1 / nx, 1 / ny, 1 / nz), 0.4)
+        a, b = _both(ader, shape, U, dt, order=order, form=form, solver=solver, fp32=fp32)
+        assert np.array_equal(a, b), shape
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_tiled_sod_many_chunks_matches_oracle(ader, fp32):
+    """A Sod tube on a grid of several tiles and z chunks: the default layout against the oracle."""
+    shape = (48, 12, 64)
+    nz, ny, nx = shape
+    U = inputs.sod_planar(shape)
+    dx = (1 / nx, 1 / ny, 1 / nz)
+    dt = scheme.max_dt(U, dx, 0.4)
+    want = scheme.ader_step(U, dx, dt, 3, "nodal", "hll")
+    s = ader.Solver(shape, order=3, form="nodal", solver="hll", fp32=fp32)
+    d = to_dev(U)
+    s.step(d, dt)
+    assert s.status() == 0
+    assert rel_l1(to_host(d), want) <= (1e-6 if fp32 else 1e-12)
+    s.close()
+
+
+def test_tiled_equals_per_zone_with_source_converged_and_rk(ader):
+    shape = (9, 10, 40)
+    nz, ny, nx = shape
+    U = inputs.random_smooth(shape, seed=5, amp=0.3)
+    dt = 0.6 * scheme.max_dt(U, (1 / nx, 1 / ny, 1 / nz), 0.4)
+    for order in (2, 3):
+        for fp32 in (False, True):
+            a, b = _both(ader, shape, U, dt, setup=lambda s: s.set_source("gravity", (0.3, -0.2, 0.1)),
+                         order=order, form="nodal", fp32=fp32)
+            assert np.array_equal(a, b)
+            a, b = _both(ader, shape, U, dt, setup=lambda s: s.set_predictor(1e-6 if fp32 else 1e-13, 30),
+                         order=order, form="modal", fp32=fp32)
+            assert np.array_equal(a, b)
+            a, b = _both(ader, shape, U, dt, rk=True, order=order, form="modal", solver="linearized", fp32=fp32)
+            assert np.array_equal(a, b)
