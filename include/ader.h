@@ -180,6 +180,27 @@ int ader_set_predictor(ader_ctx* ctx, double tol, int max_iter);
  * zones; the fourth-order predictor's cost dwarfs the face data's traffic).
  * ADER_ERR_ARG for a NULL context. */
 int ader_set_tiled(ader_ctx* ctx, int on);
+
+/* Box faces (Euler contexts).  bc[6] = {x-, x+, y-, y+, z-, z+}, each
+ * ADER_BC_PERIODIC (the default), ADER_BC_OUTFLOW or ADER_BC_REFLECTIVE; an
+ * axis is periodic on both faces or on neither.  The paper's tests with walls
+ * and open sides (Sec. VIII) state no boundary treatment; this is the usual
+ * ghost-zone one: G ghost zones (3 at orders 2-3, 4 at order 4, a step's reach)
+ * across every non-periodic face, an outflow ghost copying the nearest interior
+ * zone, a reflecting ghost the mirror-image zone with the normal momentum
+ * negated.  With a non-periodic face, ader_step / ader_step_devdt /
+ * ader_step_host fill a padded state from U (held by the context: 5 x padded
+ * zones FP64, plus the padded grid's scratch), step it and copy its interior
+ * back to U; ader_max_dt and ader_diagnostics read U as before.  The converged
+ * predictor, source terms, FP32 bulk, the positivity fallback and the launch
+ * layout carry over.  ADER_ERR_ARG for an unknown code, an axis periodic on one
+ * face only, a reflecting axis shorter than G zones, an MHD context, or a
+ * context with the learned guess or dense output; ader_rk_step then returns
+ * ADER_ERR_ARG (not built).  ADER_ERR_CUDA if an allocation fails. */
+#define ADER_BC_PERIODIC 0
+#define ADER_BC_OUTFLOW 1
+#define ADER_BC_REFLECTIVE 2
+int ader_set_boundary(ader_ctx* ctx, const int* bc);
 int ader_predictor_stats(ader_ctx* ctx, unsigned long long* out3_host, void* stream);
 
 /* Non-stiff source term S(U) of Eq. 4 (Sec. II; orders 2-4, modal and

@@ -7,14 +7,14 @@ built from csrc/ (C ABI: include/ader.h); this package is its ctypes binding
 plus the seeded input generators (``inputs``).
 """
 from . import inputs  # noqa: F401
-from ._lib import (ADER_CONVERGED_PREDICTOR, ADER_EMF_TRANSONIC, ADER_FP32_BULK, ADER_HLL,  # noqa: F401
+from ._lib import (ADER_BC_OUTFLOW, ADER_BC_PERIODIC, ADER_BC_REFLECTIVE, ADER_CONVERGED_PREDICTOR, ADER_EMF_TRANSONIC, ADER_FP32_BULK, ADER_HLL,  # noqa: F401
                    ADER_LINEARIZED, ADER_MHD, ADER_NODAL, ADER_POSITIVITY_FALLBACK,
                    ADER_SOURCE_GRAVITY, ADER_SOURCE_LINEAR, ADER_SOURCE_NONE,
                    AderError, ader_create, ader_dense_output, ader_destroy, ader_diagnostics, ader_guess_count,
                    ader_guess_eval, ader_guess_samples, ader_last_error, ader_launches_per_step, ader_max_dt,
                    ader_mlp_grad, ader_mlp_shape, ader_mlp_train, ader_predictor_stats, ader_profile,
                    ader_profile_read, ader_profile_reset, ader_rk_step, ader_set_dense_output, ader_set_guess,
-                   ader_set_predictor, ader_set_source, ader_set_tiled, ader_step, ader_step_devdt, ader_step_host,
+                   ader_set_boundary, ader_set_predictor, ader_set_source, ader_set_tiled, ader_step, ader_step_devdt, ader_step_host,
                    ader_sync_status, load)
 
 
@@ -51,6 +51,11 @@ class Solver:
 
     def set_tiled(self, on):
         ader_set_tiled(self.h, on)
+
+    def set_boundary(self, bc):
+        """Box faces (x-, x+, y-, y+, z-, z+): "periodic", "outflow" or "reflective" (or the ADER_BC_* codes)."""
+        names = {"periodic": ADER_BC_PERIODIC, "outflow": ADER_BC_OUTFLOW, "reflective": ADER_BC_REFLECTIVE}
+        ader_set_boundary(self.h, [names.get(b, b) for b in bc])
 
     def set_predictor(self, tol, max_iter=50):
         ader_set_predictor(self.h, tol, max_iter)

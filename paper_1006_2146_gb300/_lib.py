@@ -17,10 +17,11 @@ ADER_POSITIVITY_FALLBACK = 64
 ADER_OK, ADER_ERR_ARG, ADER_ERR_CUDA, ADER_ERR_UNPHYSICAL, ADER_ERR_NONFINITE, ADER_ERR_NOT_CONVERGED = 0, -1, -2, -3, -4, -5
 ADER_ERR_TIMEOUT = -6
 ADER_SOURCE_NONE, ADER_SOURCE_LINEAR, ADER_SOURCE_GRAVITY = 0, 1, 2
+ADER_BC_PERIODIC, ADER_BC_OUTFLOW, ADER_BC_REFLECTIVE = 0, 1, 2
 
 EXPORTS = ("ader_create", "ader_step", "ader_step_devdt", "ader_max_dt", "ader_rk_step", "ader_step_host",
            "ader_diagnostics", "ader_sync_status", "ader_launches_per_step", "ader_profile", "ader_profile_reset",
-           "ader_profile_read", "ader_set_tiled", "ader_set_predictor", "ader_predictor_stats", "ader_set_source", "ader_set_dense_output", "ader_dense_output", "ader_set_guess",
+           "ader_profile_read", "ader_set_tiled", "ader_set_boundary", "ader_set_predictor", "ader_predictor_stats", "ader_set_source", "ader_set_dense_output", "ader_dense_output", "ader_set_guess",
            "ader_mlp_shape", "ader_guess_samples", "ader_guess_count", "ader_guess_eval", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy",
            "ader_max_dt_static", "ader_batch_create", "ader_batch_tune", "ader_batch_step", "ader_batch_advance",
            "ader_batch_status", "ader_batch_tuning", "ader_batch_groups", "ader_batch_last_error",
@@ -65,6 +66,7 @@ def load(path=None):
     lib.ader_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(i32),
                                       ctypes.POINTER(dbl), i32]
     lib.ader_set_tiled.argtypes = [vp, i32]
+    lib.ader_set_boundary.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.ader_set_predictor.argtypes = [vp, dbl, i32]
     lib.ader_predictor_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong), vp]
     lib.ader_set_guess.argtypes = [vp, vp]
@@ -199,6 +201,12 @@ def ader_profile_read(h):
 def ader_set_tiled(h, on):
     """Euler launch layout: 1 = per-tile predictor and face solves (default), 0 = face data through memory."""
     return _check(h, load().ader_set_tiled(h, 1 if on else 0))
+
+
+def ader_set_boundary(h, bc):
+    """Box faces (x-, x+, y-, y+, z-, z+), each ADER_BC_PERIODIC, ADER_BC_OUTFLOW or ADER_BC_REFLECTIVE."""
+    arr = (ctypes.c_int * 6)(*[int(b) for b in bc])
+    return _check(h, load().ader_set_boundary(h, arr))
 
 
 def ader_set_predictor(h, tol, max_iter):

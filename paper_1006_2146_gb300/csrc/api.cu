@@ -37,6 +37,10 @@ struct ader_ctx {
     double tol = 0.0;                         // converged predictor tolerance (0: fixed M-1 iterations)
     int max_iter = 50;
     bool tiled = true;                        // Euler: per-tile predictor and face solves (ader_set_tiled)
+    int bc[6] = {0, 0, 0, 0, 0, 0};           // box faces (ader_set_boundary); all periodic by default
+    int ghosts[3] = {0, 0, 0};                // ghost zones per side of each non-periodic axis
+    ader_ctx* inner = nullptr;                // non-periodic faces: the context of the padded grid
+    double* Upad = nullptr;                   // the padded state (5 x padded zones FP64)
     unsigned long long* stats = nullptr;      // converged predictor statistics (3 words)
     const float* guess = nullptr;             // learned-guess MLP parameters (device), order 3
     float* G = nullptr;                       // per-zone learned guess (5 x NV x N FP32), allocated by ader_set_guess
@@ -256,6 +260,13 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
 
 void ader_destroy(ader_ctx* c) {
     if (!c) return;
+    if (c->inner) {              // it shares the flag and the predictor statistics of this context
+        c->inner->flag = nullptr;
+        c->inner->stats = nullptr;
+        ader_destroy(c->inner);
+        c->inner = nullptr;
+    }
+    if (c->Upad) cudaFree(c->Upad);
     for (auto& p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -328,11 +339,32 @@ static int check_bface(ader_ctx* c, const double* Bface) {
     return ADER_OK;
 }
 
+static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const double* dt_dev, void* stream);
+
+// Non-periodic faces: fill the padded state's ghost zones from U, step it with the padded grid's
+// context, copy its interior back to U.
+static int step_padded(ader_ctx* c, double* U, double dt, const double* dt_dev, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    ader_ctx* in = c->inner;
+    {
+        Trace t(c, "boundary_ghosts", st);
+        launch_fill_ghosts(c->grid, in->grid, c->bc, c->ghosts, U, c->Upad, st);
+    }
+    if (int rc = step_common(in, c->Upad, nullptr, dt, dt_dev, stream)) return fail(c, rc, in->err);
+    {
+        Trace t(c, "boundary_interior", st);
+        launch_copy_interior(c->grid, in->grid, c->ghosts, c->Upad, U, st);
+    }
+    c->launches = in->launches + 2;
+    return cuda_check(c, cudaGetLastError(), "ader_step launch");
+}
+
 static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const double* dt_dev, void* stream) {
     if (!c) return ADER_ERR_ARG;
     if (!U) return fail(c, ADER_ERR_ARG, "U is null");
     if (int rc = check_bface(c, Bface)) return rc;
     if (!dt_dev && !(dt > 0.0)) return fail(c, ADER_ERR_ARG, "dt must be positive");
+    if (c->inner) return step_padded(c, U, dt, dt_dev, stream);
     cudaStream_t st = (cudaStream_t)stream;
     StepArgs a = make_args(c, dt, dt_dev, c->order - 1);
     a.Bface = Bface;
@@ -413,6 +445,7 @@ int ader_rk_step(ader_ctx* c, double* U, double* Bface, double dt, void* stream)
     if (int rc = check_bface(c, Bface)) return rc;
     if (!(dt > 0.0)) return fail(c, ADER_ERR_ARG, "dt must be positive");
     if (c->src_kind != SOURCE_NONE) return fail(c, ADER_ERR_ARG, "SSP-RK with a source term is not built");
+    if (c->inner) return fail(c, ADER_ERR_ARG, "SSP-RK with non-periodic faces is not built");
     cudaStream_t st = (cudaStream_t)stream;
     const bool mhd = c->mhd;
     const int ns = c->order == 2 ? 2 : (c->order == 3 ? 3 : 5);
@@ -493,7 +526,68 @@ int ader_rk_step(ader_ctx* c, double* U, double* Bface, double dt, void* stream)
 int ader_set_tiled(ader_ctx* c, int on) {
     if (!c) return ADER_ERR_ARG;
     c->tiled = on != 0;
+    if (c->inner) c->inner->tiled = c->tiled;
     return ADER_OK;
+}
+
+int ader_set_boundary(ader_ctx* c, const int* bc) {
+    if (!c) return ADER_ERR_ARG;
+    if (!bc) return fail(c, ADER_ERR_ARG, "bc is null");
+    bool any = false;
+    for (int s = 0; s < 6; ++s) {
+        if (bc[s] != ADER_BC_PERIODIC && bc[s] != ADER_BC_OUTFLOW && bc[s] != ADER_BC_REFLECTIVE)
+            return fail(c, ADER_ERR_ARG, "unknown boundary code");
+        any |= bc[s] != ADER_BC_PERIODIC;
+    }
+    const int n[3] = {c->grid.nx, c->grid.ny, c->grid.nz};
+    const int G = c->order == 4 ? 4 : 3;       // a step's reach along an axis
+    int gh[3];
+    for (int d = 0; d < 3; ++d) {
+        if ((bc[2 * d] == ADER_BC_PERIODIC) != (bc[2 * d + 1] == ADER_BC_PERIODIC))
+            return fail(c, ADER_ERR_ARG, "an axis is periodic on both faces or on neither");
+        gh[d] = bc[2 * d] == ADER_BC_PERIODIC ? 0 : G;
+        if ((bc[2 * d] == ADER_BC_REFLECTIVE || bc[2 * d + 1] == ADER_BC_REFLECTIVE) && n[d] < G)
+            return fail(c, ADER_ERR_ARG, "a reflecting face needs at least the ghost width of zones on its axis");
+    }
+    if (any && c->mhd) return fail(c, ADER_ERR_ARG, "non-periodic faces are built for Euler contexts");
+    if (any && (c->guess || c->Dm))
+        return fail(c, ADER_ERR_ARG, "non-periodic faces with the learned guess or dense output are not built");
+    // drop the previous padded context
+    if (c->inner) {
+        c->inner->flag = nullptr;
+        c->inner->stats = nullptr;
+        ader_destroy(c->inner);
+        c->inner = nullptr;
+    }
+    if (c->Upad) {
+        cudaFree(c->Upad);
+        c->Upad = nullptr;
+    }
+    for (int s = 0; s < 6; ++s) c->bc[s] = bc[s];
+    for (int d = 0; d < 3; ++d) c->ghosts[d] = gh[d];
+    if (!any) return ADER_OK;
+    ader_grid gp = c->g;
+    gp.nx += 2 * gh[0];
+    gp.ny += 2 * gh[1];
+    gp.nz += 2 * gh[2];
+    ader_ctx* in = nullptr;
+    if (int rc = ader_create(&gp, c->order, c->gamma, c->solver, c->flags, &in))
+        return fail(c, rc, "context of the padded grid");
+    cudaFree(in->flag);                        // reports through this context's flag and statistics
+    cudaFree(in->stats);
+    in->flag = c->flag;
+    in->stats = c->stats;
+    in->tiled = c->tiled;
+    in->tol = c->tol;
+    in->max_iter = c->max_iter;
+    c->inner = in;
+    if (c->src_kind != SOURCE_NONE) {
+        const double par[3] = {c->src_par[0], c->src_par[1], c->src_par[2]};
+        if (int rc = ader_set_source(in, c->src_kind == SOURCE_LINEAR ? ADER_SOURCE_LINEAR : ADER_SOURCE_GRAVITY, par))
+            return fail(c, rc, in->err);
+    }
+    return cuda_check(c, cudaMalloc((void**)&c->Upad, (size_t)5 * (size_t)in->grid.n * sizeof(double)),
+                      "cudaMalloc padded state");
 }
 
 int ader_set_predictor(ader_ctx* c, double tol, int max_iter) {
@@ -501,6 +595,10 @@ int ader_set_predictor(ader_ctx* c, double tol, int max_iter) {
     if (tol < 0.0 || max_iter < 1 || max_iter > 1000) return fail(c, ADER_ERR_ARG, "tol >= 0, 1 <= max_iter <= 1000");
     c->tol = tol;
     c->max_iter = max_iter;
+    if (c->inner) {
+        c->inner->tol = tol;
+        c->inner->max_iter = max_iter;
+    }
     return ADER_OK;
 }
 
@@ -518,6 +616,7 @@ int ader_set_source(ader_ctx* c, int kind, const double* params) {
     if (!c) return ADER_ERR_ARG;
     if (kind == ADER_SOURCE_NONE) {
         c->src_kind = SOURCE_NONE;
+        if (c->inner) c->inner->src_kind = SOURCE_NONE;
         return ADER_OK;
     }
     if (kind != ADER_SOURCE_LINEAR && kind != ADER_SOURCE_GRAVITY) return fail(c, ADER_ERR_ARG, "unknown source kind");
@@ -534,11 +633,13 @@ int ader_set_source(ader_ctx* c, int kind, const double* params) {
     }
     c->src_kind = kind == ADER_SOURCE_LINEAR ? SOURCE_LINEAR : SOURCE_GRAVITY;
     for (int i = 0; i < 3; ++i) c->src_par[i] = par[i];
+    if (c->inner) return ader_set_source(c->inner, kind, params) ? fail(c, ADER_ERR_CUDA, c->inner->err) : ADER_OK;
     return ADER_OK;
 }
 
 int ader_set_guess(ader_ctx* c, const float* params) {
     if (!c) return ADER_ERR_ARG;
+    if (params && c->inner) return fail(c, ADER_ERR_ARG, "the learned guess with non-periodic faces is not built");
     if (params && c->order != 3) return fail(c, ADER_ERR_ARG, "the learned guess is built for third order");
     if (params && c->grid.n >= (1ll << 31)) return fail(c, ADER_ERR_ARG, "the learned guess takes up to 2^31 - 1 zones");
     if (params && !c->G) {
@@ -643,6 +744,7 @@ static int mode_count(int order) { return order == 2 ? 5 : (order == 3 ? 15 : 35
 
 int ader_set_dense_output(ader_ctx* c, int enable) {
     if (!c) return ADER_ERR_ARG;
+    if (enable && c->inner) return fail(c, ADER_ERR_ARG, "dense output with non-periodic faces is not built");
     if (c->Dm) {
         if (int rc = cuda_check(c, cudaFree(c->Dm), "cudaFree dense modes")) return rc;
         c->Dm = nullptr;

@@ -95,6 +95,38 @@ template <> ADER_DEV double rcp<double>(double x) {
 #endif
 }
 
+// ------------------------------------------------------------------ FP32 <-> FP64 without the FP64 units
+// GB300 runs FP64 at 1/64 of the FP32 rate and its conversion instructions on the same scarce units, so
+// the FP32-bulk kernels move values between the two formats with integer operations on the bit
+// patterns (IEEE 754 binary32 and binary64: sign, biased exponent, significand).
+
+// x rounded to the nearest FP32 value (ties to even), as a conversion would round it, except that
+// results below FP32's normal range are flushed to a signed zero (the FP32 kernels flush such values
+// anyway).  Overflow gives a signed infinity, NaN a quiet NaN.
+__device__ __forceinline__ float f32_of_f64(double x) {
+    const long long b = __double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const unsigned ef = (hi >> 20) & 0x7ffu;
+    const int e = (int)ef - 896;                          // exponent rebased from FP64's bias to FP32's
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;               // the 29 significand bits dropped
+    unsigned bits = sign | ((unsigned)(e > 0 ? e : 0) << 23) | m;
+    bits += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;   // may carry into inf
+    const bool nan = ef == 0x7ffu && ((hi & 0xfffffu) | lo) != 0u;
+    bits = e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : bits);
+    return __uint_as_float(nan ? 0x7fc00000u : bits);
+}
+
+// the FP64 value of an FP32 number, exactly (FP32 subnormals, flushed by the FP32 kernels, give zero)
+__device__ __forceinline__ double f64_of_f32(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned ed = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
+    const unsigned mant = e == 0u ? 0u : (b & 0x7fffffu);
+    return __hiloint2double((int)((b & 0x80000000u) | (ed << 20) | (mant >> 3)), (int)(mant << 29));
+}
+
 // ------------------------------------------------------------------ physics, Eq. 3 (Gaussian units)
 // NV = 5: Euler (rho, rho v, eps).  NV = 8: ideal MHD (rho, rho v, eps, B) with
 // eps = rho v^2/2 + P/(gamma-1) + B^2/(8 pi).

@@ -111,6 +111,10 @@ template <class R> int launch_emf_ct(const StepArgs& a, double* Bf, double c_hos
 int launch_guess_samples(const StepArgs& a, const double* U, float* X, float* Y, int* ok, cudaStream_t st);
 // learned guess of every zone into a.G (order 3; after launch_recon)
 template <class R> int launch_guess(const StepArgs& a, const double* U, cudaStream_t st, float* Gzero);
+// non-periodic box faces (boundary.cu): the padded state gp with ghost zones per the face rules, and back
+int launch_fill_ghosts(const Grid& g, const Grid& gp, const int bc[6], const int gh[3], const double* U, double* Up,
+                       cudaStream_t st);
+int launch_copy_interior(const Grid& g, const Grid& gp, const int gh[3], const double* Up, double* U, cudaStream_t st);
 int launch_totals(const Grid& g, const double* U, const double* Bf, const double dx[3], double* totals_dev,
                   double* partial, int nblocks, cudaStream_t st);
 

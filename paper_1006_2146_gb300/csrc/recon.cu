@@ -42,18 +42,23 @@ __global__ void __launch_bounds__(128) k_weno1d(Grid g, const T* __restrict__ U,
 }
 
 // FP32 copy of the state: every value is rounded once per step here instead of
-// at each of the 13 stencil points that read it (on GB300 the conversion runs
-// on the scarce FP64 units).  Pairs of values per thread; an odd last value is
-// taken by the first thread.
+// at each of the 13 stencil points that read it, with integer operations
+// (f32_of_f64; GB300 runs its conversion instruction on the scarce FP64 units).
+// Pairs of values per thread, two pairs per pass; an odd last value is taken by
+// the first thread.
 __global__ void __launch_bounds__(256) k_to_f32(float* __restrict__ out, const double* __restrict__ U, long long count) {
     const long long n2 = count / 2;
     const double2* in = reinterpret_cast<const double2*>(U);
     float2* o = reinterpret_cast<float2*>(out);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += 2 * stride) {
         const double2 v = in[i];
-        o[i] = make_float2((float)v.x, (float)v.y);
+        const bool two = i + stride < n2;
+        const double2 w = two ? in[i + stride] : v;
+        o[i] = make_float2(f32_of_f64(v.x), f32_of_f64(v.y));
+        if (two) o[i + stride] = make_float2(f32_of_f64(w.x), f32_of_f64(w.y));
     }
-    if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[count - 1] = (float)U[count - 1];
+    if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[count - 1] = f32_of_f64(U[count - 1]);
 }
 
 int launch_to_f32(float* out, const double* U, long long count, cudaStream_t st) {

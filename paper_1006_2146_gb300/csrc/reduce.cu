@@ -15,20 +15,13 @@ namespace ader {
 // S is the precision of the per-zone signal speed: FP64, or FP32 for FP32-bulk
 // contexts (there FP64's division and square root would dominate the kernel);
 // the maximum, its reduction and dt are FP64 in both.
-// The state in the precision S of the signal speeds.  FP32: the FP64 significand is truncated to FP32's
-// (at most one unit in FP32's last place off) with integer operations, because GB300's conversion
-// instruction runs on the scarce FP64 units; values outside FP32's normal range take the conversion.
+// The state in the precision S of the signal speeds; FP32 rounds with integer operations (f32_of_f64).
 template <class S>
 __device__ __forceinline__ S speed_operand(double x) {
-    if constexpr (sizeof(S) == 4) {
-        const long long b = __double_as_longlong(x);
-        const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-        const int e = (int)((hi >> 20) & 0x7ffu) - 896;          // FP64 exponent rebased to FP32's bias
-        if (e <= 0 || e >= 255) return (float)x;
-        return __int_as_float((int)((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)));
-    } else {
+    if constexpr (sizeof(S) == 4)
+        return f32_of_f64(x);
+    else
         return x;
-    }
 }
 
 template <class S>
@@ -39,10 +32,22 @@ __global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict
     bool bad = false;
     const long long N = g.n;
     const S gm = S(gamma), ix = S(idx), iy = S(idy), iz = S(idz);
-#pragma unroll 2
-    for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < N; z += (long long)gridDim.x * blockDim.x) {
-        const S rho = speed_operand<S>(U[z]), mx = speed_operand<S>(U[N + z]), my = speed_operand<S>(U[2 * N + z]),
-                mz = speed_operand<S>(U[3 * N + z]), E = speed_operand<S>(U[4 * N + z]);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // four zones per pass, their twenty loads issued before any arithmetic (more bytes in flight)
+    for (long long z0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; z0 < N; z0 += 4 * stride) {
+    double ld[4][5];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const long long zz = z0 + u * stride;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) ld[u][c] = zz < N ? U[c * N + zz] : 1.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const long long z = z0 + u * stride;
+        if (z >= N) break;
+        const S rho = speed_operand<S>(ld[u][0]), mx = speed_operand<S>(ld[u][1]), my = speed_operand<S>(ld[u][2]),
+                mz = speed_operand<S>(ld[u][3]), E = speed_operand<S>(ld[u][4]);
         const S ir = S(1) / rho;
         const S vx = mx * ir, vy = my * ir, vz = mz * ir;
         S v;
@@ -71,6 +76,7 @@ __global__ void __launch_bounds__(256) k_max_dt(Grid g, const double* __restrict
             v = (fabs(vx) + a) * ix + (fabs(vy) + a) * iy + (fabs(vz) + a) * iz;
         }
         sm = fmax(sm, v);
+    }
     }
     double s = (double)sm;
     if (bad) raise_flag(flag, FLAG_UNPHYSICAL);
@@ -103,7 +109,7 @@ int launch_max_dt(const Grid& g, const double* U, const double* Bf, double gamma
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long want = (g.n + 255) / 256;
+    long long want = (g.n + 1023) / 1024;                 // four zones per thread and pass
     const long long cap = (long long)sms * 8;
     const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
     if (fp32)

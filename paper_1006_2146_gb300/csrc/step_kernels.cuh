@@ -317,6 +317,30 @@ ADER_DEV bool finite_bits(double x) {
 #endif
 }
 
+// out = base + hi + lo (+ dt S-bar), FP64.  An addition that cannot change its FP64 sum is skipped when
+// no lane of the warp needs it, so the result equals the plain sum bit for bit: hi = 0 (a zone whose
+// faces all carry the same flux), and lo below half a unit in the last place of base + hi (checked on
+// the exponents: |lo| < 2^(e_lo - 126) <= 2^(e_t - 1077) = ulp(t) / 2 when e_lo + 951 <= e_t).
+__device__ __forceinline__ void store_pair_update(const StepArgs& a, double* out, const double* base, const float* hi,
+                                                  const float* lo, long long z) {
+    const long long N = a.grid.n;
+    const float* Sb = (const float*)a.Sb;
+    const unsigned lanes = __activemask();         // the lanes of this zone's warp still running
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        double val = base ? base[v * N + z] : 0.0;
+        if (__any_sync(lanes, hi[v] != 0.0f)) val += f64_of_f32(hi[v]);
+        const unsigned e_lo = (__float_as_uint(lo[v]) >> 23) & 0xffu;
+        const unsigned e_t = ((unsigned)__double2hiint(val) >> 20) & 0x7ffu;
+        if (__any_sync(lanes, lo[v] != 0.0f && e_lo + 951u > e_t)) val += f64_of_f32(lo[v]);
+        if (Sb) val += f64_of_f32(Sb[v * N + z]);
+        bad |= !finite_bits(val);
+        out[v * N + z] = val;
+    }
+    if (bad && !a.defer_nonfinite) raise_flag(a.flag, FLAG_NONFINITE);
+}
+
 template <int SOLVER, int D, int NV>
 ADER_DEV void flux_difference_pair(const StepArgs& a, long long z, int i, int j, int k, float gamma, float gm1,
                                    float chi, float clo, float* hi, float* lo) {
@@ -359,17 +383,7 @@ __global__ void __launch_bounds__(128) k_flux_update_pair(StepArgs a, double* ou
     flux_difference_pair<SOLVER, 0, NV>(a, z, i, j, k, gamma, gm1, c_hi[0], c_lo[0], hi, lo);
     flux_difference_pair<SOLVER, 1, NV>(a, z, i, j, k, gamma, gm1, c_hi[1], c_lo[1], hi, lo);
     flux_difference_pair<SOLVER, 2, NV>(a, z, i, j, k, gamma, gm1, c_hi[2], c_lo[2], hi, lo);
-    const long long N = a.grid.n;
-    const float* Sb = (const float*)a.Sb;
-    bool bad = false;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        double val = (base ? base[v * N + z] : 0.0) + ((double)hi[v] + (double)lo[v]);
-        if (Sb) val += (double)Sb[v * N + z];
-        bad |= !finite_bits(val);
-        out[v * N + z] = val;
-    }
-    if (bad && !a.defer_nonfinite) raise_flag(a.flag, FLAG_NONFINITE);
+    store_pair_update(a, out, base, hi, lo, z);
 }
 
 template <int SOLVER, int NV, class R>
@@ -432,7 +446,13 @@ __global__ void __launch_bounds__(128) k_flux_update_stored(StepArgs a, double* 
 // before any flux lands on its slots).  Only the sides of the tile's and chunk's boundary zones go to
 // S3, and k_tile_faces solves those faces afterwards.  The face data of the interior never reaches HBM,
 // and no zone is predicted twice.
-constexpr int PT_X = 32, PT_Y = 4, PT_THREADS = PT_X * PT_Y;
+#ifndef ADER_PT_X
+#define ADER_PT_X 32
+#endif
+#ifndef ADER_PT_Y
+#define ADER_PT_Y 4
+#endif
+constexpr int PT_X = ADER_PT_X, PT_Y = ADER_PT_Y, PT_THREADS = PT_X * PT_Y;
 constexpr int PT_NQ = 15;                     // values per Euler face side
 constexpr int PT_SLOTS = 7;                   // x+, x-, y+, y-, z+ (even planes), z-, z+ (odd planes)
 
@@ -494,14 +514,49 @@ ADER_DEV FaceSide<5, R> pt_load(const R* sh, int slot, int tid) {
     return f;
 }
 
-// a side of a boundary zone to S3 (layout of the file header), for k_tile_faces
+// Boundary sides for k_tile_faces, packed in S3 (unused otherwise on this path) so that both their
+// writes and k_tile_faces's reads are coalesced.  Three arrays, each [s][q][...] with s = 0 for the
+// lower side of a boundary face (the x+, y+ or z+ side of the zone below it) and s = 1 for its upper
+// side, q the 15 values of a side:
+//   x: [2][15][tiles_x][nz][ny]   the tile's last column (s = 0) and first column (s = 1), j fastest
+//   y: [2][15][tiles_y][nz][nx]   the tile's last row and first row, i fastest
+//   z: [2][15][chunks][ny][nx]    the chunk's last plane and first plane, i fastest
+// Each array has at most 30 N values (tiles_x <= nx, and so on), so the three fit in S3's 90 N.
+struct PtBoundary {
+    long long sx, sy, sz;          // values per (s, q) slice of each array
+    long long ox, oy, oz;          // offsets of the arrays in S3
+};
+
+ADER_DEV PtBoundary pt_boundary(const Grid& g, int cz) {
+    const long long ntx = (g.nx + PT_X - 1) / PT_X, nty = (g.ny + PT_Y - 1) / PT_Y, ncz = (g.nz + cz - 1) / cz;
+    PtBoundary b;
+    b.sx = ntx * g.nz * g.ny;
+    b.sy = nty * g.nz * g.nx;
+    b.sz = ncz * g.ny * g.nx;
+    b.ox = 0;
+    b.oy = 2 * PT_NQ * b.sx;
+    b.oz = b.oy + 2 * PT_NQ * b.sy;
+    return b;
+}
+
+// one side from shared memory into a packed boundary array: slice stride `slice`, position `pos`
 template <class R>
-ADER_DEV void pt_to_s3(const StepArgs& a, const R* sh, int slot, int tid, int side, long long z) {
-    R* S3 = (R*)a.S3;
-    const long long N = a.grid.n;
+ADER_DEV void pt_to_boundary(R* base, long long slice, long long pos, const R* sh, int slot, int tid) {
     const R* s = sh + slot * PT_NQ * PT_THREADS + tid;
 #pragma unroll
-    for (int q = 0; q < PT_NQ; ++q) S3[(side * PT_NQ + q) * N + z] = s[q * PT_THREADS];
+    for (int q = 0; q < PT_NQ; ++q) base[q * slice + pos] = s[q * PT_THREADS];
+}
+
+template <class R>
+ADER_DEV FaceSide<5, R> pt_from_boundary(const R* base, long long slice, long long pos) {
+    FaceSide<5, R> f;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        f.ub[v] = base[v * slice + pos];
+        f.avg[v] = base[(5 + v) * slice + pos];
+        f.F[v] = base[(10 + v) * slice + pos];
+    }
+    return f;
 }
 
 template <int D, class R>
@@ -526,6 +581,12 @@ __global__ void __launch_bounds__(PT_THREADS, sizeof(R) == 4 ? 3 : 1)
     const bool last_x = tx == PT_X - 1 || i == g.nx - 1, last_y = ty == PT_Y - 1 || j == g.ny - 1;
     const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
     const long long nxy = (long long)g.nx * g.ny;
+    const PtBoundary bd = pt_boundary(g, cz);
+    R* S3 = (R*)a.S3;
+    R* bx = S3 + bd.ox;
+    R* by = S3 + bd.oy;
+    R* bz = S3 + bd.oz;
+    const long long tile_x = blockIdx.x % tiles_x, tile_y = blockIdx.x / tiles_x, chunk = blockIdx.y;
     for (int k = k0; k < k1; ++k) {
         const long long z = (long long)k * nxy + (long long)j * g.nx + i;
         const int zp_slot = (k & 1) ? 6 : 4;          // this plane's z+ sides; the previous plane's in the other
@@ -538,69 +599,81 @@ __global__ void __launch_bounds__(PT_THREADS, sizeof(R) == 4 ? 3 : 1)
         }
         __syncthreads();
         if (valid) {
+            const long long px = (tile_x * g.nz + k) * g.ny + j, py = (tile_y * g.nz + k) * g.nx + i,
+                            pz = (chunk * g.ny + j) * g.nx + i;
             if (tx > 0)                                // face i - 1/2: x+ side of the zone on the left
                 pt_store_flux<0>(a, z - 1, riemann<SOLVER, 0>(pt_load(sh, 0, tid - 1), pt_load(sh, 1, tid), gamma, gm1));
             else
-                pt_to_s3(a, sh, 1, tid, 1, z);
-            if (last_x) pt_to_s3(a, sh, 0, tid, 0, z);
+                pt_to_boundary(bx + PT_NQ * bd.sx, bd.sx, px, sh, 1, tid);
+            if (last_x) pt_to_boundary(bx, bd.sx, px, sh, 0, tid);
             if (ty > 0)
                 pt_store_flux<1>(a, z - g.nx,
                                  riemann<SOLVER, 1>(pt_load(sh, 2, tid - PT_X), pt_load(sh, 3, tid), gamma, gm1));
             else
-                pt_to_s3(a, sh, 3, tid, 3, z);
-            if (last_y) pt_to_s3(a, sh, 2, tid, 2, z);
+                pt_to_boundary(by + PT_NQ * bd.sy, bd.sy, py, sh, 3, tid);
+            if (last_y) pt_to_boundary(by, bd.sy, py, sh, 2, tid);
             if (k > k0)
                 pt_store_flux<2>(a, z - nxy,
                                  riemann<SOLVER, 2>(pt_load(sh, 10 - zp_slot, tid), pt_load(sh, 5, tid), gamma, gm1));
             else
-                pt_to_s3(a, sh, 5, tid, 5, z);
-            if (k == k1 - 1) pt_to_s3(a, sh, zp_slot, tid, 4, z);
+                pt_to_boundary(bz + PT_NQ * bd.sz, bd.sz, pz, sh, 5, tid);
+            if (k == k1 - 1) pt_to_boundary(bz, bd.sz, pz, sh, zp_slot, tid);
         }
         __syncthreads();
     }
 }
 
-// The faces on tile and chunk boundaries, from the sides k_pf_tile left in S3: the tile boundaries in x
-// (i = multiples of PT_X, and i = 0 against nx - 1), in y (multiples of PT_Y) and the chunk boundaries in
-// z (multiples of cz).  One thread per face.
+// The faces on tile and chunk boundaries, from the sides k_pf_tile packed in S3: the tile boundaries in
+// x (i = multiples of PT_X, and i = 0 against nx - 1), in y (multiples of PT_Y) and the chunk boundaries
+// in z (multiples of cz).  One thread per face, the packed arrays' fastest index fastest across threads.
 template <int SOLVER, class R>
 __global__ void __launch_bounds__(128) k_tile_faces(StepArgs a, int cz, long long nfx, long long nfy, long long nfz) {
     const Grid& g = a.grid;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
     const long long nxy = (long long)g.nx * g.ny;
-    if (t < nfx) {                      // x: (tile, j, k)
+    const PtBoundary bd = pt_boundary(g, cz);
+    const R* S3 = (const R*)a.S3;
+    if (t < nfx) {                      // x: t = (tile * nz + k) * ny + j; lower zone in the previous tile
+        const int j = (int)(t % g.ny);
+        const long long r = t / g.ny;
+        const int k = (int)(r % g.nz), tile = (int)(r / g.nz);
         const int ntx = (g.nx + PT_X - 1) / PT_X;
-        const int tile = (int)(t % ntx);
-        const long long r = t / ntx;
-        const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-        const int i = tile * PT_X, il = i == 0 ? g.nx - 1 : i - 1;
-        const long long row = (long long)k * nxy + (long long)j * g.nx;
-        pt_store_flux<0>(a, row + il,
-                         riemann<SOLVER, 0>(load_side<5, R>(a, 0, row + il), load_side<5, R>(a, 1, row + i), gamma, gm1));
+        const int tl = tile == 0 ? ntx - 1 : tile - 1;
+        const int il = tile == 0 ? g.nx - 1 : tile * PT_X - 1;
+        const long long pl = ((long long)tl * g.nz + k) * g.ny + j;
+        const R* bx = S3 + bd.ox;
+        pt_store_flux<0>(a, (long long)k * nxy + (long long)j * g.nx + il,
+                         riemann<SOLVER, 0>(pt_from_boundary(bx, bd.sx, pl),
+                                            pt_from_boundary(bx + PT_NQ * bd.sx, bd.sx, t), gamma, gm1));
         return;
     }
     t -= nfx;
-    if (t < nfy) {                      // y: (i, tile, k)
-        const int nty = (g.ny + PT_Y - 1) / PT_Y;
+    if (t < nfy) {                      // y: t = (tile * nz + k) * nx + i
         const int i = (int)(t % g.nx);
         const long long r = t / g.nx;
-        const int tile = (int)(r % nty), k = (int)(r / nty);
-        const int j = tile * PT_Y, jl = j == 0 ? g.ny - 1 : j - 1;
-        const long long pl = (long long)k * nxy + i;
-        pt_store_flux<1>(a, pl + (long long)jl * g.nx,
-                         riemann<SOLVER, 1>(load_side<5, R>(a, 2, pl + (long long)jl * g.nx),
-                                            load_side<5, R>(a, 3, pl + (long long)j * g.nx), gamma, gm1));
+        const int k = (int)(r % g.nz), tile = (int)(r / g.nz);
+        const int nty = (g.ny + PT_Y - 1) / PT_Y;
+        const int tl = tile == 0 ? nty - 1 : tile - 1;
+        const int jl = tile == 0 ? g.ny - 1 : tile * PT_Y - 1;
+        const long long pl = ((long long)tl * g.nz + k) * g.nx + i;
+        const R* by = S3 + bd.oy;
+        pt_store_flux<1>(a, (long long)k * nxy + (long long)jl * g.nx + i,
+                         riemann<SOLVER, 1>(pt_from_boundary(by, bd.sy, pl),
+                                            pt_from_boundary(by + PT_NQ * bd.sy, bd.sy, t), gamma, gm1));
         return;
     }
     t -= nfy;
-    if (t < nfz) {                      // z: (i, j, chunk)
+    if (t < nfz) {                      // z: t = chunk * nxy + column
         const long long col = t % nxy;
         const int chunk = (int)(t / nxy);
-        const int k = chunk * cz, kl = k == 0 ? g.nz - 1 : k - 1;
+        const int ncz = (g.nz + cz - 1) / cz;
+        const int cl = chunk == 0 ? ncz - 1 : chunk - 1;
+        const int kl = chunk == 0 ? g.nz - 1 : chunk * cz - 1;
+        const R* bz = S3 + bd.oz;
         pt_store_flux<2>(a, (long long)kl * nxy + col,
-                         riemann<SOLVER, 2>(load_side<5, R>(a, 4, (long long)kl * nxy + col),
-                                            load_side<5, R>(a, 5, (long long)k * nxy + col), gamma, gm1));
+                         riemann<SOLVER, 2>(pt_from_boundary(bz, bd.sz, (long long)cl * nxy + col),
+                                            pt_from_boundary(bz + PT_NQ * bd.sz, bd.sz, t), gamma, gm1));
     }
 }
 
@@ -679,16 +752,7 @@ __global__ void __launch_bounds__(128) k_flux_update_stored_pair(StepArgs a, dou
             lo[v] += he + t;
         }
     }
-    const float* Sb = (const float*)a.Sb;
-    bool bad = false;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        double val = (base ? base[v * N + z] : 0.0) + ((double)hi[v] + (double)lo[v]);
-        if (Sb) val += (double)Sb[v * N + z];
-        bad |= !finite_bits(val);
-        out[v * N + z] = val;
-    }
-    if (bad && !a.defer_nonfinite) raise_flag(a.flag, FLAG_NONFINITE);
+    store_pair_update(a, out, base, hi, lo, z);
 }
 
 // ------------------------------------------------------------------ MHD: edge EMFs (Sec. II.3, Eq. 7)
