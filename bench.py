@@ -337,6 +337,11 @@ def mhd_learned_evaluation(ader, torch, stream, n=128, steps=3, train_n=96):
             out[name] = rec
     except Exception as exc:
         out["error"] = str(exc)[:200]
+    try:
+        out["accuracy_bound"] = guess_accuracy_bound(ader, torch, P, U0, B0, form="modal", solver="linearized",
+                                                     gamma=5.0 / 3.0, stream=stream)
+    except Exception as exc:
+        out["accuracy_bound"] = {"error": str(exc)[:200]}
     return out
 
 
@@ -601,6 +606,77 @@ def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32,
     return out
 
 
+def guess_accuracy_bound(ader, torch, P, U0, B0=None, form="modal", solver="hll", gamma=1.4, stream=None):
+    """What a guess must reach to save an iteration, measured on one step of a state (FP64, third order).
+
+    The predictor's polynomial at the end of the step minus at its start (dense output at tau = 1 and 0) is
+    its evolutionary part: u11 + u12, u13, u14, u15 per variable.  Its relative L2 error against the
+    converged predictor (tol 1e-13) is taken for the learned guess (ader_guess_eval) and for k = 1, 2, 3
+    Picard iterations from zero (the converged mode capped at k).  Starting from the guess saves the first
+    k iterations only where the guess is at least as accurate as k iterations from zero: e_guess < e_1 is
+    the bound the network must meet to pay at all."""
+    from paper_1006_2146_gb300 import _lib
+    mhd = B0 is not None
+    nz, ny, nx = U0.shape[1:]
+    nv = 8 if mhd else 5
+    zones = nx * ny * nz
+    flags = (_lib.ADER_MHD if mhd else 0) | (_lib.ADER_NODAL if form == "nodal" else 0)
+    sol = _lib.ADER_HLL if solver == "hll" else _lib.ADER_LINEARIZED
+
+    def make():
+        return _lib.ader_create(nx, ny, nz, 1.0 / nx, 1.0 / ny, 1.0 / nz, 3, gamma, sol, flags)
+
+    h = make()
+    dtv = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _lib.ader_max_dt(h, U0, B0, 0.4, dtv, stream)
+    torch.cuda.synchronize()
+    dt = float(dtv.item())
+    _lib.ader_destroy(h)
+
+    def increment(max_iter):
+        h = make()
+        try:
+            _lib.ader_set_predictor(h, 1e-13, max_iter)
+            _lib.ader_set_dense_output(h, True)
+            d = U0.clone()
+            b = B0.clone() if mhd else None
+            torch.cuda.synchronize()
+            _lib.ader_step(h, d, b, dt, stream)
+            w0 = torch.empty((10, nv, zones), dtype=torch.float64, device="cuda")
+            w1 = torch.empty_like(w0)
+            _lib.ader_dense_output(h, 0.0, w0, stream)
+            _lib.ader_dense_output(h, 1.0, w1, stream)
+            torch.cuda.synchronize()
+            _lib.ader_sync_status(h, stream)            # a capped run reports ADER_ERR_NOT_CONVERGED: expected
+        finally:
+            _lib.ader_destroy(h)
+        return (w1 - w0)[:4]                            # modes 1-4 carry the evolutionary part at tau = 1
+
+    ref = increment(50)
+    h = make()
+    try:
+        _lib.ader_set_guess(h, P)
+        G = torch.zeros((25 if not mhd else 40, zones), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        _lib.ader_guess_eval(h, U0, B0, dt, G, stream)
+        torch.cuda.synchronize()
+        st = _lib.ader_sync_status(h, stream)
+    finally:
+        _lib.ader_destroy(h)
+    Gd = G.double().reshape(5, nv, zones)               # u11..u15 of each variable
+    guess = torch.stack([Gd[0] + Gd[1], Gd[2], Gd[3], Gd[4]])
+    norm = float(ref.norm())
+
+    def err(x):
+        return float((x - ref).norm()) / norm if norm > 0 else 0.0
+
+    out = {"e_guess": err(guess), "guess_status": st, "dt": dt}
+    for k in (1, 2, 3):
+        out["e_%d_iterations_from_zero" % k] = err(increment(k))
+    out["guess_saves_an_iteration"] = out["e_guess"] < out["e_1_iterations_from_zero"]
+    return out
+
+
 def blast_evaluation(ader, torch, P, stream, n=256, steps=3):
     """The learned guess on the 256^3 hydrodynamic blast (Sec. VIII.3 set-up: rho = 1, P 1000 inside r < 0.1,
     0.1 outside): FP32 converged predictor (tol 1e-6) from zero and from the guess, timed, with the mean
@@ -708,6 +784,17 @@ def learned_variants(ader, torch, n, U0, stream, steps=3):
         ref = None
         out["fp64_converged_reference"] = {"error": str(exc)[:200]}
     out["learned_guess_on_blast_256"] = blast_evaluation(ader, torch, P, stream)
+    try:
+        from paper_1006_2146_gb300 import inputs
+        Ub = torch.from_numpy(inputs.blast(128, sub=2)).to("cuda")
+        out["learned_guess_accuracy_bound_blast_128"] = guess_accuracy_bound(ader, torch, P, Ub, form="nodal",
+                                                                             stream=stream)
+        Ur = torch.from_numpy(inputs.random_smooth((64, 64, 64), seed=1006, amp=0.3)).to("cuda")
+        out["learned_guess_accuracy_bound_random_64"] = guess_accuracy_bound(ader, torch, P, Ur, form="nodal",
+                                                                             stream=stream)
+        del Ub, Ur
+    except Exception as exc:
+        out["learned_guess_accuracy_bound_blast_128"] = {"error": str(exc)[:200]}
     for name, fp32, tol, guess in cases:
         try:
             vsecs, vprof, vs_, _, _ = run_config(ader, torch, n, 3, "nodal", "hll", fp32, 3, 1, stream, profile=True,

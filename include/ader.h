@@ -259,6 +259,15 @@ int ader_set_guess(ader_ctx* ctx, const float* params);
  * layers on the tensor cores (tcgen05, FP16 operands, FP32 accumulation).
  * Needs ader_set_guess first.  Asynchronous on the stream. */
 int ader_guess_eval(ader_ctx* ctx, const double* U, const double* Bface, double dt, float* G, void* stream);
+/* Test of the tensor-core kernel's bounded waits (failure detection; no
+ * counterpart in the paper).  Arms the context's next learned-guess launch
+ * (ader_guess_eval, or a step with a guess): that launch issues no MMA for its
+ * first layer, so that nothing ever completes the barrier it waits on; after
+ * 1024 tries the wait gives up, the kernel raises ADER_ERR_TIMEOUT (read by
+ * ader_sync_status), frees its tensor memory and returns, leaving its guess
+ * output unwritten.  The arming holds for one launch.  ADER_ERR_ARG for a NULL
+ * context or one without guess parameters. */
+int ader_test_bounded_wait(ader_ctx* ctx);
 /* The number of zones the network ran on in the context's last guess launch
  * (the zones with slopes), to *out_host; synchronises the stream.  0 before
  * the first launch or without a guess. */

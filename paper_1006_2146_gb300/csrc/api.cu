@@ -37,6 +37,7 @@ struct ader_ctx {
     double tol = 0.0;                         // converged predictor tolerance (0: fixed M-1 iterations)
     int max_iter = 50;
     bool tiled = true;                        // Euler: per-tile predictor and face solves (ader_set_tiled)
+    bool wait_test = false;                   // the next learned-guess launch tests its bounded waits
     int bc[6] = {0, 0, 0, 0, 0, 0};           // box faces (ader_set_boundary); all periodic by default
     int ghosts[3] = {0, 0, 0};                // ghost zones per side of each non-periodic axis
     ader_ctx* inner = nullptr;                // non-periodic faces: the context of the padded grid
@@ -148,6 +149,7 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.emf_transonic = (c->flags & ADER_EMF_TRANSONIC) ? 1 : 0;
     a.defer_nonfinite = 0;
     a.tiled = (!c->mhd && c->tiled) ? 1 : 0;
+    a.wait_test = c->wait_test ? 1 : 0;
     return a;
 }
 
@@ -160,6 +162,7 @@ static int enqueue_faces(ader_ctx* c, const StepArgs& a, const double* U, cudaSt
     }
     if (a.G) {
         Trace t(c, "learned_guess", st);
+        c->wait_test = false;                 // one launch only
         const int k = launch_guess<R>(a, U, st, nullptr);
         if (k < 0)
             c->setup_failed = true;       // reported by the caller
@@ -656,6 +659,13 @@ int ader_set_guess(ader_ctx* c, const float* params) {
     return ADER_OK;
 }
 
+int ader_test_bounded_wait(ader_ctx* c) {
+    if (!c) return ADER_ERR_ARG;
+    if (!c->guess) return fail(c, ADER_ERR_ARG, "no guess parameters set (ader_set_guess)");
+    c->wait_test = true;
+    return ADER_OK;
+}
+
 int ader_guess_eval(ader_ctx* c, const double* U, const double* Bface, double dt, float* G, void* stream) {
     if (!c) return ADER_ERR_ARG;
     if (!U || !G || !(dt > 0.0)) return fail(c, ADER_ERR_ARG, "null pointer or dt <= 0");
@@ -666,6 +676,7 @@ int ader_guess_eval(ader_ctx* c, const double* U, const double* Bface, double dt
     a.Bface = Bface;
     a.guess = c->guess;
     a.G = G;
+    c->wait_test = false;                     // one launch only
     if (c->fp32) {
         launch_recon<float>(a, U, st);
         if (launch_guess<float>(a, U, st, G) < 0) return fail(c, ADER_ERR_CUDA, "guess kernel set-up");

@@ -19,7 +19,11 @@
 //
 // Every wait on the MMA barrier is bounded: on time-out the CTA raises
 // FLAG_TIMEOUT, waits once more (bounded) for its MMAs, frees its TMEM and
-// returns.
+// returns.  A launch armed by ader_test_bounded_wait (a.wait_test) issues no
+// MMA and commits nothing for its first layer, so that nothing ever arrives
+// on the barrier; its waits then run out after WAIT_TEST_LIMIT tries (with no
+// MMA in flight, the clean-up wait has nothing to wait for either) and the
+// time-out path above runs for real.
 #include <cuda_fp16.h>
 
 #include "kernels.cuh"
@@ -33,6 +37,7 @@ constexpr int TM = 128;                  // zones per tile = MMA M = TMEM lanes 
 constexpr int GROUPS = 4;                // pipelines per CTA (512 threads)
 constexpr unsigned TMEM_COLS = 128;      // accumulator columns per group: the widest layer
 constexpr long long WAIT_LIMIT = 1ll << 22;
+constexpr long long WAIT_TEST_LIMIT = 1024;
 
 __host__ __device__ constexpr int k1pad(int nv) { return (mlp_in(nv) + 15) / 16 * 16; }
 __host__ __device__ constexpr int n3pad(int nv) { return (mlp_out(nv) + 15) / 16 * 16; }
@@ -89,8 +94,8 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* bar, uint32_t parit
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
-    for (long long i = 0; i < WAIT_LIMIT; ++i)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, long long limit) {
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try(bar, parity)) return true;
     return false;
 }
@@ -227,8 +232,10 @@ __global__ void __launch_bounds__(TM * GROUPS, 1) k_guess_tc(StepArgs a, const d
     const long long ntiles = (cnt + TM - 1) / TM;
     uint32_t parity = 0;
     bool timed_out = false;
+    const bool test = a.wait_test != 0;
+    const long long limit = test ? WAIT_TEST_LIMIT : WAIT_LIMIT;
     auto sync_mma = [&]() -> bool {          // the group waits for its committed layer
-        const bool ok = mbar_wait(bar, parity);
+        const bool ok = mbar_wait(bar, parity, limit);
         parity ^= 1u;
         fence_after();
         return !group_sync_or(bid, !ok);
@@ -265,9 +272,9 @@ __global__ void __launch_bounds__(TM * GROUPS, 1) k_guess_tc(StepArgs a, const d
                 *reinterpret_cast<uint4*>(&A[koff(row, kc, K1)]) = *reinterpret_cast<const uint4*>(h);
             }
         }
-        // layer 1
+        // layer 1 (none in a test of the bounded waits: the barrier then never completes)
         handoff();
-        if (row == 0) {
+        if (row == 0 && !test) {
             issue_layer(tbase, A, s.W1, K1, H);
             mma_commit(bar);
         }
@@ -306,7 +313,7 @@ __global__ void __launch_bounds__(TM * GROUPS, 1) k_guess_tc(StepArgs a, const d
     }
     if (timed_out) {
         if (row == 0) raise_flag(a.flag, FLAG_TIMEOUT);
-        mbar_wait(bar, parity ^ 1u);         // bounded: let the group's MMAs in flight finish before TMEM is freed
+        mbar_wait(bar, parity ^ 1u, limit);  // bounded: let the group's MMAs in flight finish before TMEM is freed
     }
     fence_before();
     __syncthreads();

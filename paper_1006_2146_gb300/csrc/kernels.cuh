@@ -48,6 +48,7 @@ struct StepArgs {
     void* modes_out;    // dense output: every space-time mode of the predictor (L x NV x N, R), or null
     int emf_transonic;  // MHD: twice the dissipative term of the EMF fluxes at transonic faces
     int defer_nonfinite;  // the positivity fallback checks the updated state itself (after its passes)
+    int wait_test;      // the learned-guess kernel's test of its bounded waits (ader_test_bounded_wait)
     int tiled;          // Euler, orders 2-3: predictor and face solves per 2.5-D tile (k_pf_tile), fluxes
                         // stored once per face in S1; 0: face data of every zone through S3 (MHD, order 4)
 };

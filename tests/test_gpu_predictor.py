@@ -265,3 +265,33 @@ def test_fp32_learned_guess_ten_steps(ader, trained_guess):
     s.close()
     assert capped == 0
     assert rel_l1(to_host(d), Uo) <= 1e-5
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_bounded_tensor_core_wait_runs_out_and_the_context_recovers(ader, trained_guess, fp32):
+    """Failure detection without a GPU fault: an armed guess launch issues no MMA for its first layer, so the
+    barrier it waits on never completes; the bounded wait gives up, the step status is ADER_ERR_TIMEOUT, and
+    the kernel freed its tensor memory: the next launches on the same context (the guess alone, then a
+    converged step from the guess) run normally and match the oracle."""
+    import torch
+    from paper_1006_2146_gb300 import _lib
+    shape = (12, 11, 13)
+    U = inputs.random_smooth(shape, seed=71, amp=0.3)
+    dx = _dx(shape)
+    dt = 0.8 * scheme.max_dt(U, dx, 0.4)
+    n = U[0].size
+    s = ader.Solver(shape, order=3, form="modal", fp32=fp32)
+    s.set_guess(trained_guess)
+    G = torch.full((25, n), 7.0, dtype=torch.float32, device="cuda")
+    ader.ader_test_bounded_wait(s.h)
+    ader.ader_guess_eval(s.h, to_dev(U), None, dt, G)
+    assert s.status() == _lib.ADER_ERR_TIMEOUT
+    ader.ader_guess_eval(s.h, to_dev(U), None, dt, G)     # not armed any more
+    assert s.status() == 0
+    s.set_predictor(1e-6 if fp32 else TOL, 50)
+    d = to_dev(U)
+    s.step(d, dt)
+    assert s.status() == 0
+    s.close()
+    want = scheme.ader_step(U, dx, dt, 3, "modal", "hll", tol=TOL)
+    assert rel_l1(to_host(d), want) <= (1e-6 if fp32 else 1e-12)
