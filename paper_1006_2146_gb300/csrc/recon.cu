@@ -146,24 +146,22 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_cross1_tiled(Grid g, const floa
                 s4[ty + 2][tx + 4] = w4[pk + xy_ip];
             }
             __syncthreads();
-            float a[5];
+            // the six slopes in three packed pairs (weno3_x2): (S_y w2, S_x w3), (S_z w3, S_y w4),
+            // (S_z w2, S_x w4) -- each pair is also the pair of terms of one cross moment
+            float2 a[5], r0, r1, r2, unused;
 #pragma unroll
-            for (int o = 0; o < 5; ++o) a[o] = s2[ty + o][tx];
-            const float sy2 = slope(a);
+            for (int o = 0; o < 5; ++o) a[o] = make_float2(s2[ty + o][tx], s3[ty][tx + o]);
+            weno3_x2<false>(a, r0, unused);
 #pragma unroll
-            for (int o = 0; o < 5; ++o) a[o] = s3[ty][tx + o];
-            const float sx3 = slope(a);
+            for (int o = 0; o < 5; ++o) a[o] = make_float2(c3[o], s4[ty + o][tx + 2]);
+            weno3_x2<false>(a, r1, unused);
 #pragma unroll
-            for (int o = 0; o < 5; ++o) a[o] = s4[ty + o][tx + 2];
-            const float sy4 = slope(a);
-#pragma unroll
-            for (int o = 0; o < 5; ++o) a[o] = s4[ty + 2][tx + o];
-            const float sx4 = slope(a);
-            const float sz3 = slope(c3), sz2 = slope(c2);
+            for (int o = 0; o < 5; ++o) a[o] = make_float2(c2[o], s4[ty + 2][tx + o]);
+            weno3_x2<false>(a, r2, unused);
             const long long z = pk + xy;
-            S2[(0 * NV + v) * N + z] = 0.5f * (sy2 + sx3);
-            S2[(1 * NV + v) * N + z] = 0.5f * (sz3 + sy4);
-            S2[(2 * NV + v) * N + z] = 0.5f * (sz2 + sx4);
+            S2[(0 * NV + v) * N + z] = 0.5f * (r0.x + r0.y);
+            S2[(1 * NV + v) * N + z] = 0.5f * (r1.x + r1.y);
+            S2[(2 * NV + v) * N + z] = 0.5f * (r2.x + r2.y);
             __syncthreads();
         }
     }

@@ -112,6 +112,45 @@ ADER_DEV void weno4(const R* a, R& b, R& c, R& d) {
     d = (al[0] * cd[0] + al[1] * cd[1] + al[2] * cd[2] + al[3] * cd[3]) * inv;
 }
 
+// ---------------------------------------------------------------- FP32: two stencils at once
+// GB300's FP32 units execute packed pairs (one FADD2 / FMUL2 / FFMA2 does two FP32 operations), and the
+// FP32 WENO kernels are bound by instruction issue, so the FP32 path blends two independent stencils
+// (two variables, or two directions) per instruction: the same order-3 WENO as weno3_doubled, each
+// component rounded as the scalar operations would round it, except the reciprocals (hardware
+// approximations in both).
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float2 f2rcp(float2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+
+// b (and c) of the order-3 WENO of the two stencils a[0..4].x and a[0..4].y (a[2] = centre)
+template <bool WANT_C>
+__device__ __forceinline__ void weno3_x2(const float2* a, float2& b, float2& c) {
+    const float2 d1 = f2sub(a[1], a[0]), d2 = f2sub(a[2], a[1]), d3 = f2sub(a[3], a[2]), d4 = f2sub(a[4], a[3]);
+    const float2 three = f2s(3.f);
+    const float2 B0 = f2fma(three, d2, make_float2(-d1.x, -d1.y)), C0 = f2sub(d2, d1);
+    const float2 B1 = f2add(d2, d3), C1 = f2sub(d3, d2);
+    const float2 B2 = f2fma(three, d3, make_float2(-d4.x, -d4.y)), C2 = f2sub(d4, d3);
+    const float2 k13 = f2s(13.0f / 3.0f), eps4 = f2s((float)(4.0 * WENO_EPS));
+    // q = (4 EPS + B^2 + 13/3 C^2)^2; weights (1, 10, 1) / q
+    const float2 t0 = f2add(eps4, f2fma(B0, B0, f2mul(k13, f2mul(C0, C0))));
+    const float2 t1 = f2add(eps4, f2fma(B1, B1, f2mul(k13, f2mul(C1, C1))));
+    const float2 t2 = f2add(eps4, f2fma(B2, B2, f2mul(k13, f2mul(C2, C2))));
+    const float2 a0 = f2rcp(f2mul(t0, t0));
+    const float2 a1 = f2mul(f2s(10.f), f2rcp(f2mul(t1, t1)));
+    const float2 a2 = f2rcp(f2mul(t2, t2));
+    const float2 h = f2mul(f2s(0.5f), f2rcp(f2add(f2add(a0, a1), a2)));
+    b = f2mul(f2fma(a0, B0, f2fma(a1, B1, f2mul(a2, B2))), h);
+    if (WANT_C) c = f2mul(f2fma(a0, C0, f2fma(a1, C1, f2mul(a2, C2))), h);
+}
+
 template <class R>
 ADER_DEV R slope(const R* a) {
     R b, c;
@@ -145,6 +184,47 @@ ADER_DEV void zone_weno1d(const Grid& g, const T* __restrict__ U, const R* __res
                           R* __restrict__ S1, long long z) {
     int i, j, k;
     zone_ijk(g, z, i, j, k);
+#ifdef __CUDA_ARCH__
+    if constexpr (ORDER <= 3 && NV == 5 && sizeof(R) == 4 && sizeof(T) == 4) {
+        // FP32 Euler: the fifteen stencils (variable v, direction d) in seven pairs and one single
+        long long off[3][4];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) off[d][o] = nbr_along(g, z, i, j, k, d, o < 2 ? o - 2 : o - 1) - z;
+        float st[15][5];
+#pragma unroll
+        for (int q = 0; q < 15; ++q) {
+            const int v = q / 3, d = q % 3;
+            const T* Uv = U + (long long)v * g.n + z;
+            st[q][0] = Uv[off[d][0]];
+            st[q][1] = Uv[off[d][1]];
+            st[q][2] = Uv[0];
+            st[q][3] = Uv[off[d][2]];
+            st[q][4] = Uv[off[d][3]];
+        }
+#pragma unroll
+        for (int q = 0; q < 15; q += 2) {
+            float2 a[5], b, c;
+            if (q + 1 < 15) {
+#pragma unroll
+                for (int o = 0; o < 5; ++o) a[o] = make_float2(st[q][o], st[q + 1][o]);
+            } else {
+#pragma unroll
+                for (int o = 0; o < 5; ++o) a[o] = make_float2(st[q][o], st[q][o]);
+            }
+            weno3_x2<ORDER == 3>(a, b, c);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (q + u >= 15) break;
+                const int v = (q + u) / 3, d = (q + u) % 3;
+                S1[((0 * 3 + d) * NV + v) * g.n + z] = u ? b.y : b.x;
+                if (ORDER == 3) S1[((1 * 3 + d) * NV + v) * g.n + z] = u ? c.y : c.x;
+            }
+        }
+        return;
+    }
+#endif
     constexpr int RAD = ORDER == 4 ? 3 : 2;
     // the stencil's neighbour offsets, once for all variables (offset 0 is the zone itself)
     long long off[3][2 * RAD + 1];
