@@ -119,7 +119,9 @@ ADER_DEV void weno4(const R* a, R& b, R& c, R& d) {
 // component rounded as the scalar operations would round it, except the reciprocals (hardware
 // approximations in both).
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// a - b as b * (-1) + a: one packed FFMA2, rounded once like the subtraction (a negated operand of a
+// packed addition is not folded into the instruction)
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -134,10 +136,10 @@ __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 template <bool WANT_C>
 __device__ __forceinline__ void weno3_x2(const float2* a, float2& b, float2& c) {
     const float2 d1 = f2sub(a[1], a[0]), d2 = f2sub(a[2], a[1]), d3 = f2sub(a[3], a[2]), d4 = f2sub(a[4], a[3]);
-    const float2 three = f2s(3.f);
-    const float2 B0 = f2fma(three, d2, make_float2(-d1.x, -d1.y)), C0 = f2sub(d2, d1);
+    const float2 two = f2s(2.f);
+    const float2 C0 = f2sub(d2, d1), B0 = f2fma(two, d2, C0);                  // 3 d2 - d1
     const float2 B1 = f2add(d2, d3), C1 = f2sub(d3, d2);
-    const float2 B2 = f2fma(three, d3, make_float2(-d4.x, -d4.y)), C2 = f2sub(d4, d3);
+    const float2 C2 = f2sub(d4, d3), B2 = f2fma(two, d3, f2sub(d3, d4));      // 3 d3 - d4
     const float2 k13 = f2s(13.0f / 3.0f), eps4 = f2s((float)(4.0 * WENO_EPS));
     // q = (4 EPS + B^2 + 13/3 C^2)^2; weights (1, 10, 1) / q
     const float2 t0 = f2add(eps4, f2fma(B0, B0, f2mul(k13, f2mul(C0, C0))));
