@@ -62,13 +62,13 @@ __global__ void __launch_bounds__(256) kb_face_b(BatchGroupDev g) {
     });
 }
 
-// the FP32 copy of each problem's state (five values per zone)
+// the FP32 copy of each problem's state (five values per zone), rounded by integer operations
 static __global__ void __launch_bounds__(256) kb_to_f32(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) {
         float* Uf = const_cast<float*>(it.a.Uf);
         const long long N = it.a.grid.n;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) Uf[v * N + z] = (float)it.U[v * N + z];
+        for (int v = 0; v < 5; ++v) Uf[v * N + z] = f32_of_f64(it.U[v * N + z]);
     });
 }
 
@@ -108,13 +108,16 @@ __global__ void __launch_bounds__(BATCH_PREDICT_MAX_THREADS, 3) kb_predict_faces
     });
 }
 
-// U += dt L(U) in place, dt from the problem's dt_dev (fused fluxes: the FP64 accumulation bounds the
-// FP32-bulk update, not the Riemann solves)
+// U += dt L(U) in place, dt from the problem's dt_dev: both faces of each direction solved per zone, the
+// differences carried in FP32 pairs and only the accumulation in FP64 (zone_flux_update_pair)
 template <int SOLVER, int NV, class R>
 __global__ void __launch_bounds__(256) kb_flux_update(BatchGroupDev g) {
     batch_for(g, [](const BatchItem& it, long long z) {
         const StepArgs a = it.a;
-        zone_flux_update<SOLVER, NV, R>(a, it.U, it.U, 1.0, 1, z);
+        if constexpr (sizeof(R) == 4)
+            zone_flux_update_pair<SOLVER, NV>(a, it.U, it.U, 1.0, 1, z);
+        else
+            zone_flux_update<SOLVER, NV, R>(a, it.U, it.U, 1.0, 1, z);
     });
 }
 

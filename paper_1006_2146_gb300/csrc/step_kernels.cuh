@@ -386,6 +386,30 @@ __global__ void __launch_bounds__(128) k_flux_update_pair(StepArgs a, double* ou
     store_pair_update(a, out, base, hi, lo, z);
 }
 
+// The same update for one zone whose block may not share its problem (the batched kernels): c_d's FP32
+// head and tail taken per zone, the split by integer conversions (one FP64 product and one difference
+// per direction).
+template <int SOLVER, int NV>
+__device__ __forceinline__ void zone_flux_update_pair(const StepArgs& a, double* out, const double* base,
+                                                      double c_host, int use_dt_dev, long long z) {
+    int i, j, k;
+    zone_ijk(a.grid, z, i, j, k);
+    const double c = use_dt_dev ? c_host * (*a.dt_dev) : c_host;
+    float chi[3], clo[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double cd = c * a.idx[d];
+        chi[d] = f32_of_f64(cd);
+        clo[d] = f32_of_f64(cd - f64_of_f32(chi[d]));
+    }
+    const float gamma = a.gamma_f, gm1 = a.gm1_f;
+    float hi[5] = {0, 0, 0, 0, 0}, lo[5] = {0, 0, 0, 0, 0};
+    flux_difference_pair<SOLVER, 0, NV>(a, z, i, j, k, gamma, gm1, chi[0], clo[0], hi, lo);
+    flux_difference_pair<SOLVER, 1, NV>(a, z, i, j, k, gamma, gm1, chi[1], clo[1], hi, lo);
+    flux_difference_pair<SOLVER, 2, NV>(a, z, i, j, k, gamma, gm1, chi[2], clo[2], hi, lo);
+    store_pair_update(a, out, base, hi, lo, z);
+}
+
 template <int SOLVER, int NV, class R>
 ADER_DEV void zone_face_fluxes(const StepArgs& a, long long z) {
     int i, j, k;

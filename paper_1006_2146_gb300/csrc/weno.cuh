@@ -224,42 +224,43 @@ ADER_DEV void zone_weno1d(const Grid& g, const T* __restrict__ U, const R* __res
                 if (ORDER == 3) S1[((1 * 3 + d) * NV + v) * g.n + z] = u ? c.y : c.x;
             }
         }
-        return;
-    }
+    } else
 #endif
-    constexpr int RAD = ORDER == 4 ? 3 : 2;
-    // the stencil's neighbour offsets, once for all variables (offset 0 is the zone itself)
-    long long off[3][2 * RAD + 1];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int o = -RAD; o <= RAD; ++o) off[d][o + RAD] = o == 0 ? 0 : nbr_along(g, z, i, j, k, d, o) - z;
-    for (int v = 0; v < NV; ++v) {
-        const T* Uv = v < 5 ? U + (long long)v * g.n + z : nullptr;
-        const R* Bv = v >= 5 ? ZB + (long long)(v - 5) * g.n + z : nullptr;
-        const R centre = v < 5 ? R(Uv[0]) : Bv[0];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (v >= 5 && d == v - 5) continue;
-            R a[2 * RAD + 1];
-#pragma unroll
-            for (int o = -RAD; o <= RAD; ++o) {
-                if (o == 0)
-                    a[RAD] = centre;
-                else
-                    a[o + RAD] = v < 5 ? R(Uv[off[d][o + RAD]]) : Bv[off[d][o + RAD]];
-            }
-            if (ORDER == 4) {
-                R b, c, e;
-                weno4(a, b, c, e);
-                S1[((0 * 3 + d) * NV + v) * g.n + z] = b;
-                S1[((1 * 3 + d) * NV + v) * g.n + z] = c;
-                S1[((2 * 3 + d) * NV + v) * g.n + z] = e;
-            } else {
-                R b, c;
-                weno3(a, b, c);
-                S1[((0 * 3 + d) * NV + v) * g.n + z] = b;
-                if (ORDER == 3) S1[((1 * 3 + d) * NV + v) * g.n + z] = c;
+    {
+        constexpr int RAD = ORDER == 4 ? 3 : 2;
+        // the stencil's neighbour offsets, once for all variables (offset 0 is the zone itself)
+        long long off[3][2 * RAD + 1];
+    #pragma unroll
+        for (int d = 0; d < 3; ++d)
+    #pragma unroll
+            for (int o = -RAD; o <= RAD; ++o) off[d][o + RAD] = o == 0 ? 0 : nbr_along(g, z, i, j, k, d, o) - z;
+        for (int v = 0; v < NV; ++v) {
+            const T* Uv = v < 5 ? U + (long long)v * g.n + z : nullptr;
+            const R* Bv = v >= 5 ? ZB + (long long)(v - 5) * g.n + z : nullptr;
+            const R centre = v < 5 ? R(Uv[0]) : Bv[0];
+    #pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (v >= 5 && d == v - 5) continue;
+                R a[2 * RAD + 1];
+    #pragma unroll
+                for (int o = -RAD; o <= RAD; ++o) {
+                    if (o == 0)
+                        a[RAD] = centre;
+                    else
+                        a[o + RAD] = v < 5 ? R(Uv[off[d][o + RAD]]) : Bv[off[d][o + RAD]];
+                }
+                if (ORDER == 4) {
+                    R b, c, e;
+                    weno4(a, b, c, e);
+                    S1[((0 * 3 + d) * NV + v) * g.n + z] = b;
+                    S1[((1 * 3 + d) * NV + v) * g.n + z] = c;
+                    S1[((2 * 3 + d) * NV + v) * g.n + z] = e;
+                } else {
+                    R b, c;
+                    weno3(a, b, c);
+                    S1[((0 * 3 + d) * NV + v) * g.n + z] = b;
+                    if (ORDER == 3) S1[((1 * 3 + d) * NV + v) * g.n + z] = c;
+                }
             }
         }
     }
@@ -270,6 +271,50 @@ template <int ORDER, int NV, class R>
 ADER_DEV void zone_cross1(const Grid& g, const R* __restrict__ S1, R* __restrict__ S2, long long z) {
     int i, j, k;
     zone_ijk(g, z, i, j, k);
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(R) == 4) {
+        // FP32: the two slopes of each first-level cross moment as one packed pair (weno3_x2); the
+        // neighbour offsets once per zone
+        long long off[3][5];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int o = 0; o < 5; ++o) off[d][o] = o == 2 ? 0 : nbr_along(g, z, i, j, k, d, o - 2) - z;
+        for (int v = 0; v < NV; ++v) {
+            const R* w2 = S1 + ((0 * 3 + 0) * NV + v) * g.n + z;
+            const R* w3 = S1 + ((0 * 3 + 1) * NV + v) * g.n + z;
+            const R* w4 = S1 + ((0 * 3 + 2) * NV + v) * g.n + z;
+            float2 a[5], r, unused;
+#pragma unroll
+            for (int o = 0; o < 5; ++o) a[o] = make_float2(w2[off[1][o]], w3[off[0][o]]);
+            weno3_x2<false>(a, r, unused);
+            S2[(0 * NV + v) * g.n + z] = 0.5f * (r.x + r.y);
+#pragma unroll
+            for (int o = 0; o < 5; ++o) a[o] = make_float2(w3[off[2][o]], w4[off[1][o]]);
+            weno3_x2<false>(a, r, unused);
+            S2[(1 * NV + v) * g.n + z] = 0.5f * (r.x + r.y);
+#pragma unroll
+            for (int o = 0; o < 5; ++o) a[o] = make_float2(w2[off[2][o]], w4[off[0][o]]);
+            weno3_x2<false>(a, r, unused);
+            S2[(2 * NV + v) * g.n + z] = 0.5f * (r.x + r.y);
+            if (ORDER == 4) {
+                const R* w5 = S1 + ((1 * 3 + 0) * NV + v) * g.n + z;
+                const R* w6 = S1 + ((1 * 3 + 1) * NV + v) * g.n + z;
+                const R* w7 = S1 + ((1 * 3 + 2) * NV + v) * g.n + z;
+                const R* src[6] = {w5, w5, w6, w6, w7, w7};
+                const int dir[6] = {1, 2, 0, 2, 0, 1};             // w14 .. w19
+#pragma unroll
+                for (int c = 0; c < 6; c += 2) {
+#pragma unroll
+                    for (int o = 0; o < 5; ++o) a[o] = make_float2(src[c][off[dir[c]][o]], src[c + 1][off[dir[c + 1]][o]]);
+                    weno3_x2<false>(a, r, unused);
+                    S2[((3 + c) * NV + v) * g.n + z] = r.x;
+                    S2[((4 + c) * NV + v) * g.n + z] = r.y;
+                }
+            }
+        }
+    } else
+#endif
     for (int v = 0; v < NV; ++v) {
         const R* w2 = S1 + ((0 * 3 + 0) * NV + v) * g.n;
         const R* w3 = S1 + ((0 * 3 + 1) * NV + v) * g.n;
