@@ -175,7 +175,9 @@ int ader_set_predictor(ader_ctx* ctx, double tol, int max_iter);
  * zone stay in shared memory, every face inside the tile is solved once, and
  * only the tile's boundary sides pass through memory.  on = 0: every zone
  * writes its face data to the context's scratch and a second pass solves the
- * faces.  Both give the same numbers bit for bit; MHD contexts and order 4
+ * faces.  Both give the same numbers bit for bit in FP64 (in FP32 bulk to
+ * FP32 rounding: the compiler may contract the predictor's multiply-adds
+ * differently in the two kernels); MHD contexts and order 4
  * always take the second layout (the edge fields need the face data of four
  * zones; the fourth-order predictor's cost dwarfs the face data's traffic).
  * ADER_ERR_ARG for a NULL context. */

@@ -127,6 +127,25 @@ __device__ __forceinline__ double f64_of_f32(float f) {
     return __hiloint2double((int)((b & 0x80000000u) | (ed << 20) | (mant >> 3)), (int)(mant << 29));
 }
 
+// x > 0 for an FP64 argument that is not NaN (tolerances, step sizes), decided on its bit pattern: the
+// FP32 kernels then issue no FP64 comparison per zone
+ADER_DEV bool positive_arg(double x) {
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(x) > 0;
+#else
+    return x > 0.0;
+#endif
+}
+
+// an FP64 argument in the bulk precision R (FP32: rounded by integer operations on the device)
+template <class R>
+ADER_DEV R bulk_arg(double x) {
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(R) == 4) return f32_of_f64(x);
+#endif
+    return R(x);
+}
+
 // ------------------------------------------------------------------ physics, Eq. 3 (Gaussian units)
 // NV = 5: Euler (rho, rho v, eps).  NV = 8: ideal MHD (rho, rho v, eps, B) with
 // eps = rho v^2/2 + P/(gamma-1) + B^2/(8 pi).

@@ -143,13 +143,13 @@ ADER_DEV void record_iterations(unsigned long long* stats, const PredCtl& ctl) {
 // source, the whole space-time polynomial for dense output).  m[1..L] holds the space-time modes after.
 // SRC: the context carries a non-stiff source (orders with ZoneOps::HAS_SOURCE); the predictor then also
 // writes dt S-bar of Eq. 6 for the update (a.Sb).
+// dt_in: the step size (the caller reads a.dt_dev, once per thread where it can)
 template <int ORDER, int FORM, int NV, class R, bool SRC = false>
-ADER_DEV void zone_predict(const StepArgs& a, const double* __restrict__ U, long long z, Vec<NV, R>* m) {
+ADER_DEV void zone_predict(const StepArgs& a, const double* __restrict__ U, long long z, Vec<NV, R>* m, R dt) {
     constexpr int LS = ModeCount<ORDER>::LS, L = ModeCount<ORDER>::L;
     load_modes<ORDER>(a, U, z, m);
 #pragma unroll
     for (int k = LS + 1; k <= L; ++k) m[k] = vzero<NV, R>();
-    const R dt = R(a.dt_dev ? *a.dt_dev : a.dt);
     const R gm1 = arg_gm1<R>(a);
     const R cx = dt * arg_idx<R>(a, 0), cy = dt * arg_idx<R>(a, 1), cz = dt * arg_idx<R>(a, 2);
     if (a.n_iter > 0) {      // n_iter = 0: spatial polynomial only (SSP-RK face rule)
@@ -166,7 +166,7 @@ ADER_DEV void zone_predict(const StepArgs& a, const double* __restrict__ U, long
             Src<R> src;
             src.kind = a.src_kind;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) src.a[i] = dt * R(a.src_par[i]);
+            for (int i = 0; i < 3; ++i) src.a[i] = dt * bulk_arg<R>(a.src_par[i]);
             Vec<NV, R> sdt;
             if (FORM == FORM_MODAL)
                 ZoneOps<ORDER>::predict_modal_src(m, gm1, cx, cy, cz, ctl, src, sdt);
@@ -180,7 +180,7 @@ ADER_DEV void zone_predict(const StepArgs& a, const double* __restrict__ U, long
         } else {
             ZoneOps<ORDER>::predict_nodal(m, gm1, cx, cy, cz, ctl);
         }
-        if (a.tol > 0.0 && a.stats) record_iterations(a.stats, ctl);
+        if (a.stats && positive_arg(a.tol)) record_iterations(a.stats, ctl);
         if (ctl.capped) raise_flag(a.flag, FLAG_NOT_CONVERGED);
     }
     if (a.modes_out) {      // dense output (Sec. VII): keep the whole space-time polynomial of the step
@@ -195,7 +195,7 @@ ADER_DEV void zone_predict(const StepArgs& a, const double* __restrict__ U, long
 template <int ORDER, int FORM, int NV, class R, bool SRC = false>
 ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U, long long z) {
     Vec<NV, R> m[ModeCount<ORDER>::L + 1];
-    zone_predict<ORDER, FORM, NV, R, SRC>(a, U, z, m);
+    zone_predict<ORDER, FORM, NV, R, SRC>(a, U, z, m, bulk_arg<R>(a.dt_dev ? *a.dt_dev : a.dt));
     const R gm1 = arg_gm1<R>(a);
     store_faces<ORDER, 0>(a, z, m, gm1);
     store_faces<ORDER, 1>(a, z, m, gm1);
@@ -594,6 +594,7 @@ ADER_DEV void pt_store_flux(const StepArgs& a, long long zl, const Vec<5, R>& f)
 template <int ORDER, int FORM, int SOLVER, class R, bool SRC>
 __global__ void __launch_bounds__(PT_THREADS, sizeof(R) == 4 ? 3 : 1)
     k_pf_tile(StepArgs a, const double* __restrict__ U, int cz) {
+
     extern __shared__ __align__(16) unsigned char pt_raw[];
     R* sh = reinterpret_cast<R*>(pt_raw);
     const Grid& g = a.grid;
@@ -605,6 +606,7 @@ __global__ void __launch_bounds__(PT_THREADS, sizeof(R) == 4 ? 3 : 1)
     const bool last_x = tx == PT_X - 1 || i == g.nx - 1, last_y = ty == PT_Y - 1 || j == g.ny - 1;
     const R gamma = arg_gamma<R>(a), gm1 = arg_gm1<R>(a);
     const long long nxy = (long long)g.nx * g.ny;
+    const R dt = bulk_arg<R>(a.dt_dev ? *a.dt_dev : a.dt);     // once per thread, for every plane
     const PtBoundary bd = pt_boundary(g, cz);
     R* S3 = (R*)a.S3;
     R* bx = S3 + bd.ox;
@@ -616,7 +618,7 @@ __global__ void __launch_bounds__(PT_THREADS, sizeof(R) == 4 ? 3 : 1)
         const int zp_slot = (k & 1) ? 6 : 4;          // this plane's z+ sides; the previous plane's in the other
         if (valid) {
             Vec<5, R> m[ModeCount<ORDER>::L + 1];
-            zone_predict<ORDER, FORM, 5, R, SRC>(a, U, z, m);
+            zone_predict<ORDER, FORM, 5, R, SRC>(a, U, z, m, dt);
             pt_sides<ORDER, 0>(sh, tid, 0, 1, m, gm1);
             pt_sides<ORDER, 1>(sh, tid, 2, 3, m, gm1);
             pt_sides<ORDER, 2>(sh, tid, zp_slot, 5, m, gm1);

@@ -9,7 +9,7 @@ namespace o2 {
 
 template <int NV, class R>
 ADER_DEV void finish_o2(Vec<NV, R>* m, const Vec<NV, R>& n5, PredCtl& ctl) {
-    const bool conv = ctl.tol > 0.0;
+    const bool conv = positive_arg(ctl.tol);
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
     const R ref = max_abs(m[1]) + R(1e-300);
     ctl.iters = 0;
@@ -59,7 +59,7 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
 // iterate.  `next(m5)` gives the new u5 for the current one.
 template <int NV, class R, class Next>
 ADER_DEV void iterate_o2(Vec<NV, R>* m, PredCtl& ctl, Next next) {
-    const bool conv = ctl.tol > 0.0;
+    const bool conv = positive_arg(ctl.tol);
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
     const R ref = max_abs(m[1]) + R(1e-300);
     ctl.iters = 0;

@@ -81,7 +81,7 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
         s1 = sn[1];
         S1 = s1 + (S5 + S6 + S7) / 12.0;
     }
-    const bool conv = ctl.tol > 0.0;
+    const bool conv = positive_arg(ctl.tol);
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
     const R ref = max_abs(m[1]) + R(1e-300);
     ctl.iters = 0;
@@ -213,7 +213,7 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
     const Vec<NV, R> g0 = 0.5 * m[11] + 0.25 * m[12];
     Vec<NV, R> u11 = u[1] + g0, u12 = u[2] + g0 + 0.25 * m[13], u13 = u[4] + g0 + 0.25 * m[14];
     Vec<NV, R> u14 = u[6] + g0 + 0.25 * m[15], u15 = u[1] + m[11] + m[12];
-    const bool conv = ctl.tol > 0.0;
+    const bool conv = positive_arg(ctl.tol);
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
     const R ref = max_abs(m[1]) + R(1e-300);
     ctl.iters = 0;

@@ -199,7 +199,7 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
     const Vec<NV, R> e25 = -(scale(cx, F8) + scale(cy, 2.0 * G6) + scale(cz, H9));
     const Vec<NV, R> e26 = -(scale(cx, F10) + scale(cy, G9) + scale(cz, 2.0 * H7));
 
-    const bool conv = ctl.tol > 0.0;
+    const bool conv = positive_arg(ctl.tol);
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
     const R ref = max_abs(m[1]) + R(1e-300);
     ctl.iters = 0;
@@ -413,7 +413,7 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
     // tau > 0 nodes of Eq. C.1
     Vec<NV, R> e[16];
     nodal_o4_initial(u, m, e);
-    const bool conv = ctl.tol > 0.0;
+    const bool conv = positive_arg(ctl.tol);
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
     const R ref = max_abs(m[1]) + R(1e-300);
     ctl.iters = 0;
