@@ -68,9 +68,11 @@ def ader_step(U, dx, dt, order, form="nodal", solver="hll", gamma=1.4, Bface=Non
         Un = Un + res[2][:5]
     out = Un
     if mhd:
-        Bn = ct_update(Bface, F, edge_data, Uz, order, gamma, solver, dt, dx, emf_transonic)
+        E = edge_emfs(edge_fluxes(edge_data, Uz, order, gamma, solver, emf_transonic))
+        Bn = ct_from_emfs(Bface, E, dt, dx)
         if positivity:
-            Un = positivity_fallback(U, Un, F, dx, dt, gamma, None if source is None else res[2][:5], Uz=Uz, Bnew=Bn)
+            Un, Bn = positivity_fallback(U, Un, F, dx, dt, gamma, None if source is None else res[2][:5], Uz=Uz,
+                                         Bnew=Bn, Bold=Bface, E=E)
         out = (Un, Bn)
     elif positivity:
         out = positivity_fallback(U, Un, F, dx, dt, gamma, None if source is None else res[2][:5])
@@ -79,7 +81,7 @@ def ader_step(U, dx, dt, order, form="nodal", solver="hll", gamma=1.4, Bface=Non
     return out
 
 
-def positivity_fallback(U, Un, F, dx, dt, gamma, extra=None, passes=3, Uz=None, Bnew=None):
+def positivity_fallback(U, Un, F, dx, dt, gamma, extra=None, passes=3, Uz=None, Bnew=None, Bold=None, E=None):
     """A posteriori positivity fallback (an option of this implementation; the paper names none).
 
     Zones whose updated average is non-physical (rho <= 0, P <= 0 or not finite) are marked; every face
@@ -87,31 +89,55 @@ def positivity_fallback(U, Un, F, dx, dt, gamma, extra=None, passes=3, Uz=None, 
     zone averages as both the barycentre and the averaged states), and every zone is updated again from
     U^n with the modified fluxes, which its neighbour across each face shares (so the update stays
     conservative).  `passes` rounds, the marks accumulating.  `extra` is the source part (dt S-bar) of the
-    update.  MHD (Uz: the zone states of step n with the zone field of the face-B reconstruction; Bnew:
-    the face field after constrained transport, which the fallback leaves alone): a zone's pressure is
-    taken with the mean of its two new face values per direction, and the first-order flux is the MHD
-    one, of which the five hydrodynamic components replace the stored fluxes."""
+    update.
+
+    MHD (Uz: the zone states of step n with the zone field of the face-B reconstruction; Bold: the face
+    field of step n; E: the step's edge fields (Ex, Ey, Ez); Bnew: the face field after constrained
+    transport): a zone's pressure is taken with the mean of its two new face values per direction, and
+    the first-order flux is the MHD one, of which the five hydrodynamic components replace the stored
+    fluxes.  Every edge that touches a marked zone takes the first-order electric field, Eq. 7's mean of
+    the four adjacent faces' first-order fluxes (the edge averages of a piecewise-constant state are its
+    zone averages), and the face field is advanced again from step n by Eq. 8 with those edges: low-beta
+    zones, whose pressure is a small difference of energies, otherwise keep the high-order field's
+    errors.  The discrete curl keeps div B for any edge fields.  Returns Un, or (Un, Bn) for MHD."""
     mark = np.zeros(U.shape[1:], dtype=bool)
     F = [f[:5].copy() for f in F]
-    if Bnew is not None:
-        zB = np.stack([0.5 * (Bnew[d] + weno.shift(Bnew[d], d, 1)) for d in range(3)])
+    mhd = Bnew is not None
     W = U if Uz is None else Uz
+    F1 = []
+    for d in range(3):
+        WR = weno.shift(W, d, 1)
+        F1.append(riemann.hll(d, gamma, W, WR, W, WR, physics.flux(W, gamma, d), physics.flux(WR, gamma, d), W, WR))
+    if mhd:
+        E1 = edge_emfs([{(e, se): F1[d] for e in range(3) if e != d for se in (+1, -1)} for d in range(3)])
+        sh = weno.shift
+        # edge touching zones: x-edge (j+1/2, k+1/2) the zones (j..j+1, k..k+1), likewise for y and z
+        around = ((1, 2), (0, 2), (0, 1))
     for _ in range(passes):
-        state = Un if Bnew is None else np.concatenate([Un, zB])
+        if mhd:
+            zB = np.stack([0.5 * (Bnew[d] + weno.shift(Bnew[d], d, 1)) for d in range(3)])
+            state = np.concatenate([Un, zB])
+        else:
+            state = Un
         mark |= ~physics.physical(state, gamma)
         if not mark.any():
             break
         for d in range(3):
             face = mark | weno.shift(mark, d, 1)          # face i+1/2 is stored at zone i
-            WR = weno.shift(W, d, 1)
-            f1 = riemann.hll(d, gamma, W, WR, W, WR, physics.flux(W, gamma, d), physics.flux(WR, gamma, d), W, WR)
-            F[d] = np.where(face[None], f1[:5], F[d])
+            F[d] = np.where(face[None], F1[d][:5], F[d])
         Un = U.copy()
         for d in range(3):
             Un = Un - (dt / dx[d]) * (F[d] - weno.shift(F[d], d, -1))
         if extra is not None:
             Un = Un + extra
-    return Un
+        if mhd:
+            Em = []
+            for c in range(3):
+                a, b = around[c]
+                touch = mark | sh(mark, a, 1) | sh(mark, b, 1) | sh(sh(mark, a, 1), b, 1)
+                Em.append(np.where(touch, E1[c], E[c]))
+            Bnew = ct_from_emfs(Bold, Em, dt, dx)
+    return (Un, Bnew) if mhd else Un
 
 
 def max_dt(U, dx, cfl, gamma=1.4, Bface=None):
@@ -173,7 +199,12 @@ def edge_emfs(Fe):
 def ct_update(Bface, F, edge_data, Uz, order, gamma, solver, dt, dx, emf_transonic=False):
     """Face-averaged B at t^{n+1} by the discrete Stokes theorem of Eq. 8.  emf_transonic: the electric
     fields take twice the dissipation at transonic faces (Sec. V's option for Eq. 17)."""
-    Ex, Ey, Ez = edge_emfs(edge_fluxes(edge_data, Uz, order, gamma, solver, emf_transonic))
+    return ct_from_emfs(Bface, edge_emfs(edge_fluxes(edge_data, Uz, order, gamma, solver, emf_transonic)), dt, dx)
+
+
+def ct_from_emfs(Bface, E, dt, dx):
+    """Eq. 8: B^{n+1} = B^n - dt curl E on every face, from the edge fields E = (Ex, Ey, Ez) of edge_emfs."""
+    Ex, Ey, Ez = E
     sh = weno.shift
     # Bface[d][..., i_d] is the face i_d - 1/2: its edges are stored one zone lower along d
     Ez_x, Ey_x = sh(Ez, 0, -1), sh(Ey, 0, -1)

@@ -13,8 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 @pytest.fixture(scope="module")
 def lib():
     from paper_1006_2146_gb300 import _lib, build
-    if not os.path.exists(_lib.LIB_PATH):
-        build.build()
+    build.build()           # incremental: recompiles only what is older than its sources
     return _lib.load()
 
 
