@@ -437,7 +437,7 @@ def velocity_asymmetry(torch, U):
 def blast_symmetry(ader, torch, orders=(2, 3, 4), forms=("modal", "nodal"),
                    cases=(("hydro_blast_96", "hll"), ("mhd_blast_97", "hll"), ("mhd_blast_97", "linearized"),
                           ("mhd_blast_97", "hll_emf_transonic"), ("hydro_blast_96", "hll_positivity"),
-                          ("mhd_blast_97", "hll_positivity"))):
+                          ("mhd_blast_97", "hll_positivity"), ("mhd_blast_97", "linearized_positivity"))):
     """The paper's 3-D blasts run to their end times at CFL 0.3 (FP64): the velocity asymmetry of each
     order and form beside the printed nodal figures, the step count and wall time, or the error status
     of a run that does not finish (the robustness half of the test)."""

@@ -54,6 +54,7 @@ struct ader_ctx {
     void* Sb = nullptr;                       // dt S-bar per zone (5 x N, bulk precision), allocated with the source
     void* Dm = nullptr;                       // dense output: the last step's space-time modes (L x NV x N, bulk)
     double* Uold = nullptr;                   // positivity fallback: U^n of the current step (5 x N FP64)
+    double* Bold = nullptr;                   // MHD positivity fallback: the face field of step n (3 x N FP64)
     unsigned char* pmark = nullptr;           // positivity fallback: zones marked non-physical (N bytes)
     bool dense_valid = false;                 // a step has written Dm since it was allocated
     bool setup_failed = false;                // a kernel could not be configured while enqueuing
@@ -239,6 +240,7 @@ int ader_create(const ader_grid* g, int order, double gamma, int solver, unsigne
     if (flags & ADER_POSITIVITY_FALLBACK) {
         alloc((void**)&c->Uold, N * 5 * sizeof(double), "cudaMalloc U^n copy");
         alloc((void**)&c->pmark, N, "cudaMalloc positivity marks");
+        if (c->mhd) alloc((void**)&c->Bold, N * 3 * sizeof(double), "cudaMalloc B^n copy");
     }
     alloc((void**)&c->flag, sizeof(unsigned), "cudaMalloc flag");
     alloc((void**)&c->stats, 3 * sizeof(unsigned long long), "cudaMalloc predictor statistics");
@@ -275,7 +277,7 @@ void ader_destroy(ader_ctx* c) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->spare) cudaEventDestroy(e);
-    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Glist, c->Gact, c->Gcount, c->Uf, c->Sb, c->Dm, c->Uold, c->pmark, c->flag,
+    void* ptrs[] = {c->S1, c->S2, c->S3, c->ZB, c->E, c->G, c->Glist, c->Gact, c->Gcount, c->Uf, c->Sb, c->Dm, c->Uold, c->Bold, c->pmark, c->flag,
                     c->stats, c->dtscr, c->partial, c->dt_dev,
                     c->Ustage, c->rk[0], c->rk[1], c->rk[2], c->rk[3], c->rk[4], c->rk[5], c->rk[6],
                     c->rkB[0], c->rkB[1], c->rkB[2], c->rkB[3], c->rkB[4], c->rkB[5]};
@@ -378,6 +380,10 @@ static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const d
         if (int rc = cuda_check(c, cudaMemcpyAsync(c->Uold, U, (size_t)c->grid.n * 5 * sizeof(double),
                                                    cudaMemcpyDeviceToDevice, st), "copy of U^n"))
             return rc;
+    if (c->Bold)
+        if (int rc = cuda_check(c, cudaMemcpyAsync(c->Bold, Bface, (size_t)c->grid.n * 3 * sizeof(double),
+                                                   cudaMemcpyDeviceToDevice, st), "copy of B^n"))
+            return rc;
     c->launches = enqueue_operator(c, a, U, U, U, coef, dt_dev != nullptr, st);
     if (c->Dm) c->dense_valid = true;
     if (c->setup_failed) {
@@ -391,7 +397,7 @@ static int step_common(ader_ctx* c, double* U, double* Bface, double dt, const d
     }
     if (c->Uold) {          // after constrained transport: an MHD zone's pressure takes the new face field
         Trace t(c, "positivity_fallback", st);
-        c->launches += launch_positivity_fallback(a, U, c->Uold, c->pmark, coef, dt_dev != nullptr, st);
+        c->launches += launch_positivity_fallback(a, U, c->Uold, c->Bold, c->pmark, coef, dt_dev != nullptr, st);
     }
     return cuda_check(c, cudaGetLastError(), "ader_step launch");
 }

@@ -90,9 +90,10 @@ inline int s3_per_zone(int mhd, int linearized = 0) {
 template <class R> int launch_recon(const StepArgs& a, const double* U, cudaStream_t st);
 // out[i] = (float)U[i], i < count (the FP32 copy of the state the FP32 WENO reads)
 int launch_to_f32(float* out, const double* U, long long count, cudaStream_t st);
-// FP64 Euler: first-order fluxes on the faces of zones left non-physical, conservative re-update (positivity.cu)
-int launch_positivity_fallback(const StepArgs& a, double* U, const double* Uold, unsigned char* mark, double c_host,
-                               bool use_dt_dev, cudaStream_t st);
+// FP64: first-order fluxes on the faces of zones left non-physical, conservative re-update; MHD (Bold: the face
+// field of step n) also first-order edge fields around them and Eq. 8 again (positivity.cu)
+int launch_positivity_fallback(const StepArgs& a, double* U, const double* Uold, const double* Bold,
+                               unsigned char* mark, double c_host, bool use_dt_dev, cudaStream_t st);
 // dense output: the LS spatial modes at time tau of the space-time modes kept by a step (dense.cu)
 int launch_dense_eval(int order, int nv, bool fp32, const void* modes, long long N, double tau, double* out,
                       cudaStream_t st);

@@ -3,8 +3,10 @@
 // are marked; every face of a marked zone gets the first-order HLL flux of the two zone averages of U^n
 // (Eq. 56 with the zone averages as barycentre and averaged states), written over the stored face flux;
 // every zone next to a marked one is then updated again from U^n with the stored fluxes, which both
-// zones of a face share, so the step stays conservative.  Three passes, the marks accumulating; a pass
-// with no mark changes nothing.  The update leaves the non-finite check to the fallback, which mends such
+// zones of a face share, so the step stays conservative.  MHD: every edge touching a marked zone also
+// takes the first-order electric field, and the faces around those edges are advanced again from the
+// face field of step n (Eq. 8; div B is kept).  Three passes, the marks accumulating; a pass with no mark
+// changes nothing.  The update leaves the non-finite check to the fallback, which mends such
 // zones like non-physical ones and checks the state (and, for MHD, the face field) after its passes.
 #include "kernels.cuh"
 #include "riemann.cuh"
@@ -101,6 +103,90 @@ __global__ void __launch_bounds__(128) k_pos_update(StepArgs a, double* U, const
     if (near) zone_flux_update_stored<double>(a, U, Uold, c_host, use_dt_dev, z);
 }
 
+// MHD: the first-order electric field of every edge that touches a marked zone (Eq. 7's mean of the four
+// adjacent faces' fluxes, each the first-order HLL flux of the zone states of step n: the edge averages of
+// a piecewise-constant state are its zone averages), written over the step's edge field in E.  Zone z
+// owns its three upper edges, as in zone_emf: Ex on (j+1/2, k+1/2), Ey on (i+1/2, k+1/2), Ez on
+// (i+1/2, j+1/2).
+template <int D>
+ADER_DEV Vec<8, double> first_order_flux(const StepArgs& a, const double* Uold, long long zl, long long zr) {
+    FaceSide<8, double> L, Rt;
+    L.ub = L.avg = state_n<8>(a, Uold, zl);
+    Rt.ub = Rt.avg = state_n<8>(a, Uold, zr);
+    L.F = flux<D>(L.ub, a.gm1);
+    Rt.F = flux<D>(Rt.ub, a.gm1);
+    return riemann_hll<D>(L, Rt, a.gamma, a.gm1);
+}
+
+__global__ void __launch_bounds__(128) k_pos_emf(StepArgs a, const double* __restrict__ Uold,
+                                                 const unsigned char* __restrict__ mark) {
+    const Grid& g = a.grid;
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= g.n) return;
+    int i, j, k;
+    zone_ijk(g, z, i, j, k);
+    const long long zx = nbr(g, i, j, k, 1, 0, 0), zy = nbr(g, i, j, k, 0, 1, 0), zz = nbr(g, i, j, k, 0, 0, 1);
+    const long long zxy = nbr(g, i, j, k, 1, 1, 0), zxz = nbr(g, i, j, k, 1, 0, 1), zyz = nbr(g, i, j, k, 0, 1, 1);
+    const bool m0 = mark[z], mx = mark[zx], my = mark[zy], mz = mark[zz];
+    double* E = (double*)a.E;
+    if (m0 || mx || my || mark[zxy]) {          // Ez = (-F7 - F7 + G6 + G6) / 4
+        const double f1 = first_order_flux<0>(a, Uold, z, zx)[6], f2 = first_order_flux<0>(a, Uold, zy, zxy)[6];
+        const double g1 = first_order_flux<1>(a, Uold, z, zy)[5], g2 = first_order_flux<1>(a, Uold, zx, zxy)[5];
+        E[2 * g.n + z] = 0.25 * (-f1 - f2 + g1 + g2);
+    }
+    if (m0 || mx || mz || mark[zxz]) {          // Ey = (F8 + F8 - H6 - H6) / 4
+        const double f1 = first_order_flux<0>(a, Uold, z, zx)[7], f2 = first_order_flux<0>(a, Uold, zz, zxz)[7];
+        const double h1 = first_order_flux<2>(a, Uold, z, zz)[5], h2 = first_order_flux<2>(a, Uold, zx, zxz)[5];
+        E[g.n + z] = 0.25 * (f1 + f2 - h1 - h2);
+    }
+    if (m0 || my || mz || mark[zyz]) {          // Ex = (-G8 - G8 + H7 + H7) / 4
+        const double g1 = first_order_flux<1>(a, Uold, z, zy)[7], g2 = first_order_flux<1>(a, Uold, zz, zyz)[7];
+        const double h1 = first_order_flux<2>(a, Uold, z, zz)[6], h2 = first_order_flux<2>(a, Uold, zy, zyz)[6];
+        E[z] = 0.25 * (-g1 - g2 + h1 + h2);
+    }
+}
+
+// MHD: Eq. 8 again from the face field of step n on the faces with an edge next to a marked zone (the
+// others keep the step's value, which the same arithmetic gives).  Zone z owns its faces i-1/2, j-1/2,
+// k-1/2 (as in zone_ct), whose edges are stored one zone lower along the face's normal; a face's four
+// edges touch the zones within one of it in the face's plane, on both of its sides.
+__global__ void __launch_bounds__(128) k_pos_ct(StepArgs a, double* __restrict__ Bf, const double* __restrict__ Bold,
+                                                const unsigned char* __restrict__ mark, double c_host,
+                                                int use_dt_dev) {
+    const Grid& g = a.grid;
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= g.n) return;
+    int i, j, k;
+    zone_ijk(g, z, i, j, k);
+    bool near[3] = {false, false, false};          // x, y, z faces of zone z
+#pragma unroll
+    for (int dk = -1; dk <= 1; ++dk)
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) {
+                if (!mark[nbr(g, i, j, k, di, dj, dk)]) continue;
+                // the face i-1/2 lies between x-offsets -1 and 0; its edges reach one zone along y and z
+                near[0] |= di <= 0;
+                near[1] |= dj <= 0;
+                near[2] |= dk <= 0;
+            }
+    if (!(near[0] || near[1] || near[2])) return;
+    const double* E = (const double*)a.E;
+    const long long N = g.n;
+    auto Ex = [&](int di, int dj, int dk) { return E[nbr(g, i, j, k, di, dj, dk)]; };
+    auto Ey = [&](int di, int dj, int dk) { return E[N + nbr(g, i, j, k, di, dj, dk)]; };
+    auto Ez = [&](int di, int dj, int dk) { return E[2 * N + nbr(g, i, j, k, di, dj, dk)]; };
+    const double dt = use_dt_dev ? c_host * (*a.dt_dev) : c_host;
+    const double idx = a.idx[0], idy = a.idx[1], idz = a.idx[2];
+    if (near[0]) Bf[z] = Bold[z] - dt * ((Ez(-1, 0, 0) - Ez(-1, -1, 0)) * idy - (Ey(-1, 0, 0) - Ey(-1, 0, -1)) * idz);
+    if (near[1])
+        Bf[N + z] = Bold[N + z] - dt * ((Ex(0, -1, 0) - Ex(0, -1, -1)) * idz - (Ez(0, -1, 0) - Ez(-1, -1, 0)) * idx);
+    if (near[2])
+        Bf[2 * N + z] =
+            Bold[2 * N + z] - dt * ((Ey(0, 0, -1) - Ey(-1, 0, -1)) * idx - (Ex(0, 0, -1) - Ex(0, -1, -1)) * idy);
+}
+
 // After the passes (the update deferred its own check to here): a zone value that is not finite raises
 // FLAG_NONFINITE, and so does, for MHD, a face field value that is not finite: the fallback replaces only
 // hydrodynamic face fluxes, so a non-finite edge field written by constrained transport survives its
@@ -126,8 +212,8 @@ __global__ void __launch_bounds__(256) k_pos_check(Grid g, const double* __restr
 
 }  // namespace
 
-int launch_positivity_fallback(const StepArgs& a, double* U, const double* Uold, unsigned char* mark, double c_host,
-                               bool use_dt_dev, cudaStream_t st) {
+int launch_positivity_fallback(const StepArgs& a, double* U, const double* Uold, const double* Bold,
+                               unsigned char* mark, double c_host, bool use_dt_dev, cudaStream_t st) {
     const long long N = a.grid.n;
     if (N <= 0) return 0;
     cudaMemsetAsync(mark, 0, (size_t)N, st);
@@ -143,6 +229,11 @@ int launch_positivity_fallback(const StepArgs& a, double* U, const double* Uold,
         }
         k_pos_update<<<b128, 128, 0, st>>>(a, U, Uold, mark, c_host, use_dt_dev ? 1 : 0);
         n += 3;
+        if (a.mhd && Bold) {        // first-order edge fields around the marks, Eq. 8 again from step n
+            k_pos_emf<<<b128, 128, 0, st>>>(a, Uold, mark);
+            k_pos_ct<<<b128, 128, 0, st>>>(a, const_cast<double*>(a.Bface), Bold, mark, c_host, use_dt_dev ? 1 : 0);
+            n += 2;
+        }
     }
     if (a.mhd)
         k_pos_check<8><<<b256, 256, 0, st>>>(a.grid, U, a.Bface, a.gm1, a.flag);
