@@ -24,31 +24,35 @@ namespace ader {
 // ---------------------------------------------------------------- per-problem CFL dt
 // Every block works on one problem (padded layout, 256 zones per block and
 // iteration); its maximum goes to smax[p] as the bit pattern of a
-// non-negative double, which orders like an unsigned integer.
+// non-negative double, which orders like an unsigned integer.  Every batched
+// problem is FP32 bulk: each zone's signal speed is FP32 from the state rounded
+// by integer operations, with the FP32 copies of gamma and 1/dx (no FP64
+// division or conversion per zone), as the single-problem FP32 reduction; the
+// block's maximum is widened to FP64 exactly.
 __global__ void __launch_bounds__(256) kb_max_dt(BatchGroupDev g, unsigned long long* smax) {
-    __shared__ double wm[8];
+    __shared__ float wm[8];
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < g.total; base += stride) {
         const long long gz = base + threadIdx.x;
         const int p = batch_find(g.zpad, g.np, base);          // the same for the whole block
         const BatchItem& it = g.items[p];
-        const Grid& gr = it.a.grid;
+        const Grid gr = it.a.grid;
         const long long z = gz - g.zpad[p];
-        double s = 0.0;
-        if (z < gr.n) {      // signal speed in FP32 (every batched problem is FP32 bulk); maximum in FP64
+        float s = 0.f;
+        if (z < gr.n) {
             using F = float;
             const long long N = gr.n;
             const double* U = it.U;
-            const F gamma = F(it.a.gamma);
-            const F rho = F(U[z]), mx = F(U[N + z]), my = F(U[2 * N + z]), mz = F(U[3 * N + z]), E = F(U[4 * N + z]);
+            const F gamma = it.a.gamma_f;
+            const F ix = it.a.idx_f[0], iy = it.a.idx_f[1], iz = it.a.idx_f[2];
+            const F rho = f32_of_f64(U[z]), mx = f32_of_f64(U[N + z]), my = f32_of_f64(U[2 * N + z]),
+                    mz = f32_of_f64(U[3 * N + z]), E = f32_of_f64(U[4 * N + z]);
             const F ir = F(1) / rho;
             const F vx = mx * ir, vy = my * ir, vz = mz * ir;
-            const F idx = F(1.0 / it.a.dx[0]), idy = F(1.0 / it.a.dx[1]), idz = F(1.0 / it.a.dx[2]);
             bool bad;
             if (it.Bf) {
-                const int i = (int)(z % gr.nx);
-                const long long t = z / gr.nx;
-                const int j = (int)(t % gr.ny), k = (int)(t / gr.ny);
+                int i, j, k;
+                zone_ijk(gr, z, i, j, k);
                 const double* Bf = it.Bf;
                 Vec<8, F> u;
                 u[0] = rho; u[1] = mx; u[2] = my; u[3] = mz; u[4] = E;
@@ -58,27 +62,26 @@ __global__ void __launch_bounds__(256) kb_max_dt(BatchGroupDev g, unsigned long 
                 const Prim<8, F> q = primitives(u, gamma - F(1));
                 bad = !(rho > F(0)) || !(q.p > F(0));
                 if (!bad)
-                    s = (double)((fabsf(vx) + fast_speed<0>(u, q, gamma)) * idx +
-                                 (fabsf(vy) + fast_speed<1>(u, q, gamma)) * idy +
-                                 (fabsf(vz) + fast_speed<2>(u, q, gamma)) * idz);
+                    s = (fabsf(vx) + fast_speed<0>(u, q, gamma)) * ix + (fabsf(vy) + fast_speed<1>(u, q, gamma)) * iy +
+                        (fabsf(vz) + fast_speed<2>(u, q, gamma)) * iz;
             } else {
                 const F pr = (gamma - F(1)) * (E - F(0.5) * (mx * vx + my * vy + mz * vz));
                 bad = !(rho > F(0)) || !(pr > F(0));
                 if (!bad) {
                     const F a = sqrtf(gamma * pr * ir);
-                    s = (double)((fabsf(vx) + a) * idx + (fabsf(vy) + a) * idy + (fabsf(vz) + a) * idz);
+                    s = (fabsf(vx) + a) * ix + (fabsf(vy) + a) * iy + (fabsf(vz) + a) * iz;
                 }
             }
             if (bad) raise_flag(it.a.flag, FLAG_UNPHYSICAL);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        for (int o = 16; o > 0; o >>= 1) s = fmaxf(s, __shfl_xor_sync(0xffffffffu, s, o));
         if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = s;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double b = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, wm[w]);
-            atomicMax(&smax[p], (unsigned long long)__double_as_longlong(b));
+            float b = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, wm[w]);
+            atomicMax(&smax[p], (unsigned long long)__double_as_longlong(f64_of_f32(b)));
         }
         __syncthreads();
     }
@@ -168,7 +171,7 @@ int phase_nv(int nv, int ph, const BatchGroupDev& g, int form, int solver, int T
 int run_phase(const Group& gr, int ph, int T, int B, cudaStream_t st, bool go, const void** fn) {
     BatchGroupDev g{gr.items_dev, gr.zpad_dev, (int)gr.members.size(), gr.total};
     const int nv = gr.mhd ? 8 : 5;
-    if (B <= 0) B = (int)std::max<long long>(1, (gr.total + T - 1) / T);
+    if (B <= 0 || !batch_phase_persistent(ph)) B = (int)std::max<long long>(1, (gr.total + T - 1) / T);
     switch (gr.order) {
         case 2: return phase_nv<2>(nv, ph, g, gr.form, gr.solver, T, B, st, go, fn);
         case 3: return phase_nv<3>(nv, ph, g, gr.form, gr.solver, T, B, st, go, fn);
@@ -462,7 +465,7 @@ int ader_batch_tune(ader_batch* b, double* const* U, double* const* Bface, void*
             if (!batch_phase_applies(ph, g.order, g.mhd)) continue;
             Tuned best;
             for (int T : Ts) {
-                if (ph == PH_PREDICT && T > BATCH_PREDICT_MAX_THREADS) continue;
+                if (T > batch_phase_max_threads(ph)) continue;
                 const void* fn = nullptr;
                 run_phase(g, ph, T, 1, st, false, &fn);
                 int occ = 0;
@@ -471,7 +474,7 @@ int ader_batch_tune(ader_batch* b, double* const* U, double* const* Bface, void*
                 const long long full = (g.total + T - 1) / T;
                 const int cand[5] = {b->sms * occ, b->sms * occ * 2, b->sms * occ * 4, b->sms * occ * 8, 0};
                 for (int B : cand) {
-                    if (B > 0 && B >= full) continue;          // same as the full grid
+                    if (B > 0 && (B >= full || !batch_phase_persistent(ph))) continue;   // same as the full grid
                     // one warm-up, then the best of three
                     if (run_phase(g, ph, T, B, st, true, nullptr) < 0) {
                         rc = fail(b, ADER_ERR_CUDA, "tuning launch");

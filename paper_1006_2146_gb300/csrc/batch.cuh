@@ -42,104 +42,153 @@ ADER_DEV int batch_find(const long long* __restrict__ zpad, int np, long long gz
     return lo;
 }
 
-// Calls f(item, z) for every real zone of the group (grid-stride over the padded range).
-template <class F>
-ADER_DEV void batch_for(const BatchGroupDev& g, F f) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long gz = (long long)blockIdx.x * blockDim.x + threadIdx.x; gz < g.total; gz += stride) {
-        const int p = batch_find(g.zpad, g.np, gz);
-        const BatchItem& it = g.items[p];
-        const long long z = gz - g.zpad[p];
-        if (z < it.a.grid.n) f(it, z);
-    }
+// The grid-stride walk over the group's padded range: the first padded index of this thread and the
+// stride; batch_zone maps a padded index to its problem's item and zone index (false for a padding
+// zone).  Every kernel below writes the walk out itself, so that the zone's code is inlined into the
+// kernel (a per-zone call through a lambda was compiled as a real call, with the predictor's registers
+// spilled around it).
+ADER_DEV long long batch_first() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+ADER_DEV long long batch_stride() { return (long long)gridDim.x * blockDim.x; }
+
+ADER_DEV bool batch_zone(const BatchGroupDev& g, long long gz, const BatchItem*& it, long long& z) {
+    const int p = batch_find(g.zpad, g.np, gz);
+    it = g.items + p;
+    z = gz - g.zpad[p];
+    return z < it->a.grid.n;
 }
 
 template <int ORDER, class R>
 __global__ void __launch_bounds__(256) kb_face_b(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) {
-        const Grid gr = it.a.grid;    // local copies: the loop's stores cannot alias them
-        zone_face_b<ORDER, R>(gr, it.Bf, (R*)it.a.ZB, (R*)it.a.S1, z);
-    });
+    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
+        const BatchItem* it;
+        long long z;
+        if (!batch_zone(g, gz, it, z)) continue;
+        const Grid gr = it->a.grid;    // local copies: the zone's stores cannot alias them
+        zone_face_b<ORDER, R>(gr, it->Bf, (R*)it->a.ZB, (R*)it->a.S1, z);
+    }
 }
 
 // the FP32 copy of each problem's state (five values per zone), rounded by integer operations
 static __global__ void __launch_bounds__(256) kb_to_f32(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) {
-        float* Uf = const_cast<float*>(it.a.Uf);
-        const long long N = it.a.grid.n;
+    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
+        const BatchItem* it;
+        long long z;
+        if (!batch_zone(g, gz, it, z)) continue;
+        float* Uf = const_cast<float*>(it->a.Uf);
+        const double* U = it->U;
+        const long long N = it->a.grid.n;
+        double u[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) Uf[v * N + z] = f32_of_f64(it.U[v * N + z]);
-    });
+        for (int v = 0; v < 5; ++v) u[v] = U[v * N + z];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Uf[v * N + z] = f32_of_f64(u[v]);
+    }
 }
 
 template <int ORDER, int NV, class R>
-__global__ void __launch_bounds__(256) kb_weno1d(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) {
-        const Grid gr = it.a.grid;
-        zone_weno1d<ORDER, NV, R>(gr, it.a.Uf, (const R*)it.a.ZB, (R*)it.a.S1, z);
-    });
+__global__ void __launch_bounds__(128, 5) kb_weno1d(BatchGroupDev g) {
+    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
+        const BatchItem* it;
+        long long z;
+        if (!batch_zone(g, gz, it, z)) continue;
+        const Grid gr = it->a.grid;
+        zone_weno1d<ORDER, NV, R>(gr, it->a.Uf, (const R*)it->a.ZB, (R*)it->a.S1, z);
+    }
 }
 
+// at most 128 zones per block and three blocks per SM, as the single-problem kernel gets them: at order 4
+// the cross moments need about 170 registers, and with 256-thread blocks only one block fits an SM
 template <int ORDER, int NV, class R>
-__global__ void __launch_bounds__(256) kb_cross1(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) {
-        const Grid gr = it.a.grid;
-        zone_cross1<ORDER, NV, R>(gr, (const R*)it.a.S1, (R*)it.a.S2, z);
-    });
+__global__ void __launch_bounds__(128, 3) kb_cross1(BatchGroupDev g) {
+    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
+        const BatchItem* it;
+        long long z;
+        if (!batch_zone(g, gz, it, z)) continue;
+        const Grid gr = it->a.grid;
+        zone_cross1<ORDER, NV, R>(gr, (const R*)it->a.S1, (R*)it->a.S2, z);
+    }
 }
 
 template <int NV, class R>
 __global__ void __launch_bounds__(256) kb_cross2(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) {
-        const Grid gr = it.a.grid;
-        zone_cross2<NV, R>(gr, (R*)it.a.S2, z);
-    });
+    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
+        const BatchItem* it;
+        long long z;
+        if (!batch_zone(g, gz, it, z)) continue;
+        const Grid gr = it->a.grid;
+        zone_cross2<NV, R>(gr, (R*)it->a.S2, z);
+    }
 }
 
-// at most 128 zones per block, three blocks per SM (as the single-problem FP32 predictor): the tuner
-// tries no larger block for this phase
+// at most 128 zones per block, three blocks per SM (two at order 4), as the single-problem FP32 predictor
 constexpr int BATCH_PREDICT_MAX_THREADS = 128;
 
+// One zone per thread (never persistent): a grid-stride loop around the predictor's body keeps a few
+// more values live through it, and at 168 registers those spill (about 1 KB more local traffic per zone
+// at order 3); the launch covers the padded range (batch_phase_persistent).
 template <int ORDER, int FORM, int NV, class R>
-__global__ void __launch_bounds__(BATCH_PREDICT_MAX_THREADS, 3) kb_predict_faces(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) {
-        const StepArgs a = it.a;      // a local copy: the arguments stay in registers across the face stores
-        zone_predict_faces<ORDER, FORM, NV, R>(a, it.U, z);
-    });
+__global__ void __launch_bounds__(BATCH_PREDICT_MAX_THREADS, ORDER == 4 ? 2 : 3) kb_predict_faces(BatchGroupDev g) {
+    const long long gz = batch_first();
+    if (gz >= g.total) return;
+    const BatchItem* it;
+    long long z;
+    if (!batch_zone(g, gz, it, z)) return;
+    zone_predict_faces<ORDER, FORM, NV, R>(it->a, it->U, z);     // arguments read in place (fewer spills
+                                                                  // than a copy)
 }
 
 // U += dt L(U) in place, dt from the problem's dt_dev: both faces of each direction solved per zone, the
 // differences carried in FP32 pairs and only the accumulation in FP64 (zone_flux_update_pair)
 template <int SOLVER, int NV, class R>
 __global__ void __launch_bounds__(256) kb_flux_update(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) {
-        const StepArgs a = it.a;
+    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
+        const BatchItem* it;
+        long long z;
+        if (!batch_zone(g, gz, it, z)) continue;
+        const StepArgs a = it->a;
+        double* U = it->U;
         if constexpr (sizeof(R) == 4)
-            zone_flux_update_pair<SOLVER, NV>(a, it.U, it.U, 1.0, 1, z);
+            zone_flux_update_pair<SOLVER, NV>(a, U, U, 1.0, 1, z);
         else
-            zone_flux_update<SOLVER, NV, R>(a, it.U, it.U, 1.0, 1, z);
-    });
+            zone_flux_update<SOLVER, NV, R>(a, U, U, 1.0, 1, z);
+    }
 }
 
 template <class R>
 __global__ void __launch_bounds__(256) kb_emf(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) {
-        const StepArgs a = it.a;
+    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
+        const BatchItem* it;
+        long long z;
+        if (!batch_zone(g, gz, it, z)) continue;
+        const StepArgs a = it->a;
         zone_emf<R>(a, z);
-    });
+    }
 }
 
 template <class R>
 __global__ void __launch_bounds__(256) kb_ct(BatchGroupDev g) {
-    batch_for(g, [](const BatchItem& it, long long z) {
-        const StepArgs a = it.a;
-        zone_ct<R>(a, it.Bf, 1.0, 1, z);
-    });
+    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
+        const BatchItem* it;
+        long long z;
+        if (!batch_zone(g, gz, it, z)) continue;
+        const StepArgs a = it->a;
+        double* Bf = it->Bf;
+        zone_ct<R>(a, Bf, 1.0, 1, z);
+    }
 }
 
 // Phases of one step, in order; a group runs those that apply to it.
 enum BatchPhase { PH_TO_F32 = 0, PH_FACE_B, PH_WENO1D, PH_CROSS1, PH_CROSS2, PH_PREDICT, PH_UPDATE, PH_EMF, PH_CT,
                   PH_COUNT };
+
+// whether a phase's kernel walks the group's range with a grid-stride loop (any grid size), or needs a
+// thread for every padded zone
+inline bool batch_phase_persistent(int ph) { return ph != PH_PREDICT; }
+
+// the largest block a phase's kernel is compiled for (its launch bounds)
+inline int batch_phase_max_threads(int ph) {
+    return ph == PH_PREDICT ? BATCH_PREDICT_MAX_THREADS : (ph == PH_WENO1D || ph == PH_CROSS1) ? 128 : 256;
+}
 
 inline bool batch_phase_applies(int ph, int order, int mhd) {
     switch (ph) {

@@ -202,10 +202,12 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
     store_faces<ORDER, 2>(a, z, m, gm1);
 }
 
-// FP32 bulk asks for three 128-thread blocks per SM (at most 168 registers, a few hundred bytes of
-// spills to L1): the extra warps hide more latency than the spills cost (about 12% per 256^3 step).
+// FP32 bulk asks for three 128-thread blocks per SM at orders 2-3 (at most 168 registers, a few hundred
+// bytes of spills to L1): the extra warps hide more latency than the spills cost (about 12% per 256^3
+// step).  At order 4 the predictor spills kilobytes per zone at 168 registers; it takes two blocks per
+// SM and 255 registers.
 template <int ORDER, int FORM, int NV, class R, bool SRC = false>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (ORDER == 4 ? 2 : 3) : 1)
     k_predict_faces(StepArgs a, const double* __restrict__ U) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z < a.grid.n) zone_predict_faces<ORDER, FORM, NV, R, SRC>(a, U, z);
@@ -327,14 +329,22 @@ __device__ __forceinline__ void store_pair_update(const StepArgs& a, double* out
     const float* Sb = (const float*)a.Sb;
     const unsigned lanes = __activemask();         // the lanes of this zone's warp still running
     bool bad = false;
+    // every load before the first store (out may be base: in place)
+    double b[5];
+    float sb[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-        double val = base ? base[v * N + z] : 0.0;
+        b[v] = base ? base[v * N + z] : 0.0;
+        sb[v] = Sb ? Sb[v * N + z] : 0.0f;
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        double val = b[v];
         if (__any_sync(lanes, hi[v] != 0.0f)) val += f64_of_f32(hi[v]);
         const unsigned e_lo = (__float_as_uint(lo[v]) >> 23) & 0xffu;
         const unsigned e_t = ((unsigned)__double2hiint(val) >> 20) & 0x7ffu;
         if (__any_sync(lanes, lo[v] != 0.0f && e_lo + 951u > e_t)) val += f64_of_f32(lo[v]);
-        if (Sb) val += f64_of_f32(Sb[v * N + z]);
+        if (Sb) val += f64_of_f32(sb[v]);
         bad |= !finite_bits(val);
         out[v * N + z] = val;
     }

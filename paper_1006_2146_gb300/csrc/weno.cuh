@@ -234,10 +234,13 @@ ADER_DEV void zone_weno1d(const Grid& g, const T* __restrict__ U, const R* __res
         for (int d = 0; d < 3; ++d)
     #pragma unroll
             for (int o = -RAD; o <= RAD; ++o) off[d][o + RAD] = o == 0 ? 0 : nbr_along(g, z, i, j, k, d, o) - z;
+        // per variable the three directions' moments before any store (a store could alias the next
+        // loads for all the compiler knows, and would hold them back)
         for (int v = 0; v < NV; ++v) {
             const T* Uv = v < 5 ? U + (long long)v * g.n + z : nullptr;
             const R* Bv = v >= 5 ? ZB + (long long)(v - 5) * g.n + z : nullptr;
             const R centre = v < 5 ? R(Uv[0]) : Bv[0];
+            R m[3][3];
     #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 if (v >= 5 && d == v - 5) continue;
@@ -249,18 +252,17 @@ ADER_DEV void zone_weno1d(const Grid& g, const T* __restrict__ U, const R* __res
                     else
                         a[o + RAD] = v < 5 ? R(Uv[off[d][o + RAD]]) : Bv[off[d][o + RAD]];
                 }
-                if (ORDER == 4) {
-                    R b, c, e;
-                    weno4(a, b, c, e);
-                    S1[((0 * 3 + d) * NV + v) * g.n + z] = b;
-                    S1[((1 * 3 + d) * NV + v) * g.n + z] = c;
-                    S1[((2 * 3 + d) * NV + v) * g.n + z] = e;
-                } else {
-                    R b, c;
-                    weno3(a, b, c);
-                    S1[((0 * 3 + d) * NV + v) * g.n + z] = b;
-                    if (ORDER == 3) S1[((1 * 3 + d) * NV + v) * g.n + z] = c;
-                }
+                if (ORDER == 4)
+                    weno4(a, m[d][0], m[d][1], m[d][2]);
+                else
+                    weno3(a, m[d][0], m[d][1]);
+            }
+    #pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (v >= 5 && d == v - 5) continue;
+                S1[((0 * 3 + d) * NV + v) * g.n + z] = m[d][0];
+                if (ORDER >= 3) S1[((1 * 3 + d) * NV + v) * g.n + z] = m[d][1];
+                if (ORDER == 4) S1[((2 * 3 + d) * NV + v) * g.n + z] = m[d][2];
             }
         }
     }
@@ -280,23 +282,22 @@ ADER_DEV void zone_cross1(const Grid& g, const R* __restrict__ S1, R* __restrict
         for (int d = 0; d < 3; ++d)
 #pragma unroll
             for (int o = 0; o < 5; ++o) off[d][o] = o == 2 ? 0 : nbr_along(g, z, i, j, k, d, o - 2) - z;
+        // per variable every result before any store: a store could alias the next loads for all the
+        // compiler knows (the batched kernels pass no restricted pointers), and would hold them back
         for (int v = 0; v < NV; ++v) {
             const R* w2 = S1 + ((0 * 3 + 0) * NV + v) * g.n + z;
             const R* w3 = S1 + ((0 * 3 + 1) * NV + v) * g.n + z;
             const R* w4 = S1 + ((0 * 3 + 2) * NV + v) * g.n + z;
-            float2 a[5], r, unused;
+            float2 a[5], r[6], unused;
 #pragma unroll
             for (int o = 0; o < 5; ++o) a[o] = make_float2(w2[off[1][o]], w3[off[0][o]]);
-            weno3_x2<false>(a, r, unused);
-            S2[(0 * NV + v) * g.n + z] = 0.5f * (r.x + r.y);
+            weno3_x2<false>(a, r[0], unused);
 #pragma unroll
             for (int o = 0; o < 5; ++o) a[o] = make_float2(w3[off[2][o]], w4[off[1][o]]);
-            weno3_x2<false>(a, r, unused);
-            S2[(1 * NV + v) * g.n + z] = 0.5f * (r.x + r.y);
+            weno3_x2<false>(a, r[1], unused);
 #pragma unroll
             for (int o = 0; o < 5; ++o) a[o] = make_float2(w2[off[2][o]], w4[off[0][o]]);
-            weno3_x2<false>(a, r, unused);
-            S2[(2 * NV + v) * g.n + z] = 0.5f * (r.x + r.y);
+            weno3_x2<false>(a, r[2], unused);
             if (ORDER == 4) {
                 const R* w5 = S1 + ((1 * 3 + 0) * NV + v) * g.n + z;
                 const R* w6 = S1 + ((1 * 3 + 1) * NV + v) * g.n + z;
@@ -307,9 +308,16 @@ ADER_DEV void zone_cross1(const Grid& g, const R* __restrict__ S1, R* __restrict
                 for (int c = 0; c < 6; c += 2) {
 #pragma unroll
                     for (int o = 0; o < 5; ++o) a[o] = make_float2(src[c][off[dir[c]][o]], src[c + 1][off[dir[c + 1]][o]]);
-                    weno3_x2<false>(a, r, unused);
-                    S2[((3 + c) * NV + v) * g.n + z] = r.x;
-                    S2[((4 + c) * NV + v) * g.n + z] = r.y;
+                    weno3_x2<false>(a, r[3 + c / 2], unused);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) S2[(c * NV + v) * g.n + z] = 0.5f * (r[c].x + r[c].y);
+            if (ORDER == 4) {
+#pragma unroll
+                for (int c = 0; c < 6; c += 2) {
+                    S2[((3 + c) * NV + v) * g.n + z] = r[3 + c / 2].x;
+                    S2[((4 + c) * NV + v) * g.n + z] = r[3 + c / 2].y;
                 }
             }
         }
