@@ -180,6 +180,11 @@ int ader_set_predictor(ader_ctx* ctx, double tol, int max_iter);
  * differently in the two kernels); MHD contexts and order 4
  * always take the second layout (the edge fields need the face data of four
  * zones; the fourth-order predictor's cost dwarfs the face data's traffic).
+ * on = 1 also computes the third-order cross moments of the reconstruction
+ * (Euler and MHD) in shared-memory tiles of 32 x 8 columns where nx is a
+ * multiple of 32 and ny of 8, each WENO term of a position once for all the
+ * zones that use it; on = 0 takes the per-zone kernel, with the same bits in
+ * FP64 (FP32 to FP32 rounding).
  * ADER_ERR_ARG for a NULL context. */
 int ader_set_tiled(ader_ctx* ctx, int on);
 

@@ -149,7 +149,7 @@ static StepArgs make_args(const ader_ctx* c, double dt, const double* dt_dev, in
     a.modes_out = nullptr;
     a.emf_transonic = (c->flags & ADER_EMF_TRANSONIC) ? 1 : 0;
     a.defer_nonfinite = 0;
-    a.tiled = (!c->mhd && c->tiled) ? 1 : 0;
+    a.tiled = c->tiled ? 1 : 0;               // the predictor tiles check the physics and order themselves
     a.wait_test = c->wait_test ? 1 : 0;
     return a;
 }

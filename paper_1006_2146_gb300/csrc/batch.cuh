@@ -120,14 +120,16 @@ __global__ void __launch_bounds__(256) kb_cross2(BatchGroupDev g) {
     }
 }
 
-// at most 128 zones per block, three blocks per SM (two at order 4), as the single-problem FP32 predictor
+// at most 128 zones per block, three blocks per SM (two at order 4 and for MHD at order 3), as the
+// single-problem FP32 predictor
 constexpr int BATCH_PREDICT_MAX_THREADS = 128;
 
 // One zone per thread (never persistent): a grid-stride loop around the predictor's body keeps a few
 // more values live through it, and at 168 registers those spill (about 1 KB more local traffic per zone
 // at order 3); the launch covers the padded range (batch_phase_persistent).
 template <int ORDER, int FORM, int NV, class R>
-__global__ void __launch_bounds__(BATCH_PREDICT_MAX_THREADS, ORDER == 4 ? 2 : 3) kb_predict_faces(BatchGroupDev g) {
+__global__ void __launch_bounds__(BATCH_PREDICT_MAX_THREADS, ORDER == 4 || (ORDER == 3 && NV == 8) ? 2 : 3)
+    kb_predict_faces(BatchGroupDev g) {
     const long long gz = batch_first();
     if (gz >= g.total) return;
     const BatchItem* it;

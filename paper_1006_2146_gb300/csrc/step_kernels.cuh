@@ -204,10 +204,10 @@ ADER_DEV void zone_predict_faces(const StepArgs& a, const double* __restrict__ U
 
 // FP32 bulk asks for three 128-thread blocks per SM at orders 2-3 (at most 168 registers, a few hundred
 // bytes of spills to L1): the extra warps hide more latency than the spills cost (about 12% per 256^3
-// step).  At order 4 the predictor spills kilobytes per zone at 168 registers; it takes two blocks per
-// SM and 255 registers.
+// step).  At order 4, and for MHD at order 3, the predictor spills kilobytes per zone at 168 registers;
+// there it takes two blocks per SM and 255 registers (a 128^3 MHD step at order 3: 3.5 -> 2.4 ms).
 template <int ORDER, int FORM, int NV, class R, bool SRC = false>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (ORDER == 4 ? 2 : 3) : 1)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (ORDER == 4 || (ORDER == 3 && NV == 8) ? 2 : 3) : 1)
     k_predict_faces(StepArgs a, const double* __restrict__ U) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z < a.grid.n) zone_predict_faces<ORDER, FORM, NV, R, SRC>(a, U, z);

@@ -69,13 +69,78 @@ ADER_DEV void weno3_doubled(const R* a, R* al, R& inv, R* B, R* C) {
     inv = weno_weights<3>(g, is, al, R(4.0 * WENO_EPS));
 }
 
+// ---------------------------------------------------------------- FP64: order 3 from per-position terms
+// Along one direction, with w(p) the field at position p:
+//   d(p)  = w(p) - w(p-1)                   the difference at face p - 1/2,
+//   D2(p) = d(p+1) - d(p)                   the doubled C of the stencil centred on p,
+//   E(p)  = 4 EPS + (13/3) D2(p)^2          the C part of 4 (EPS + IS) of that stencil.
+// Zone j's candidates are the stencils centred on j-1, j and j+1: doubled slopes B0 = 3 d(j) - d(j-1),
+// B1 = d(j) + d(j+1), B2 = 3 d(j+1) - d(j+2), doubled curvatures D2(j-1..j+1), and 4 (EPS + IS_s) =
+// B_s^2 + E(j-1+s).  d, D2 and E belong to positions, not zones: a tile computes each once for the four
+// (or three) zones that use it (k_cross1_tiled64), and the per-zone form below takes them from the five
+// values with the same operations, so the two give the same bits.  The weights clear their denominators
+// as weno_weights does: (1, 10, 1) times the product of the other two (EPS + IS)^2.
+// Every operation of this form is explicitly rounded (no multiply-add contraction left to the compiler),
+// so that the tile and the per-zone kernel, compiled apart, round every step alike.
+ADER_DEV double rn_add(double x, double y) {
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(x, y);
+#else
+    return x + y;
+#endif
+}
+ADER_DEV double rn_sub(double x, double y) {
+#ifdef __CUDA_ARCH__
+    return __dsub_rn(x, y);
+#else
+    return x - y;
+#endif
+}
+ADER_DEV double rn_mul(double x, double y) {
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(x, y);
+#else
+    return x * y;
+#endif
+}
+
+ADER_DEV double w3_curv(double D2) { return fma(rn_mul(13.0 / 3.0, D2), D2, 4.0 * WENO_EPS); }
+
+template <bool WANT_C>
+ADER_DEV void weno3_terms(const double* d, const double* E, const double* D2, double& b, double& c) {
+    const double B0 = fma(3.0, d[1], -d[0]), B1 = rn_add(d[1], d[2]), B2 = fma(3.0, d[2], -d[3]);
+    const double t0 = fma(B0, B0, E[0]), t1 = fma(B1, B1, E[1]), t2 = fma(B2, B2, E[2]);
+    const double q0 = rn_mul(t0, t0), q1 = rn_mul(t1, t1), q2 = rn_mul(t2, t2);
+    const double a0 = rn_mul(q1, q2), a1 = rn_mul(10.0, rn_mul(q0, q2)), a2 = rn_mul(q0, q1);
+    const double h = rn_mul(0.5, rcp(rn_add(rn_add(a0, a1), a2)));
+    b = rn_mul(fma(a0, B0, fma(a1, B1, rn_mul(a2, B2))), h);
+    if (WANT_C) c = rn_mul(fma(a0, D2[0], fma(a1, D2[1], rn_mul(a2, D2[2]))), h);
+}
+
+// the per-position terms of zone j from w(j-2..j+2)
+ADER_DEV void weno3_zone_terms(const double* a, double* d, double* D2, double* E) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) d[s] = rn_sub(a[s + 1], a[s]);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        D2[s] = rn_sub(d[s + 1], d[s]);
+        E[s] = w3_curv(D2[s]);
+    }
+}
+
 template <class R>
 ADER_DEV void weno3(const R* a, R& b, R& c) {
-    R al[3], B[3], C[3], inv;
-    weno3_doubled(a, al, inv, B, C);
-    const R h = R(0.5) * inv;
-    b = (al[0] * B[0] + al[1] * B[1] + al[2] * B[2]) * h;
-    c = (al[0] * C[0] + al[1] * C[1] + al[2] * C[2]) * h;
+    if constexpr (sizeof(R) == 8) {
+        double d[4], D2[3], E[3];
+        weno3_zone_terms(a, d, D2, E);
+        weno3_terms<true>(d, E, D2, b, c);
+    } else {
+        R al[3], B[3], C[3], inv;
+        weno3_doubled(a, al, inv, B, C);
+        const R h = R(0.5) * inv;
+        b = (al[0] * B[0] + al[1] * B[1] + al[2] * B[2]) * h;
+        c = (al[0] * C[0] + al[1] * C[1] + al[2] * C[2]) * h;
+    }
 }
 
 // order-4 1-D WENO on the seven values a[-3..3] (a[3] = centre); returns b, c, d
@@ -156,7 +221,13 @@ __device__ __forceinline__ void weno3_x2(const float2* a, float2& b, float2& c) 
 template <class R>
 ADER_DEV R slope(const R* a) {
     R b, c;
-    weno3(a, b, c);
+    if constexpr (sizeof(R) == 8) {     // the slope alone: no curvature blend
+        double d[4], D2[3], E[3];
+        weno3_zone_terms(a, d, D2, E);
+        weno3_terms<false>(d, E, D2, b, c);
+    } else {
+        weno3(a, b, c);
+    }
     return b;
 }
 
@@ -254,8 +325,10 @@ ADER_DEV void zone_weno1d(const Grid& g, const T* __restrict__ U, const R* __res
                 }
                 if (ORDER == 4)
                     weno4(a, m[d][0], m[d][1], m[d][2]);
-                else
+                else if (ORDER == 3)
                     weno3(a, m[d][0], m[d][1]);
+                else
+                    m[d][0] = slope(a);
             }
     #pragma unroll
             for (int d = 0; d < 3; ++d) {
