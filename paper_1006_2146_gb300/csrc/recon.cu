@@ -340,6 +340,132 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_cross1_tiled64(Grid g, const do
     }
 }
 
+// FP64 1-D moments at orders 2-3 (w2..w4, and w5..w7 at order 3) in the same tiles: the plane of each
+// variable with two zones of halo in x and y in shared memory, from it the per-position terms (d, D2, E)
+// along x and y, the z terms in registers per column; each zone then blends from four d, three D2 and
+// three E per direction (weno3_terms).  MHD field components (v >= 5) come from the face-B WENO's zone
+// means, and their own direction is left to it, as in zone_weno1d.  Same bits as zone_weno1d.
+// Requires nx % CT_X == 0 and ny % CT_Y == 0 (other grids use k_weno1d).
+template <int ORDER, int NV>
+__global__ void __launch_bounds__(CT_X * CT_Y) k_weno1d_tiled64(Grid g, const double* __restrict__ U,
+                                                                const double* __restrict__ ZB,
+                                                                double* __restrict__ S1) {
+    constexpr bool WANT_C = ORDER == 3;
+    __shared__ double su[CT_Y + 4][CT_X + 4];                         // the plane, x and y halos of two
+    __shared__ double dx[CT_Y][CT_X + 3], cx[CT_Y][CT_X + 2], ex[CT_Y][CT_X + 2];   // at i0 - 1 + c
+    __shared__ double dy[CT_Y + 3][CT_X], cy[CT_Y + 2][CT_X], ey[CT_Y + 2][CT_X];   // at j0 - 1 + r
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tiles_x = g.nx / CT_X;
+    const int i = (int)(blockIdx.x % tiles_x) * CT_X + tx, j = (int)(blockIdx.x / tiles_x) * CT_Y + ty;
+    const int k0 = (int)blockIdx.y * CT_Z, k1 = min(k0 + CT_Z, g.nz);
+    const long long N = g.n;
+    const long long nxy = (long long)g.nx * g.ny;
+    const long long xy = (long long)j * g.nx + i;
+    const long long xy_jm = (long long)wrap(j - 2, g.ny) * g.nx + i, xy_jp = (long long)wrap(j + 2, g.ny) * g.nx + i;
+    const long long xy_im = (long long)j * g.nx + wrap(i - 2, g.nx), xy_ip = (long long)j * g.nx + wrap(i + 2, g.nx);
+    auto plane = [&](int kk) -> long long { return (long long)wrap(kk, g.nz) * nxy; };
+    const int hx_d = tx == 0 ? 0 : CT_X + tx;          // halo entries, as in k_cross1_tiled64
+    const int hx_e = tx == 0 ? 0 : CT_X + 1;
+    const int hy_d = ty == 0 ? 0 : CT_Y + ty;
+    const int hy_e = ty == 0 ? 0 : CT_Y + 1;
+    for (int v = 0; v < NV; ++v) {
+        const double* u = v < 5 ? U + (long long)v * N : ZB + (long long)(v - 5) * N;
+        const int own = v >= 5 ? v - 5 : -1;           // an MHD field's own direction: not reconstructed here
+        double c[5], dz[4], cz[3], ez[3];
+#pragma unroll
+        for (int o = -2; o <= 2; ++o) c[o + 2] = u[plane(k0 + o) + xy];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dz[q] = rn_sub(c[q + 1], c[q]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            cz[q] = rn_sub(dz[q + 1], dz[q]);
+            ez[q] = w3_curv(cz[q]);
+        }
+        for (int k = k0; k < k1; ++k) {
+            if (k > k0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) c[q] = c[q + 1];
+                c[4] = u[plane(k + 2) + xy];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) dz[q] = dz[q + 1];
+                dz[3] = rn_sub(c[4], c[3]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    cz[q] = cz[q + 1];
+                    ez[q] = ez[q + 1];
+                }
+                cz[2] = rn_sub(dz[3], dz[2]);
+                ez[2] = w3_curv(cz[2]);
+            }
+            const long long pk = (long long)k * nxy;
+            su[ty + 2][tx + 2] = c[2];
+            if (ty < 2) su[ty][tx + 2] = u[pk + xy_jm];
+            if (ty >= CT_Y - 2) su[ty + 4][tx + 2] = u[pk + xy_jp];
+            if (tx < 2) su[ty + 2][tx] = u[pk + xy_im];
+            if (tx >= CT_X - 2) su[ty + 2][tx + 4] = u[pk + xy_ip];
+            __syncthreads();
+            dx[ty][tx + 1] = rn_sub(su[ty + 2][tx + 2], su[ty + 2][tx + 1]);
+            dy[ty + 1][tx] = rn_sub(su[ty + 2][tx + 2], su[ty + 1][tx + 2]);
+            if (tx < 3) dx[ty][hx_d] = rn_sub(su[ty + 2][hx_d + 1], su[ty + 2][hx_d]);
+            if (ty < 3) dy[hy_d][tx] = rn_sub(su[hy_d + 1][tx + 2], su[hy_d][tx + 2]);
+            __syncthreads();
+            cx[ty][tx + 1] = rn_sub(dx[ty][tx + 2], dx[ty][tx + 1]);
+            ex[ty][tx + 1] = w3_curv(cx[ty][tx + 1]);
+            cy[ty + 1][tx] = rn_sub(dy[ty + 2][tx], dy[ty + 1][tx]);
+            ey[ty + 1][tx] = w3_curv(cy[ty + 1][tx]);
+            if (tx < 2) {
+                cx[ty][hx_e] = rn_sub(dx[ty][hx_e + 1], dx[ty][hx_e]);
+                ex[ty][hx_e] = w3_curv(cx[ty][hx_e]);
+            }
+            if (ty < 2) {
+                cy[hy_e][tx] = rn_sub(dy[hy_e + 1][tx], dy[hy_e][tx]);
+                ey[hy_e][tx] = w3_curv(cy[hy_e][tx]);
+            }
+            __syncthreads();
+            const long long z = pk + xy;
+            double d[4], D2[3], E[3], b, cc;
+            if (own != 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d[q] = dx[ty][tx + q];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    D2[q] = cx[ty][tx + q];
+                    E[q] = ex[ty][tx + q];
+                }
+                weno3_terms<WANT_C>(d, E, D2, b, cc);
+                S1[((0 * 3 + 0) * NV + v) * N + z] = b;
+                if (WANT_C) S1[((1 * 3 + 0) * NV + v) * N + z] = cc;
+            }
+            if (own != 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d[q] = dy[ty + q][tx];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    D2[q] = cy[ty + q][tx];
+                    E[q] = ey[ty + q][tx];
+                }
+                weno3_terms<WANT_C>(d, E, D2, b, cc);
+                S1[((0 * 3 + 1) * NV + v) * N + z] = b;
+                if (WANT_C) S1[((1 * 3 + 1) * NV + v) * N + z] = cc;
+            }
+            if (own != 2) {
+                weno3_terms<WANT_C>(dz, ez, cz, b, cc);
+                S1[((0 * 3 + 2) * NV + v) * N + z] = b;
+                if (WANT_C) S1[((1 * 3 + 2) * NV + v) * N + z] = cc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int ORDER, int NV>
+static bool launch_weno1d_tiled64(const Grid& g, const double* U, const double* ZB, double* S1, cudaStream_t st) {
+    if (g.nx % CT_X != 0 || g.ny % CT_Y != 0) return false;
+    const dim3 grid((unsigned)((g.nx / CT_X) * (g.ny / CT_Y)), (unsigned)((g.nz + CT_Z - 1) / CT_Z));
+    k_weno1d_tiled64<ORDER, NV><<<grid, dim3(CT_X, CT_Y), 0, st>>>(g, U, ZB, S1);
+    return true;
+}
+
 template <int NV>
 static bool launch_cross1_tiled64(const Grid& g, const double* S1, double* S2, cudaStream_t st) {
     if (g.nx % CT_X != 0 || g.ny % CT_Y != 0) return false;
@@ -379,10 +505,19 @@ static int launch_recon_nv(const StepArgs& a, const double* U, cudaStream_t st) 
     } else {
         Ui = U;
     }
+    // FP64 orders 2-3: the 1-D moments from shared-memory tiles where the grid allows them
+    bool tiled1d = false;
+    if constexpr (sizeof(R) == 8) {
+        if (a.tiled && a.order == 2) tiled1d = launch_weno1d_tiled64<2, NV>(a.grid, Ui, ZB, S1, st);
+        if (a.tiled && a.order == 3) tiled1d = launch_weno1d_tiled64<3, NV>(a.grid, Ui, ZB, S1, st);
+    }
     switch (a.order) {
-        case 2: k_weno1d<2, NV, R, In><<<blocks, T, 0, st>>>(a.grid, Ui, ZB, S1); n += 1; break;
+        case 2:
+            if (!tiled1d) k_weno1d<2, NV, R, In><<<blocks, T, 0, st>>>(a.grid, Ui, ZB, S1);
+            n += 1;
+            break;
         case 3:
-            k_weno1d<3, NV, R, In><<<blocks, T, 0, st>>>(a.grid, Ui, ZB, S1);
+            if (!tiled1d) k_weno1d<3, NV, R, In><<<blocks, T, 0, st>>>(a.grid, Ui, ZB, S1);
             // shared-memory tiles where the grid allows them (and the context has not turned tiles off)
             if constexpr (sizeof(R) == 4) {
                 if (!(a.tiled && launch_cross1_tiled<NV>(a.grid, S1, S2, st)))
