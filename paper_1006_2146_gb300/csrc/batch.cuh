@@ -57,6 +57,21 @@ ADER_DEV bool batch_zone(const BatchGroupDev& g, long long gz, const BatchItem*&
     return z < it->a.grid.n;
 }
 
+// One block-iteration's problem for kernels that read the full step arguments: every block covers
+// BATCH_ALIGN-aligned zones of one problem, so its item is copied once into shared memory, where the zone
+// code reads it (the zone's stores cannot alias it: nothing is reloaded from global memory or held in
+// registers across them).  Returns this thread's zone index in that problem (>= its n on padding).
+// Called by every thread of the block.
+__device__ __forceinline__ long long batch_block_item(const BatchGroupDev& g, long long base, BatchItem& it) {
+    static_assert(sizeof(BatchItem) % sizeof(int) == 0, "BatchItem is copied as ints");
+    const int p = batch_find(g.zpad, g.np, base);
+    __syncthreads();                                    // the previous iteration's readers are done
+    for (int w = threadIdx.x; w < (int)(sizeof(BatchItem) / sizeof(int)); w += blockDim.x)
+        reinterpret_cast<int*>(&it)[w] = reinterpret_cast<const int*>(g.items + p)[w];
+    __syncthreads();
+    return base + threadIdx.x - g.zpad[p];
+}
+
 template <int ORDER, class R>
 __global__ void __launch_bounds__(256) kb_face_b(BatchGroupDev g) {
     for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
@@ -130,52 +145,47 @@ constexpr int BATCH_PREDICT_MAX_THREADS = 128;
 template <int ORDER, int FORM, int NV, class R>
 __global__ void __launch_bounds__(BATCH_PREDICT_MAX_THREADS, ORDER == 4 || (ORDER == 3 && NV == 8) ? 2 : 3)
     kb_predict_faces(BatchGroupDev g) {
-    const long long gz = batch_first();
-    if (gz >= g.total) return;
-    const BatchItem* it;
-    long long z;
-    if (!batch_zone(g, gz, it, z)) return;
-    zone_predict_faces<ORDER, FORM, NV, R>(it->a, it->U, z);     // arguments read in place (fewer spills
-                                                                  // than a copy)
+    __shared__ BatchItem it;                            // the block's arguments (batch_block_item)
+    const long long base = (long long)blockIdx.x * blockDim.x;
+    if (base >= g.total) return;                        // the whole block
+    const long long z = batch_block_item(g, base, it);
+    if (z >= it.a.grid.n) return;
+    zone_predict_faces<ORDER, FORM, NV, R>(it.a, it.U, z);
 }
 
 // U += dt L(U) in place, dt from the problem's dt_dev: both faces of each direction solved per zone, the
 // differences carried in FP32 pairs and only the accumulation in FP64 (zone_flux_update_pair)
 template <int SOLVER, int NV, class R>
 __global__ void __launch_bounds__(256) kb_flux_update(BatchGroupDev g) {
-    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
-        const BatchItem* it;
-        long long z;
-        if (!batch_zone(g, gz, it, z)) continue;
-        const StepArgs a = it->a;
-        double* U = it->U;
+    __shared__ BatchItem it;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < g.total; base += batch_stride()) {
+        const long long z = batch_block_item(g, base, it);
+        if (z >= it.a.grid.n) continue;
+        double* U = it.U;
         if constexpr (sizeof(R) == 4)
-            zone_flux_update_pair<SOLVER, NV>(a, U, U, 1.0, 1, z);
+            zone_flux_update_pair<SOLVER, NV>(it.a, U, U, 1.0, 1, z);
         else
-            zone_flux_update<SOLVER, NV, R>(a, U, U, 1.0, 1, z);
+            zone_flux_update<SOLVER, NV, R>(it.a, U, U, 1.0, 1, z);
     }
 }
 
 template <class R>
 __global__ void __launch_bounds__(256) kb_emf(BatchGroupDev g) {
-    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
-        const BatchItem* it;
-        long long z;
-        if (!batch_zone(g, gz, it, z)) continue;
-        const StepArgs a = it->a;
-        zone_emf<R>(a, z);
+    __shared__ BatchItem it;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < g.total; base += batch_stride()) {
+        const long long z = batch_block_item(g, base, it);
+        if (z >= it.a.grid.n) continue;
+        zone_emf<R>(it.a, z);
     }
 }
 
 template <class R>
 __global__ void __launch_bounds__(256) kb_ct(BatchGroupDev g) {
-    for (long long gz = batch_first(); gz < g.total; gz += batch_stride()) {
-        const BatchItem* it;
-        long long z;
-        if (!batch_zone(g, gz, it, z)) continue;
-        const StepArgs a = it->a;
-        double* Bf = it->Bf;
-        zone_ct<R>(a, Bf, 1.0, 1, z);
+    __shared__ BatchItem it;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < g.total; base += batch_stride()) {
+        const long long z = batch_block_item(g, base, it);
+        if (z >= it.a.grid.n) continue;
+        zone_ct<R>(it.a, it.Bf, 1.0, 1, z);
     }
 }
 
