@@ -6,7 +6,8 @@
 // padded index of problem p (zpad[np] the total).  Launches are persistent:
 // a grid sized to the SMs loops over the padded range.  Because every block
 // size divides BATCH_ALIGN, all threads of a block always work on the same
-// problem, and the padding zones (z >= n of their problem) are skipped.
+// problem, and the padding zones (z >= n of their problem) are skipped.  The
+// predictor is the exception: one zone per thread over the whole padded range.
 #pragma once
 #include "kernels.cuh"
 #include "step_kernels.cuh"
