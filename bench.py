@@ -49,6 +49,11 @@ def parse():
     p.add_argument("--blast-symmetry", action="store_true",
                    help="also run the 3-D hydrodynamic and MHD blasts to their end times (about ten minutes)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batch-only", action="store_true",
+                   help="only the batched-step comparison (64 and 512 problems), one JSON line of its own")
+    p.add_argument("--profile-range", action="store_true",
+                   help="with --batch-only: one sequential and one batched step of each set inside "
+                        "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return p.parse_args()
 
 
@@ -508,10 +513,12 @@ def dense_output_variant(ader, torch, stream, n, U0, reps=5):
     return res
 
 
-def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32, 48, 64, 80, 96, 112, 128)):
+def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32, 48, 64, 80, 96, 112, 128),
+                    profile_range=False):
     """`count` seeded independent problems of uneven cubic sizes (Euler and MHD, orders 2-4, FP32 bulk):
     one tuned batch replayed from a captured graph vs one context per problem launched in sequence.
-    Each step includes every problem's CFL dt."""
+    Each step includes every problem's CFL dt.  profile_range: after the timing, one more step of each
+    inside cudaProfilerStart/Stop."""
     from paper_1006_2146_gb300 import _lib, inputs
     t0 = time.perf_counter()
     probs = inputs.batch_problems(count, seed=1006, sizes=sizes)
@@ -557,6 +564,12 @@ def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32,
             e1.record(stream)
         torch.cuda.synchronize()
         seq_s = e0.elapsed_time(e1) / 1e3
+        if profile_range:
+            torch.cuda.cudart().cudaProfilerStart()
+            with torch.cuda.stream(stream):
+                seq_step()
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
         bad = [k for k, h in enumerate(hs) if _lib.ader_sync_status(h, stream) != 0]
         out["sequential"] = {"zone_updates_per_s": zones * steps / seq_s, "ms_per_step": seq_s / steps * 1e3,
                              "launches_per_step": sum(_lib.ader_launches_per_step(h) + 1 for h in hs),
@@ -592,6 +605,12 @@ def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32,
             e1.record(stream)
         torch.cuda.synchronize()
         bs = e0.elapsed_time(e1) / 1e3
+        if profile_range:
+            torch.cuda.cudart().cudaProfilerStart()
+            with torch.cuda.stream(stream):
+                _lib.ader_batch_advance(b, d, db, 0.4, dtb, stream)
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
         rc, codes = _lib.ader_batch_status(b, len(probs), stream)
         out["batched"] = {"zone_updates_per_s": zones * steps / bs, "ms_per_step": bs / steps * 1e3,
                           "graph_launches_per_step": 1, "groups": _lib.ader_batch_groups(b), "tune_s": tune_s,
@@ -876,9 +895,18 @@ def gpu_arm(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     ader.load()
+    stream = torch.cuda.Stream()
+    if args.batch_only:
+        res = {"batched_64_problems_fp32": batched_variant(ader, torch, stream, profile_range=args.profile_range),
+               "batched_512_small_problems_fp32": batched_variant(ader, torch, stream, count=512, sizes=(16, 24, 32),
+                                                                  profile_range=args.profile_range)}
+        for r in res.values():
+            r.get("batched", {}).pop("tuned_shapes", None)
+        if rank == 0:
+            print(json.dumps(res))
+        return
     n = args.n
     zones = n ** 3
-    stream = torch.cuda.Stream()
     U0 = torch.from_numpy(inputs.sod_planar(n)).to("cuda")
 
     def barrier():
