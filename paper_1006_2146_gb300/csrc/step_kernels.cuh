@@ -904,9 +904,14 @@ ADER_DEV void zone_ct(const StepArgs& a, double* Bf, double c_host, int use_dt_d
     zone_ijk(g, z, i, j, k);
     const R* E = (const R*)a.E;
     const long long N = g.n;
-    auto Ex = [&](int di, int dj, int dk) { return (double)E[nbr(g, i, j, k, di, dj, dk)]; };
-    auto Ey = [&](int di, int dj, int dk) { return (double)E[N + nbr(g, i, j, k, di, dj, dk)]; };
-    auto Ez = [&](int di, int dj, int dk) { return (double)E[2 * N + nbr(g, i, j, k, di, dj, dk)]; };
+    // FP32 edge fields widen to FP64 exactly on the integer pipe (f64_of_f32), not by conversions on the
+    // FP64 units
+    auto wide = [](R e) -> double {
+        if constexpr (sizeof(R) == 4) return f64_of_f32(e); else return e;
+    };
+    auto Ex = [&](int di, int dj, int dk) { return wide(E[nbr(g, i, j, k, di, dj, dk)]); };
+    auto Ey = [&](int di, int dj, int dk) { return wide(E[N + nbr(g, i, j, k, di, dj, dk)]); };
+    auto Ez = [&](int di, int dj, int dk) { return wide(E[2 * N + nbr(g, i, j, k, di, dj, dk)]); };
     const double dt = use_dt_dev ? c_host * (*a.dt_dev) : c_host;
     const double idx = a.idx[0], idy = a.idx[1], idz = a.idx[2];
     // the edges of face i-1/2 are stored one zone lower in x (likewise for y, z)

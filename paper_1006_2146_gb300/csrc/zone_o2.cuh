@@ -11,7 +11,7 @@ template <int NV, class R>
 ADER_DEV void finish_o2(Vec<NV, R>* m, const Vec<NV, R>& n5, PredCtl& ctl) {
     const bool conv = positive_arg(ctl.tol);
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
-    const R ref = max_abs(m[1]) + R(1e-300);
+    const R ref = max_abs(m[1]) + R(sizeof(R) == 8 ? 1e-300 : 1e-30);   // never zero in R
     ctl.iters = 0;
     ctl.capped = conv;
     for (int it = 0; it < cap; ++it) {
@@ -61,7 +61,7 @@ template <int NV, class R, class Next>
 ADER_DEV void iterate_o2(Vec<NV, R>* m, PredCtl& ctl, Next next) {
     const bool conv = positive_arg(ctl.tol);
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
-    const R ref = max_abs(m[1]) + R(1e-300);
+    const R ref = max_abs(m[1]) + R(sizeof(R) == 8 ? 1e-300 : 1e-30);   // never zero in R
     ctl.iters = 0;
     ctl.capped = conv;
     for (int it = 0; it < cap; ++it) {

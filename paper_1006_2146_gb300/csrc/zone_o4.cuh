@@ -201,7 +201,7 @@ ADER_DEV void predict_modal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
 
     const bool conv = positive_arg(ctl.tol);
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
-    const R ref = max_abs(m[1]) + R(1e-300);
+    const R ref = max_abs(m[1]) + R(sizeof(R) == 8 ? 1e-300 : 1e-30);   // never zero in R
     ctl.iters = 0;
     ctl.capped = conv;
     for (int it = 0; it < cap; ++it) {
@@ -415,7 +415,7 @@ ADER_DEV void predict_nodal(Vec<NV, R>* m, R gm1, R cx, R cy, R cz, PredCtl& ctl
     nodal_o4_initial(u, m, e);
     const bool conv = positive_arg(ctl.tol);
     const int cap = conv ? ctl.max_iter : ctl.n_iter;
-    const R ref = max_abs(m[1]) + R(1e-300);
+    const R ref = max_abs(m[1]) + R(sizeof(R) == 8 ? 1e-300 : 1e-30);   // never zero in R
     ctl.iters = 0;
     ctl.capped = conv;
     for (int it = 0; it < cap; ++it) {
