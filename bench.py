@@ -520,6 +520,7 @@ def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32,
     Each step includes every problem's CFL dt.  profile_range: after the timing, one more step of each
     inside cudaProfilerStart/Stop."""
     from paper_1006_2146_gb300 import _lib, inputs
+    _lib.ader_trim_local_memory()                     # the layout the batch's own kernels need (run_config)
     t0 = time.perf_counter()
     probs = inputs.batch_problems(count, seed=1006, sizes=sizes)
     gen_s = time.perf_counter() - t0
@@ -843,6 +844,9 @@ def run_config(ader, torch, n, order, form, solver, fp32, steps, warmup, stream,
     source: (kind, params) of Solver.set_source; tiled: the Euler launch layout (ader_set_tiled).
     """
     from paper_1006_2146_gb300 import inputs
+    # each configuration in the local-memory layout its own kernels need, as when run alone (a fourth-order
+    # FP64 run before it would otherwise leave every later kernel a 5 KB-per-thread stack)
+    ader.ader_trim_local_memory()
     s = ader.Solver((n, n, n), order=order, form=form, solver=solver, fp32=fp32)
     s.set_tiled(tiled)
     if source is not None:

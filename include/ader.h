@@ -266,6 +266,17 @@ int ader_set_guess(ader_ctx* ctx, const float* params);
  * layers on the tensor cores (tcgen05, FP16 operands, FP32 accumulation).
  * Needs ader_set_guess first.  Asynchronous on the stream. */
 int ader_guess_eval(ader_ctx* ctx, const double* U, const double* Bface, double dt, float* G, void* stream);
+/* Local memory of the CUDA context (runtime housekeeping; no counterpart in
+ * the paper).  The context keeps, for every thread of every later launch, the
+ * largest per-thread stack a kernel has needed (the FP64 fourth-order
+ * predictor needs about 5 KB); kernels with smaller frames that spill then
+ * run in that wider layout, the FP32 fourth-order predictor about 25% slower.
+ * This sets the context's stack limit back to 1 KB per thread
+ * (cudaDeviceSetLimit(cudaLimitStackSize)), freeing the rest; the next launch
+ * that needs more grows it again.  *kept_bytes (host, may be NULL) receives
+ * the per-thread stack size held before the call.  Synchronises the device;
+ * not during a stream capture.  ADER_ERR_CUDA if the runtime refuses. */
+int ader_trim_local_memory(size_t* kept_bytes);
 /* Test of the tensor-core kernel's bounded waits (failure detection; no
  * counterpart in the paper).  Arms the context's next learned-guess launch
  * (ader_guess_eval, or a step with a guess): that launch issues no MMA for its

@@ -14,7 +14,7 @@ from ._lib import (ADER_BC_OUTFLOW, ADER_BC_PERIODIC, ADER_BC_REFLECTIVE, ADER_C
                    ader_guess_eval, ader_guess_samples, ader_last_error, ader_launches_per_step, ader_max_dt,
                    ader_mlp_grad, ader_mlp_shape, ader_mlp_train, ader_predictor_stats, ader_profile,
                    ader_profile_read, ader_profile_reset, ader_rk_step, ader_set_dense_output, ader_set_guess,
-                   ader_set_boundary, ader_set_predictor, ader_set_source, ader_set_tiled, ader_step, ader_test_bounded_wait, ader_step_devdt, ader_step_host,
+                   ader_set_boundary, ader_set_predictor, ader_set_source, ader_set_tiled, ader_step, ader_test_bounded_wait, ader_trim_local_memory, ader_step_devdt, ader_step_host,
                    ader_sync_status, load)
 
 

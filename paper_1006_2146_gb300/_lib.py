@@ -22,7 +22,7 @@ ADER_BC_PERIODIC, ADER_BC_OUTFLOW, ADER_BC_REFLECTIVE = 0, 1, 2
 EXPORTS = ("ader_create", "ader_step", "ader_step_devdt", "ader_max_dt", "ader_rk_step", "ader_step_host",
            "ader_diagnostics", "ader_sync_status", "ader_launches_per_step", "ader_profile", "ader_profile_reset",
            "ader_profile_read", "ader_set_tiled", "ader_set_boundary", "ader_set_predictor", "ader_predictor_stats", "ader_set_source", "ader_set_dense_output", "ader_dense_output", "ader_set_guess",
-           "ader_mlp_shape", "ader_guess_samples", "ader_guess_count", "ader_guess_eval", "ader_test_bounded_wait", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy",
+           "ader_mlp_shape", "ader_guess_samples", "ader_guess_count", "ader_guess_eval", "ader_test_bounded_wait", "ader_trim_local_memory", "ader_mlp_train", "ader_mlp_grad", "ader_last_error", "ader_destroy",
            "ader_max_dt_static", "ader_batch_create", "ader_batch_tune", "ader_batch_step", "ader_batch_advance",
            "ader_batch_status", "ader_batch_tuning", "ader_batch_groups", "ader_batch_last_error",
            "ader_batch_destroy")
@@ -79,6 +79,7 @@ def load(path=None):
     lib.ader_guess_samples.argtypes = [vp, vp, vp, dbl, vp, vp, vp, vp]
     lib.ader_guess_eval.argtypes = [vp, vp, vp, dbl, vp, vp]
     lib.ader_test_bounded_wait.argtypes = [vp]
+    lib.ader_trim_local_memory.argtypes = [ctypes.POINTER(ctypes.c_size_t)]
     lib.ader_mlp_train.argtypes = [vp, vp, ctypes.c_longlong, i32, i32, i32, ctypes.c_float, ctypes.c_ulonglong,
                                    vp, ctypes.POINTER(dbl), vp]
     lib.ader_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_longlong, i32, vp, ctypes.POINTER(dbl), vp]
@@ -266,6 +267,15 @@ def ader_mlp_shape(mhd=False):
 def ader_guess_samples(h, U, Bface, dt, X, Y, ok, stream=None):
     return _check(h, load().ader_guess_samples(h, _ptr(U), _ptr(Bface), float(dt), _ptr(X), _ptr(Y), _ptr(ok),
                                                _stream(stream)))
+
+
+def ader_trim_local_memory():
+    """Per-thread stack back to 1 KB; returns the size the context held before (bytes)."""
+    kept = ctypes.c_size_t(0)
+    rc = load().ader_trim_local_memory(ctypes.byref(kept))
+    if rc != ADER_OK:
+        raise AderError(rc, "the CUDA runtime refused the stack limit")
+    return kept.value
 
 
 def ader_test_bounded_wait(h):

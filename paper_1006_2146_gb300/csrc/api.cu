@@ -665,6 +665,14 @@ int ader_set_guess(ader_ctx* c, const float* params) {
     return ADER_OK;
 }
 
+int ader_trim_local_memory(size_t* kept_bytes) {
+    size_t kept = 0;
+    if (cudaDeviceGetLimit(&kept, cudaLimitStackSize) != cudaSuccess) return ADER_ERR_CUDA;
+    if (kept_bytes) *kept_bytes = kept;
+    if (cudaDeviceSynchronize() != cudaSuccess) return ADER_ERR_CUDA;
+    return cudaDeviceSetLimit(cudaLimitStackSize, 1024) == cudaSuccess ? ADER_OK : ADER_ERR_CUDA;
+}
+
 int ader_test_bounded_wait(ader_ctx* c) {
     if (!c) return ADER_ERR_ARG;
     if (!c->guess) return fail(c, ADER_ERR_ARG, "no guess parameters set (ader_set_guess)");
