@@ -206,9 +206,26 @@ ADER_DEV Vec<NV, R> flux_from(const Vec<NV, R>& u, const Prim<NV, R>& q) {
     return f;
 }
 
+// the physical flux of one direction from the conserved state; Euler takes only what that direction
+// needs (the normal velocity and P = (gamma - 1)(eps - |rho v|^2 / 2 rho), no transverse velocities)
 template <int D, int NV, class R>
 ADER_DEV Vec<NV, R> flux(const Vec<NV, R>& u, R gm1) {
-    return flux_from<D>(u, primitives(u, gm1));
+    if constexpr (NV == 5) {
+        const R irho = rcp(u[0]);
+        const R vn = u[1 + D] * irho;
+        const R m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+        const R p = gm1 * (u[4] - R(0.5) * irho * m2);
+        Vec<NV, R> f;
+        f[0] = u[1 + D];
+        f[1] = u[1] * vn;
+        f[2] = u[2] * vn;
+        f[3] = u[3] * vn;
+        f[1 + D] += p;
+        f[4] = (u[4] + p) * vn;
+        return f;
+    } else {
+        return flux_from<D>(u, primitives(u, gm1));
+    }
 }
 
 // fast magnetosonic speed in direction D (the sound speed for Euler)
