@@ -37,6 +37,7 @@ inline Cnt sqrt(Cnt a) { ++g_sqrt; return Cnt(std::sqrt(a.v)); }
 inline Cnt fmin(Cnt a, Cnt b) { ++g_cmp; return Cnt(std::fmin(a.v, b.v)); }
 inline Cnt fmax(Cnt a, Cnt b) { ++g_cmp; return Cnt(std::fmax(a.v, b.v)); }
 inline Cnt fabs(Cnt a) { ++g_cmp; return Cnt(std::fabs(a.v)); }
+inline Cnt fma(Cnt a, Cnt b, Cnt c) { ++g_mul; ++g_add; return Cnt(std::fma(a.v, b.v, c.v)); }
 
 #include "../weno.cuh"
 #include "../step_inst.cuh"

@@ -313,24 +313,24 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_cross1_tiled64(Grid g, const do
             for (int q = 0; q < 4; ++q) d[q] = dy2[ty + q][tx];
 #pragma unroll
             for (int q = 0; q < 3; ++q) E[q] = ey2[ty + q][tx];
-            weno3_terms<false>(d, E, nullptr, sy2, unused);
+            weno3_terms<false, double>(d, E, nullptr, sy2, unused);
 #pragma unroll
             for (int q = 0; q < 4; ++q) d[q] = dx3[ty][tx + q];
 #pragma unroll
             for (int q = 0; q < 3; ++q) E[q] = ex3[ty][tx + q];
-            weno3_terms<false>(d, E, nullptr, sx3, unused);
-            weno3_terms<false>(dz3, ez3, nullptr, sz3, unused);
+            weno3_terms<false, double>(d, E, nullptr, sx3, unused);
+            weno3_terms<false, double>(dz3, ez3, nullptr, sz3, unused);
 #pragma unroll
             for (int q = 0; q < 4; ++q) d[q] = dy4[ty + q][tx];
 #pragma unroll
             for (int q = 0; q < 3; ++q) E[q] = ey4[ty + q][tx];
-            weno3_terms<false>(d, E, nullptr, sy4, unused);
-            weno3_terms<false>(dz2, ez2, nullptr, sz2, unused);
+            weno3_terms<false, double>(d, E, nullptr, sy4, unused);
+            weno3_terms<false, double>(dz2, ez2, nullptr, sz2, unused);
 #pragma unroll
             for (int q = 0; q < 4; ++q) d[q] = dx4[ty][tx + q];
 #pragma unroll
             for (int q = 0; q < 3; ++q) E[q] = ex4[ty][tx + q];
-            weno3_terms<false>(d, E, nullptr, sx4, unused);
+            weno3_terms<false, double>(d, E, nullptr, sx4, unused);
             const long long z = pk + xy;
             S2[(0 * NV + v) * N + z] = rn_mul(0.5, rn_add(sy2, sx3));
             S2[(1 * NV + v) * N + z] = rn_mul(0.5, rn_add(sz3, sy4));
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_weno1d_tiled64(Grid g, const do
                     D2[q] = cx[ty][tx + q];
                     E[q] = ex[ty][tx + q];
                 }
-                weno3_terms<WANT_C>(d, E, D2, b, cc);
+                weno3_terms<WANT_C, double>(d, E, D2, b, cc);
                 S1[((0 * 3 + 0) * NV + v) * N + z] = b;
                 if (WANT_C) S1[((1 * 3 + 0) * NV + v) * N + z] = cc;
             }
@@ -444,12 +444,12 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_weno1d_tiled64(Grid g, const do
                     D2[q] = cy[ty + q][tx];
                     E[q] = ey[ty + q][tx];
                 }
-                weno3_terms<WANT_C>(d, E, D2, b, cc);
+                weno3_terms<WANT_C, double>(d, E, D2, b, cc);
                 S1[((0 * 3 + 1) * NV + v) * N + z] = b;
                 if (WANT_C) S1[((1 * 3 + 1) * NV + v) * N + z] = cc;
             }
             if (own != 2) {
-                weno3_terms<WANT_C>(dz, ez, cz, b, cc);
+                weno3_terms<WANT_C, double>(dz, ez, cz, b, cc);
                 S1[((0 * 3 + 2) * NV + v) * N + z] = b;
                 if (WANT_C) S1[((1 * 3 + 2) * NV + v) * N + z] = cc;
             }

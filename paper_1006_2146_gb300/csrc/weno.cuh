@@ -81,22 +81,26 @@ ADER_DEV void weno3_doubled(const R* a, R* al, R& inv, R* B, R* C) {
 // values with the same operations, so the two give the same bits.  The weights clear their denominators
 // as weno_weights does: (1, 10, 1) times the product of the other two (EPS + IS)^2.
 // Every operation of this form is explicitly rounded (no multiply-add contraction left to the compiler),
-// so that the tile and the per-zone kernel, compiled apart, round every step alike.
-ADER_DEV double rn_add(double x, double y) {
+// so that the tile and the per-zone kernel, compiled apart, round every step alike.  (Other scalar types,
+// such as the host FLOP counter's, take the plain operators.)
+template <class R> ADER_DEV R rn_add(R x, R y) { return x + y; }
+template <class R> ADER_DEV R rn_sub(R x, R y) { return x - y; }
+template <class R> ADER_DEV R rn_mul(R x, R y) { return x * y; }
+template <> ADER_DEV double rn_add<double>(double x, double y) {
 #ifdef __CUDA_ARCH__
     return __dadd_rn(x, y);
 #else
     return x + y;
 #endif
 }
-ADER_DEV double rn_sub(double x, double y) {
+template <> ADER_DEV double rn_sub<double>(double x, double y) {
 #ifdef __CUDA_ARCH__
     return __dsub_rn(x, y);
 #else
     return x - y;
 #endif
 }
-ADER_DEV double rn_mul(double x, double y) {
+template <> ADER_DEV double rn_mul<double>(double x, double y) {
 #ifdef __CUDA_ARCH__
     return __dmul_rn(x, y);
 #else
@@ -104,21 +108,23 @@ ADER_DEV double rn_mul(double x, double y) {
 #endif
 }
 
-ADER_DEV double w3_curv(double D2) { return fma(rn_mul(13.0 / 3.0, D2), D2, 4.0 * WENO_EPS); }
+template <class R>
+ADER_DEV R w3_curv(R D2) { return fma(rn_mul(R(13.0 / 3.0), D2), D2, R(4.0 * WENO_EPS)); }
 
-template <bool WANT_C>
-ADER_DEV void weno3_terms(const double* d, const double* E, const double* D2, double& b, double& c) {
-    const double B0 = fma(3.0, d[1], -d[0]), B1 = rn_add(d[1], d[2]), B2 = fma(3.0, d[2], -d[3]);
-    const double t0 = fma(B0, B0, E[0]), t1 = fma(B1, B1, E[1]), t2 = fma(B2, B2, E[2]);
-    const double q0 = rn_mul(t0, t0), q1 = rn_mul(t1, t1), q2 = rn_mul(t2, t2);
-    const double a0 = rn_mul(q1, q2), a1 = rn_mul(10.0, rn_mul(q0, q2)), a2 = rn_mul(q0, q1);
-    const double h = rn_mul(0.5, rcp(rn_add(rn_add(a0, a1), a2)));
+template <bool WANT_C, class R>
+ADER_DEV void weno3_terms(const R* d, const R* E, const R* D2, R& b, R& c) {
+    const R B0 = fma(R(3.0), d[1], -d[0]), B1 = rn_add(d[1], d[2]), B2 = fma(R(3.0), d[2], -d[3]);
+    const R t0 = fma(B0, B0, E[0]), t1 = fma(B1, B1, E[1]), t2 = fma(B2, B2, E[2]);
+    const R q0 = rn_mul(t0, t0), q1 = rn_mul(t1, t1), q2 = rn_mul(t2, t2);
+    const R a0 = rn_mul(q1, q2), a1 = rn_mul(R(10.0), rn_mul(q0, q2)), a2 = rn_mul(q0, q1);
+    const R h = rn_mul(R(0.5), rcp(rn_add(rn_add(a0, a1), a2)));
     b = rn_mul(fma(a0, B0, fma(a1, B1, rn_mul(a2, B2))), h);
     if (WANT_C) c = rn_mul(fma(a0, D2[0], fma(a1, D2[1], rn_mul(a2, D2[2]))), h);
 }
 
 // the per-position terms of zone j from w(j-2..j+2)
-ADER_DEV void weno3_zone_terms(const double* a, double* d, double* D2, double* E) {
+template <class R>
+ADER_DEV void weno3_zone_terms(const R* a, R* d, R* D2, R* E) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) d[s] = rn_sub(a[s + 1], a[s]);
 #pragma unroll
@@ -131,9 +137,9 @@ ADER_DEV void weno3_zone_terms(const double* a, double* d, double* D2, double* E
 template <class R>
 ADER_DEV void weno3(const R* a, R& b, R& c) {
     if constexpr (sizeof(R) == 8) {
-        double d[4], D2[3], E[3];
+        R d[4], D2[3], E[3];
         weno3_zone_terms(a, d, D2, E);
-        weno3_terms<true>(d, E, D2, b, c);
+        weno3_terms<true, R>(d, E, D2, b, c);
     } else {
         R al[3], B[3], C[3], inv;
         weno3_doubled(a, al, inv, B, C);
@@ -222,9 +228,9 @@ template <class R>
 ADER_DEV R slope(const R* a) {
     R b, c;
     if constexpr (sizeof(R) == 8) {     // the slope alone: no curvature blend
-        double d[4], D2[3], E[3];
+        R d[4], D2[3], E[3];
         weno3_zone_terms(a, d, D2, E);
-        weno3_terms<false>(d, E, D2, b, c);
+        weno3_terms<false, R>(d, E, D2, b, c);
     } else {
         weno3(a, b, c);
     }
