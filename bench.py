@@ -520,7 +520,7 @@ def batched_variant(ader, torch, stream, steps=3, warmup=1, count=64, sizes=(32,
     Each step includes every problem's CFL dt.  profile_range: after the timing, one more step of each
     inside cudaProfilerStart/Stop."""
     from paper_1006_2146_gb300 import _lib, inputs
-    _lib.ader_trim_local_memory()                     # the layout the batch's own kernels need (run_config)
+    trim_local_memory(_lib)                           # the layout the batch's own kernels need (run_config)
     t0 = time.perf_counter()
     probs = inputs.batch_problems(count, seed=1006, sizes=sizes)
     gen_s = time.perf_counter() - t0
@@ -836,6 +836,14 @@ def learned_variants(ader, torch, n, U0, stream, steps=3):
 
 
 
+def trim_local_memory(lib):
+    """ader_trim_local_memory, best effort: housekeeping between configurations, never a reason to fail."""
+    try:
+        lib.ader_trim_local_memory()
+    except Exception as exc:                           # noqa: BLE001 - reported, not fatal
+        print("note: local memory not trimmed (%s)" % exc, file=sys.stderr)
+
+
 def run_config(ader, torch, n, order, form, solver, fp32, steps, warmup, stream, profile=False, state=None,
                tol=None, guess=None, source=None, tiled=True):
     """Times `steps` steps of max_dt + step_devdt; returns (seconds, profile dict, solver, device state).
@@ -846,7 +854,7 @@ def run_config(ader, torch, n, order, form, solver, fp32, steps, warmup, stream,
     from paper_1006_2146_gb300 import inputs
     # each configuration in the local-memory layout its own kernels need, as when run alone (a fourth-order
     # FP64 run before it would otherwise leave every later kernel a 5 KB-per-thread stack)
-    ader.ader_trim_local_memory()
+    trim_local_memory(ader)
     s = ader.Solver((n, n, n), order=order, form=form, solver=solver, fp32=fp32)
     s.set_tiled(tiled)
     if source is not None:
