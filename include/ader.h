@@ -63,7 +63,10 @@ enum {
                                            (MHD: P with the mean of the new face field) take the
                                            first-order HLL flux of the zone averages of step n and the
                                            zones around them are updated again (conservative; three
-                                           passes; the face field is left to constrained transport).
+                                           passes).  MHD: every edge touching such a zone takes the
+                                           first-order edge field (Eq. 7 from those fluxes) and the
+                                           face field is advanced again from step n by Eq. 8 (div B
+                                           kept).
                                            Costs a copy of U (5 x zones FP64) held by the context.  After
                                            the passes the step itself reports what is left: a non-finite
                                            zone value or (MHD) face value raises ADER_ERR_NONFINITE, a zone
